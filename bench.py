@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark: multi-octave polynomial-noise heightmap generation on GB300.
+
+Workload (one step = one pass of the whole generation path): a 2D heightmap of
+8192 x 8192 samples, 12 octaves, base lattice 8 x 8 cells (1024 samples per
+cell), C1 polynomial cells, persistence 0.5, lacunarity 2, FP32 output, seeds
+cycling 0..3 (Thorimbert & Chopard, arXiv:1610.03525: cell polynomial of
+Sec. 3, fractal sum of Sec. 4).  The output (268 MB) is larger than L2, so no
+flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gsamples/s and % of roofline (8192² 12-oct C1) vs Perlin/OpenSimplex; p50/p99"
+UNIT = "Gsamples/s"
+SIZE, SPC, OCTAVES = (8192, 8192), 1024, 12
+WORKLOAD = "2D heightmap 8192x8192, 12 octaves, base lattice 8x8 (spc 1024), C1, p=0.5, L=2, FP32 out, seeds 0..3"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def shard_seed(rank: int, step: int) -> int:
+    """Seed of a step on a rank: each rank makes its own fields (weak scaling,
+    no data exchange); seeds 0..3 cycle per step as in the workload."""
+    return (rank * 4 + step % 4) % (1 << 24)
+
+
+def aggregate_max(value: float, world: int):
+    """Max of a per-rank value over all ranks (identity at world size 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples (200 ms period) in the background."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        inside = [p for (t, p) in self.samples if t0 - 0.05 <= t <= t1 + 0.05]
+        src = "timed_region"
+        if len(inside) < 3:
+            inside = [p for (t, p) in self.samples]
+            src = "timed_region_and_adjacent_window"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[2]) for p in inside if num(p[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for p in inside:
+            for k, n in enumerate(names):
+                if p[6 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(inside[0][3]),
+                "power_w_max": max((num(p[4]) or 0.0) for p in inside), "reasons": sorted(reasons),
+                "samples": len(inside), "source": src}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the timed kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fbm2d_c1_8192_n12.md")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in ("ptg_fbm2d.cu", "ptg_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1610_03525_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    src = h.hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != src:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def oracle_sample_rate(rows: int, seed: int = 0):
+    """Oracle throughput on `rows` distinct full rows of the workload, evenly
+    spread over the field.  Returns (samples/s, samples, seconds, threads)."""
+    import numpy as np
+    import oracle as O
+    ys = np.unique(np.linspace(0, SIZE[1] - 1, max(1, rows)).astype(np.int64))
+    idx = np.concatenate([np.stack([np.arange(SIZE[0]), np.full(SIZE[0], y)], 1) for y in ys]).astype(np.int64)
+    O.lib()
+    t0 = time.perf_counter()
+    O.field_samples(2, (SPC, SPC), (1, 1), idx, octaves=OCTAVES, method=O.C1, seed=seed, persistence=0.5)
+    dt = time.perf_counter() - t0
+    return idx.shape[0] / dt, idx.shape[0], dt, O.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    rows = max(1, args.ref_rows)
+    for _ in range(args.warmup):
+        oracle_sample_rate(1)
+    per = []
+    tot_samples = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        rate, n, dt, threads = oracle_sample_rate(rows, seed=k % 4)
+        per.append(dt)
+        tot_samples += n
+    elapsed = time.perf_counter() - t0
+    value = tot_samples / elapsed / 1e9
+    sample = "%d full rows (%d samples) of the 8192^2 field per step, oracle FP64, %d threads" % (
+        rows, rows * SIZE[0], threads)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-rows", type=int, default=32)
+    ap.add_argument("--cpu-rows", type=int, default=1536, help="oracle rows for the cpu_baseline sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip baselines, e2e and the oracle leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1610_03525_gb300 import build as _build
+    _build.build()
+    import paper_1610_03525_gb300 as P
+    from paper_1610_03525_gb300 import roofline as R
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx = P.ptg_create(local)
+    stream = torch.cuda.current_stream()
+    n_samples = SIZE[0] * SIZE[1]
+    out = torch.empty((SIZE[1], SIZE[0]), dtype=torch.float32, device="cuda")
+    descs = [P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, smoothness=P.PTG_C1, persistence=0.5,
+                         seed=shard_seed(rank, k)) for k in range(4)]
+
+    def step(k):
+        P.ptg_field(ctx, descs[k % 4], out, stream)
+
+    for k in range(args.warmup):
+        step(k)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)  # let the sampler take its first readings
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step(k)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    barrier()
+    wall1 = time.time()
+    # adjacent window of identical work for clock readings when the timed
+    # region is shorter than the sampling period
+    while time.time() - wall1 < 1.0:
+        for k in range(8):
+            step(k)
+        torch.cuda.synchronize()
+    sampler.stop()
+    clocks = sampler.summary(wall0, wall1)
+    local_ms = t_start.elapsed_time(t_end)
+    max_ms = aggregate_max(local_ms, world)
+    per = sorted(a.elapsed_time(b) for a, b in ev)
+    value = world * n_samples * args.steps / (max_ms / 1e3) / 1e9
+    avg_launch_s = statistics.mean(per) / 1e3
+
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = R.alu_peak(props.multi_processor_count, sm_max)
+    ops = R.lane_ops_2d("c1", SIZE, SPC, OCTAVES)
+    achieved = ops["total"] / avg_launch_s
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-ops/s",
+            "frac": achieved / peak, "traffic": profile_traffic(),
+            "ops_per_launch": ops["total"], "ops_per_sample": ops["per_sample"],
+            "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (
+                props.multi_processor_count, sm_max, peak_src),
+            "hbm_write_gbs": n_samples * 4 / avg_launch_s / 1e9,
+            "hbm_frac": n_samples * 4 / avg_launch_s / 1e9 / float(peaks.get("hbm_gbs", 6800.0))}
+    if clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / R.alu_peak(props.multi_processor_count, clocks["sm_mhz"])
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": world, "samples_per_step": world * n_samples,
+                   "parallelism": "replicas (independent fields per rank)" if world > 1 else "single GPU",
+                   "l2": "output 268 MB > 129 MB L2 each step; no flush"},
+        "p50_ms": per[len(per) // 2], "p99_ms": per[min(len(per) - 1, int(0.99 * len(per)))],
+        "gpu_launches": args.steps,
+        "roofline": roof,
+        "clocks": clocks,
+    }
+
+    if not args.no_extras:
+        # same-GPU baselines and variants at the same size and octave count
+        extras = {}
+        n_ex = max(5, min(args.steps, 50))
+
+        def time_fn(fn, dtype=torch.float32, reps=n_ex):
+            o = torch.empty((SIZE[1], SIZE[0]), dtype=dtype, device="cuda")
+            for _ in range(3):
+                fn(o)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn(o)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            del o
+            return {"gsamples_s": n_samples / ms / 1e6, "ms": ms}
+        dC2 = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, smoothness=P.PTG_C2, seed=0)
+        d16 = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, smoothness=P.PTG_C1, seed=0,
+                          dtype=P.PTG_F16)
+        dP = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, seed=0, variant=P.PTG_PERLIN_S5)
+        extras["c2_f32"] = time_fn(lambda o: P.ptg_field(ctx, dC2, o, stream))
+        extras["c1_f16"] = time_fn(lambda o: P.ptg_field(ctx, d16, o, stream), torch.float16)
+        extras["perlin_s5_f32"] = time_fn(lambda o: P.ptg_perlin(ctx, dP, o, stream))
+        extras["opensimplex_f32"] = time_fn(lambda o: P.ptg_opensimplex(ctx, dP, o, stream), reps=5)
+        for k, v in extras.items():
+            v["ops_per_sample"] = R.lane_ops_2d({"c2_f32": "c2", "c1_f16": "c1", "perlin_s5_f32": "perlin_s5",
+                                                 "opensimplex_f32": "opensimplex"}[k], SIZE, SPC,
+                                                OCTAVES)["per_sample"]
+        line["baselines"] = extras
+
+        # end to end through the C ABI into pinned host memory
+        host = torch.empty((SIZE[1], SIZE[0]), dtype=torch.float32).pin_memory()
+        P.ptg_generate_host(ctx, descs[0], P.METHOD_FIELD, host)
+        n_e2e = max(3, min(args.steps, 20))
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            P.ptg_generate_host(ctx, descs[k % 4], P.METHOD_FIELD, host)
+        dt = aggregate_max(time.perf_counter() - t0, world)
+        line["e2e"] = {"value": world * n_samples * n_e2e / dt / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": P.ctypes.sizeof(P.ptg_field_desc),
+                       "d2h_bytes_per_step": n_samples * 4, "steps": n_e2e,
+                       "note": "descriptor in, whole FP32 field out to pinned host memory; banded D2H overlapped "
+                               "with generation"}
+        if rank == 0 and world == 1:
+            rate, n, dtc, threads = oracle_sample_rate(args.cpu_rows)
+            line["cpu_baseline"] = {"value": rate / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                    "sample": "%d full rows (%d samples) of the 8192^2 field, %.1f s" % (
+                                        args.cpu_rows, n, dtc)}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

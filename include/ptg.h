@@ -1,0 +1,187 @@
+/*
+ * ptg.h -- C ABI of the GB300 polynomial terrain-noise library.
+ *
+ * Method: Thorimbert & Chopard, "Polynomial methods for fast Procedural
+ * Terrain Generation", arXiv:1610.03525.  A field is the fractal (fBm) sum of
+ * Sec. 4 over N octaves; octave i uses a lattice 2^i times finer than the base
+ * lattice and amplitude persistence^i.  In every octave each sample finds its
+ * lattice cell (the unit cell of Sec. 2.1), takes pseudo-random values and
+ * gradients at the cell's corners and evaluates the cell polynomial of
+ * Eq. (polynomial) that meets the corner constraints of Eq. (mixedderiv):
+ *   PTG_C1 -- D2M1N3 / D3M1N3 (Sec. 3.1, 3.4) with zero mixed corner
+ *             derivatives: the tensor-product cubic Hermite cell, C1 across
+ *             cell faces;
+ *   PTG_C2 -- the M = 2 analogue (Sec. 3.4) with per-variable degree 5 and
+ *             zero second-order corner derivatives: C2 across faces.
+ * Perlin's polynomial (Sec. 3.2) and an OpenSimplex-style simplex-lattice
+ * gradient noise (the comparison points of Sec. 1 and 5) use the same octave
+ * sum.
+ *
+ * Conventions shared by every call
+ *   - Sample j of axis k sits at base-lattice coordinate
+ *     origin[k] + (offset[k] + j) / spc: spc samples per base cell (a power of
+ *     two, the same on every axis), origin in whole base cells, offset in
+ *     samples.  A field is a window of an unbounded world, so chunks of any
+ *     size tile it exactly (the locality argument of Sec. 1).  Cell indices
+ *     wrap modulo 2^32.
+ *   - Corner data comes from a counter-based hash (pcg3d in 2D, pcg4d in 3D;
+ *     Jarzynski & Olano, JCGT 9(3) 2020) of (ix, iy[, iz], seed << 8 | i);
+ *     each output word u maps to (u >> 9) * 2^-22 - 1 in [-1, 1).  Word 0 is
+ *     the corner value, words 1.. the gradient along x, y[, z], scaled by
+ *     grad_weight (the weight w of Sec. 4).
+ *   - out is row-major: out[y * W + x] in 2D, out[(z * H + y) * W + x] in 3D,
+ *     FP32 or FP16 (round to nearest even from the FP32 sum).
+ *   - Device pointers are caller-owned device memory of at least
+ *     prod(size) * sizeof(dtype) bytes; the library never frees or keeps them
+ *     past the completion of the call's work.
+ *   - stream is a cudaStream_t, or NULL for the context's own stream.  Calls
+ *     return after enqueueing; results are ready when the stream is.
+ *   - Argument errors return synchronously and write nothing.  Asynchronous
+ *     CUDA errors are reported as PTG_ERR_CUDA by the next call.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef PTG_H
+#define PTG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ptg_ctx ptg_ctx;
+
+typedef enum {
+    PTG_OK = 0,
+    PTG_PENDING = 1,
+    PTG_ERR_INVALID = -1,     /* bad argument                                  */
+    PTG_ERR_UNSUPPORTED = -2, /* valid but not supported (e.g. lacunarity != 2)*/
+    PTG_ERR_NOMEM = -3,       /* an allocation failed                          */
+    PTG_ERR_BUDGET = -4,      /* request can never fit the HBM budget          */
+    PTG_ERR_CUDA = -5,        /* a CUDA call failed                            */
+    PTG_ERR_TIMEOUT = -6,     /* a bounded wait ran out                        */
+    PTG_ERR_CANCELLED = -7
+} ptg_status;
+
+typedef enum { PTG_C1 = 1, PTG_C2 = 2 } ptg_smoothness;
+
+typedef enum { PTG_F32 = 0, PTG_F16 = 1 } ptg_dtype;
+
+/* Perlin blend (Sec. 3.2): smootherstep S5 (default) or smoothstep S3. */
+typedef enum { PTG_PERLIN_S5 = 0, PTG_PERLIN_S3 = 1 } ptg_perlin_blend;
+
+/* Full description of one field (Sec. 2.1 cell lattice, Sec. 4 octaves). */
+typedef struct {
+    uint32_t struct_size; /* sizeof(ptg_field_desc)                            */
+    int32_t dims;         /* 2 or 3                                            */
+    int64_t size[3];      /* samples per axis (x, y, z), each in [1, 2^30]; unused = 1 */
+    int64_t spc;          /* samples per base cell: power of two in [1, 2^30]  */
+    int64_t origin[3];    /* base-lattice cell of the window (wraps mod 2^32)  */
+    int64_t offset[3];    /* sample offset of the window: a multiple of
+                             min(spc, tile) with tile 64 (2D) or 32/16/8 (3D
+                             x/y/z); offset + size <= 2^31                     */
+    int32_t octaves;      /* N in [1, 32]                                      */
+    int32_t smoothness;   /* ptg_smoothness (ptg_field, ptg_submit)            */
+    float persistence;    /* amplitude ratio between octaves (0.5 typical)     */
+    float lacunarity;     /* frequency ratio between octaves; must be 2        */
+    float grad_weight;    /* w of Sec. 4; 1.0 default, 0.01 = the paper's      */
+    uint32_t seed;        /* < 2^24                                            */
+    int32_t dtype;        /* ptg_dtype                                         */
+    int32_t variant;      /* ptg_perlin_blend for ptg_perlin; else 0           */
+} ptg_field_desc;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * output bytes that the request loop (ptg_submit) holds admitted at once;
+ * 0 means 40 GiB.  *ctx receives the handle.  Returns PTG_OK,
+ * PTG_ERR_INVALID (ctx NULL, bad device) or PTG_ERR_CUDA. */
+int ptg_create(ptg_ctx** ctx, int device, uint64_t hbm_budget_bytes);
+
+/* Wait for outstanding work and free the context.  NULL is allowed. */
+int ptg_destroy(ptg_ctx* ctx);
+
+/* 2D heightmap of Sec. 4 with the short-form defaults: spc = 64, origin 0,
+ * offset 0, grad_weight 1, FP32 output.  size[2] = (W, H).
+ * out: device, W*H floats. */
+int ptg_heightmap2d(ptg_ctx* ctx, const int64_t size[2], int32_t octaves, int32_t smoothness,
+                    float persistence, float lacunarity, uint32_t seed, void* out, void* stream);
+
+/* 3D volume, same defaults (spc = 64, FP32 output).  size[3] = (W, H, D).
+ * out: device, W*H*D floats. */
+int ptg_volume3d(ptg_ctx* ctx, const int64_t size[3], int32_t octaves, int32_t smoothness,
+                 float persistence, float lacunarity, uint32_t seed, void* out, void* stream);
+
+/* Polynomial-noise field from a full descriptor (C1 or C2, 2D or 3D). */
+int ptg_field(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, void* stream);
+
+/* Perlin's polynomial (Sec. 3.2) with the same lattice, hash words 1..2 as
+ * the corner gradient (unweighted), desc->variant selects S5 or S3.  2D. */
+int ptg_perlin(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, void* stream);
+
+/* OpenSimplex-style noise (Sec. 1, Sec. 5 baseline): the base lattice is
+ * squished into equilateral triangles of edge sqrt(2) (stretch
+ * (1/sqrt(3) - 1)/2, squish (sqrt(3) - 1)/2); every vertex (a, b) within
+ * distance sqrt(2) of the point adds (2 - r^2)^4 (g . d), g from hash words
+ * 1..2 of (a, b, seed << 8 | i); the sum is scaled by 1/8.  2D; the
+ * finest octave's lattice coordinates must stay below 2^30 in magnitude
+ * ((|origin| + (offset + size)/spc) * 2^(N-1) < 2^30), else
+ * PTG_ERR_UNSUPPORTED. */
+int ptg_opensimplex(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, void* stream);
+
+/* Generate into HOST memory: the field is produced in bands on the device and
+ * each band is copied to `host_out` while the next is computed.  Blocks until
+ * the whole field is in host_out.  host_out should be pinned for full copy
+ * bandwidth.  method: 0 = ptg_field, 1 = ptg_perlin, 2 = ptg_opensimplex.
+ * Uses context-owned device staging (allocated on first use, kept). */
+int ptg_generate_host(ptg_ctx* ctx, const ptg_field_desc* desc, int32_t method, void* host_out);
+
+/* Batched generation: n independent fields (any mix of 2D sizes, octave
+ * counts, C1/C2, seeds, origins) in ONE persistent launch.  descs: host array
+ * of n descriptors; outs: host array of n device output pointers.  Work is
+ * split into tiles pulled from a device work list by resident CTAs.
+ * Uses context-owned device memory for the work list (grown on demand). */
+int ptg_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n, void* stream);
+
+/* Request loop.  Queue one field for asynchronous generation into device
+ * memory `out`.  Requests are admitted in arrival order while the admitted
+ * output bytes stay within the context's HBM budget; admitted requests run
+ * concurrently on the context's worker streams.  *req_id receives the id.
+ * Returns PTG_ERR_BUDGET if the request alone exceeds the budget. */
+int ptg_submit(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, uint64_t* req_id);
+
+/* Non-blocking status of a request: *st = PTG_PENDING or its final status;
+ * ts_ns (may be NULL) = submit, admit, start and end times in ns of a
+ * monotonic host clock (0 where not reached yet).  Returns PTG_OK or
+ * PTG_ERR_INVALID (unknown id). */
+int ptg_poll(ptg_ctx* ctx, uint64_t req_id, ptg_status* st, uint64_t ts_ns[4]);
+
+/* Wait at most timeout_ns for a request; returns its final status or
+ * PTG_ERR_TIMEOUT. */
+int ptg_wait(ptg_ctx* ctx, uint64_t req_id, uint64_t timeout_ns);
+
+/* Check a descriptor for generator `method` (0 = ptg_field, 1 = ptg_perlin,
+ * 2 = ptg_opensimplex) without touching any device: returns the status the
+ * generator would return for its arguments (PTG_OK, PTG_ERR_INVALID or
+ * PTG_ERR_UNSUPPORTED) and writes the reason into msg (msg_len bytes, may be
+ * NULL). */
+int ptg_validate(const ptg_field_desc* desc, int32_t method, char* msg, int32_t msg_len);
+
+/* Text of the last error reported on this context ("" if none). */
+const char* ptg_last_error(ptg_ctx* ctx);
+
+/* --- Test hooks (same device code as the generators) ------------------- */
+
+/* Hash n keys of dims+1 words (dims 2: pcg3d, 3: pcg4d) on the device.
+ * keys, out: device arrays of n*(dims+1) uint32. */
+int ptg_debug_hash(ptg_ctx* ctx, int32_t dims, const uint32_t* keys, int64_t n, uint32_t* out, void* stream);
+
+/* Cell index and in-cell position of n sample indices j (device int64) on
+ * one axis at octave i, with the generators' fixed-point map:
+ * cell (device uint32) and t (device float). */
+int ptg_debug_axis(ptg_ctx* ctx, int64_t origin, int64_t spc, int32_t octave, const int64_t* j, int64_t n,
+                   uint32_t* cell, float* t, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTG_H */

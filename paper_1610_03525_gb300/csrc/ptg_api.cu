@@ -1,0 +1,381 @@
+// ptg_api.cu -- the C ABI declared in include/ptg.h: argument validation,
+// per-field launch plans, contexts, and the banded host-output path.
+//
+// Method: Thorimbert & Chopard, arXiv:1610.03525 (cell polynomials of
+// Sec. 2-3, fractal sum of Sec. 4).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "ptg.h"
+#include "ptg_internal.h"
+#include "ptg_kernels.h"
+
+using namespace ptg;
+
+namespace {
+
+int log2_exact(int64_t v)
+{
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int s = 0;
+    while ((int64_t{1} << s) < v) ++s;
+    return s;
+}
+
+}  // namespace
+
+int ptg_fail(ptg_ctx* ctx, int code, const char* fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+int ptg_cuda_fail(ptg_ctx* ctx, cudaError_t e, const char* where)
+{
+    return ptg_fail(ctx, PTG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Argument checks common to every generator.  On success fills *spc_log2.
+int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log2)
+{
+    if (!d) return ptg_fail(ctx, PTG_ERR_INVALID, "descriptor is NULL");
+    if (d->struct_size != sizeof(ptg_field_desc))
+        return ptg_fail(ctx, PTG_ERR_INVALID, "struct_size %u != %zu", d->struct_size, sizeof(ptg_field_desc));
+    if (d->dims != 2 && d->dims != 3) return ptg_fail(ctx, PTG_ERR_INVALID, "dims must be 2 or 3");
+    if (kind != kKindField && d->dims != 2)
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "Perlin and OpenSimplex baselines are 2D");
+    const int s = log2_exact(d->spc);
+    if (d->spc <= 0 || d->spc > (int64_t{1} << 30)) return ptg_fail(ctx, PTG_ERR_INVALID, "spc out of [1, 2^30]");
+    if (s < 0) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "spc (samples per cell) must be a power of two");
+    static const int tile2[3] = {kTile2dX, kTile2dY, 1}, tile3[3] = {kTile3dX, kTile3dY, kTile3dZ};
+    for (int k = 0; k < d->dims; ++k) {
+        if (d->size[k] <= 0 || d->size[k] > (int64_t{1} << 30))
+            return ptg_fail(ctx, PTG_ERR_INVALID, "size[%d] = %lld out of [1, 2^30]", k, (long long)d->size[k]);
+        if (d->offset[k] < 0 || d->offset[k] + d->size[k] > (int64_t{1} << 31))
+            return ptg_fail(ctx, PTG_ERR_INVALID, "offset[%d] must be >= 0 with offset + size <= 2^31", k);
+        const int64_t tile = d->dims == 3 ? tile3[k] : tile2[k];
+        const int64_t align = d->spc < tile ? d->spc : tile;
+        if (d->offset[k] % align)
+            return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "offset[%d] must be a multiple of %lld", k, (long long)align);
+    }
+    if (d->octaves < 1 || d->octaves > kMaxOctaves)
+        return ptg_fail(ctx, PTG_ERR_INVALID, "octaves %d out of [1, 32]", d->octaves);
+    if (kind == kKindField && d->smoothness != PTG_C1 && d->smoothness != PTG_C2)
+        return ptg_fail(ctx, PTG_ERR_INVALID, "smoothness must be PTG_C1 or PTG_C2");
+    if (kind == kKindPerlin && d->variant != PTG_PERLIN_S5 && d->variant != PTG_PERLIN_S3)
+        return ptg_fail(ctx, PTG_ERR_INVALID, "Perlin variant must be PTG_PERLIN_S5 or PTG_PERLIN_S3");
+    if (!std::isfinite(d->persistence) || !std::isfinite(d->grad_weight))
+        return ptg_fail(ctx, PTG_ERR_INVALID, "persistence and grad_weight must be finite");
+    if (!std::isfinite(d->lacunarity)) return ptg_fail(ctx, PTG_ERR_INVALID, "lacunarity must be finite");
+    if (d->lacunarity != 2.0f) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "lacunarity must be 2");
+    if (d->seed >= (1u << 24)) return ptg_fail(ctx, PTG_ERR_INVALID, "seed must be < 2^24");
+    if (d->dtype != PTG_F32 && d->dtype != PTG_F16) return ptg_fail(ctx, PTG_ERR_INVALID, "bad dtype");
+    *spc_log2 = s;
+    return PTG_OK;
+}
+
+// Launch plan of a polynomial / Perlin field (or of a band of one: `band`
+// rows/planes starting at sample `band_start` along the slowest axis).
+int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int s, int64_t band_start,
+                        int64_t band_len, FieldPlan* P)
+{
+    memset(P, 0, sizeof *P);
+    const bool is3d = d->dims == 3;
+    P->out = out;
+    P->W = (int32_t)d->size[0];
+    P->H = (int32_t)d->size[1];
+    P->D = is3d ? (int32_t)d->size[2] : 1;
+    P->jx0 = (int32_t)d->offset[0];
+    P->jy0 = (int32_t)d->offset[1];
+    P->jz0 = is3d ? (int32_t)d->offset[2] : 0;
+    if (is3d) {
+        P->D = (int32_t)band_len;
+        P->jz0 += (int32_t)band_start;
+    } else {
+        P->H = (int32_t)band_len;
+        P->jy0 += (int32_t)band_start;
+    }
+    P->dtype = d->dtype;
+    P->N = d->octaves;
+    const int TW = is3d ? kTile3dX : kTile2dX, TH = is3d ? kTile3dY : kTile2dY, TD = is3d ? kTile3dZ : 1;
+    P->tiles_x = (P->W + TW - 1) / TW;
+    P->tiles_y = (P->H + TH - 1) / TH;
+    P->tiles_z = (P->D + TD - 1) / TD;
+    if (P->tiles_y > 65535 || P->tiles_z > 65535)
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall for one launch (%d x %d tiles along y/z)",
+                        P->tiles_y, P->tiles_z);
+    const int esz = d->dtype == PTG_F16 ? 2 : 4;
+    P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
+    P->nst = d->octaves < s ? d->octaves : s;
+    int coff = 0;
+    double amp = 1.0;
+    const double p = (double)d->persistence, w = (double)d->grad_weight;
+    for (int i = 0; i < d->octaves; ++i) {
+        OctPlan& o = P->oct[i];
+        if (i < s) {
+            const int k = s - i;
+            o.mode = k >= 3 ? kModeRun8 : (k == 2 ? kModeRun4 : kModeRun2);
+            o.k = k;
+            o.ncx = ((TW - 1) >> (k < 31 ? k : 31)) + 2;
+            o.ncy = ((TH - 1) >> (k < 31 ? k : 31)) + 2;
+            o.ncz = is3d ? ((TD - 1) >> (k < 31 ? k : 31)) + 2 : 1;
+            o.coff = coff;
+            coff += o.ncx * o.ncy * o.ncz;
+        } else {
+            o.mode = kModeLattice;
+            o.k = i - s;
+        }
+        o.key = (d->seed << 8) | (uint32_t)i;
+        o.ox = (uint32_t)((uint64_t)d->origin[0] << i);
+        o.oy = (uint32_t)((uint64_t)d->origin[1] << i);
+        o.oz = is3d ? (uint32_t)((uint64_t)d->origin[2] << i) : 0u;
+        o.amp = (float)amp;
+        o.ampw = (float)(amp * w);
+        amp *= p;
+    }
+    P->ncorner = coff;
+    (void)method;
+    const size_t smem = is3d ? fbm3d_smem_bytes(*P) : fbm2d_smem_bytes(*P);
+    if (smem > (size_t)ctx->max_smem)
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "staging needs %zu bytes of shared memory (max %d)", smem,
+                        ctx->max_smem);
+    return PTG_OK;
+}
+
+int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int s, int64_t band_start,
+                          int64_t band_len, SimplexPlan* P)
+{
+    memset(P, 0, sizeof *P);
+    P->out = out;
+    P->W = (int32_t)d->size[0];
+    P->H = (int32_t)band_len;
+    P->dtype = d->dtype;
+    P->N = d->octaves;
+    P->tiles_x = (P->W + kTile2dX - 1) / kTile2dX;
+    P->tiles_y = (P->H + kTile2dY - 1) / kTile2dY;
+    if (P->tiles_y > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall for one launch");
+    const int esz = d->dtype == PTG_F16 ? 2 : 4;
+    P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
+    const double spc = std::ldexp(1.0, s);
+    double lim = 0.0;
+    for (int k = 0; k < 2; ++k) {
+        const double e = std::fabs((double)d->origin[k]) + (double)(d->offset[k] + d->size[k]) / spc;
+        if (e > lim) lim = e;
+    }
+    if (std::ldexp(lim, d->octaves - 1) >= std::ldexp(1.0, 30))
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "OpenSimplex lattice coordinates exceed 2^30");
+    double amp = 1.0;
+    for (int i = 0; i < d->octaves; ++i) {
+        const double scale = std::ldexp(1.0, i);
+        const double step = scale / spc;
+        P->base_x[i] = (double)d->origin[0] * scale + (double)d->offset[0] * step;
+        P->base_y[i] = (double)d->origin[1] * scale + (double)(d->offset[1] + band_start) * step;
+        P->step[i] = (float)step;
+        P->amp[i] = (float)amp;
+        P->key[i] = (d->seed << 8) | (uint32_t)i;
+        amp *= (double)d->persistence;
+    }
+    return PTG_OK;
+}
+
+int ptg_kernel_method(int kind, const ptg_field_desc* d)
+{
+    if (kind == kKindPerlin) return d->variant == PTG_PERLIN_S3 ? kPerlinS3 : kPerlinS5;
+    return d->smoothness == PTG_C2 ? kC2 : kC1;
+}
+
+int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void* out, int64_t band_start,
+                    int64_t band_len, cudaStream_t st)
+{
+    cudaError_t e;
+    if (kind == kKindSimplex) {
+        SimplexPlan P;
+        int rc = ptg_make_simplex_plan(ctx, d, out, s, band_start, band_len, &P);
+        if (rc != PTG_OK) return rc;
+        e = launch_opensimplex2d(P, st);
+    } else {
+        const int method = ptg_kernel_method(kind, d);
+        FieldPlan P;
+        int rc = ptg_make_field_plan(ctx, d, method, out, s, band_start, band_len, &P);
+        if (rc != PTG_OK) return rc;
+        e = d->dims == 3 ? launch_fbm3d(P, method, s, st) : launch_fbm2d(P, method, s, st);
+    }
+    if (e != cudaSuccess) return ptg_cuda_fail(ctx, e, "kernel launch");
+    return PTG_OK;
+}
+
+static int generate(ptg_ctx* ctx, const ptg_field_desc* d, int kind, void* out, void* stream)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+    ctx->err.clear();
+    int s = 0;
+    int rc = ptg_check_desc(ctx, d, kind, &s);
+    if (rc != PTG_OK) return rc;
+    if (!out) return ptg_fail(ctx, PTG_ERR_INVALID, "out is NULL");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return ptg_fail(ctx, PTG_ERR_CUDA, "cudaSetDevice(%d) failed", ctx->device);
+    cudaError_t pending = cudaGetLastError();
+    if (pending != cudaSuccess) return ptg_cuda_fail(ctx, pending, "earlier asynchronous error");
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    const int64_t slow = d->dims == 3 ? d->size[2] : d->size[1];
+    return ptg_launch_plan(ctx, kind, d, s, out, 0, slow, st);
+}
+
+static ptg_field_desc short_desc(int dims, const int64_t* size, int32_t octaves, int32_t smoothness, float p,
+                                 float lac, uint32_t seed)
+{
+    ptg_field_desc d;
+    memset(&d, 0, sizeof d);
+    d.struct_size = sizeof d;
+    d.dims = dims;
+    for (int k = 0; k < 3; ++k) d.size[k] = k < dims ? size[k] : 1;
+    d.spc = 64;
+    d.octaves = octaves;
+    d.smoothness = smoothness;
+    d.persistence = p;
+    d.lacunarity = lac;
+    d.grad_weight = 1.0f;
+    d.seed = seed;
+    d.dtype = PTG_F32;
+    return d;
+}
+
+extern "C" {
+
+int ptg_create(ptg_ctx** out, int device, uint64_t hbm_budget_bytes)
+{
+    if (!out) return PTG_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return PTG_ERR_CUDA;
+    if (device < 0 || device >= ndev) return PTG_ERR_INVALID;
+    ptg_ctx* ctx = new (std::nothrow) ptg_ctx();
+    if (!ctx) return PTG_ERR_NOMEM;
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (uint64_t{40} << 30);
+    DeviceGuard g(device);
+    if (!g.ok) {
+        delete ctx;
+        return PTG_ERR_CUDA;
+    }
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    ctx->num_sms = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    ctx->max_smem = v;
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return PTG_ERR_CUDA;
+    }
+    *out = ctx;
+    return PTG_OK;
+}
+
+int ptg_destroy(ptg_ctx* ctx)
+{
+    if (!ctx) return PTG_OK;
+    DeviceGuard g(ctx->device);
+    ptg_serve_shutdown(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    ptg_host_release(ctx);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return PTG_OK;
+}
+
+const char* ptg_last_error(ptg_ctx* ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
+
+int ptg_field(ptg_ctx* ctx, const ptg_field_desc* d, void* out, void* stream)
+{
+    return generate(ctx, d, kKindField, out, stream);
+}
+
+int ptg_perlin(ptg_ctx* ctx, const ptg_field_desc* d, void* out, void* stream)
+{
+    return generate(ctx, d, kKindPerlin, out, stream);
+}
+
+int ptg_opensimplex(ptg_ctx* ctx, const ptg_field_desc* d, void* out, void* stream)
+{
+    return generate(ctx, d, kKindSimplex, out, stream);
+}
+
+int ptg_heightmap2d(ptg_ctx* ctx, const int64_t size[2], int32_t octaves, int32_t smoothness, float persistence,
+                    float lacunarity, uint32_t seed, void* out, void* stream)
+{
+    if (!size) return ptg_fail(ctx, PTG_ERR_INVALID, "size is NULL");
+    ptg_field_desc d = short_desc(2, size, octaves, smoothness, persistence, lacunarity, seed);
+    return generate(ctx, &d, kKindField, out, stream);
+}
+
+int ptg_volume3d(ptg_ctx* ctx, const int64_t size[3], int32_t octaves, int32_t smoothness, float persistence,
+                 float lacunarity, uint32_t seed, void* out, void* stream)
+{
+    if (!size) return ptg_fail(ctx, PTG_ERR_INVALID, "size is NULL");
+    ptg_field_desc d = short_desc(3, size, octaves, smoothness, persistence, lacunarity, seed);
+    return generate(ctx, &d, kKindField, out, stream);
+}
+
+int ptg_validate(const ptg_field_desc* d, int32_t method, char* msg, int32_t msg_len)
+{
+    if (msg && msg_len > 0) msg[0] = 0;
+    if (method < 0 || method > 2) return PTG_ERR_INVALID;
+    const int kind = method == 0 ? kKindField : (method == 1 ? kKindPerlin : kKindSimplex);
+    ptg_ctx scratch;  // host-only: collects the message, no device state
+    scratch.max_smem = 227 * 1024;
+    int s = 0;
+    int rc = ptg_check_desc(&scratch, d, kind, &s);
+    if (rc == PTG_OK) {
+        const int64_t slow = d->dims == 3 ? d->size[2] : d->size[1];
+        if (kind == kKindSimplex) {
+            SimplexPlan P;
+            rc = ptg_make_simplex_plan(&scratch, d, nullptr, s, 0, slow, &P);
+        } else {
+            FieldPlan P;
+            rc = ptg_make_field_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, s, 0, slow, &P);
+        }
+    }
+    if (msg && msg_len > 0) {
+        strncpy(msg, scratch.err.c_str(), (size_t)msg_len - 1);
+        msg[msg_len - 1] = 0;
+    }
+    return rc;
+}
+
+int ptg_debug_hash(ptg_ctx* ctx, int32_t dims, const uint32_t* keys, int64_t n, uint32_t* out, void* stream)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+    if ((dims != 2 && dims != 3) || n < 0 || (n > 0 && (!keys || !out)))
+        return ptg_fail(ctx, PTG_ERR_INVALID, "bad debug_hash arguments");
+    if (n == 0) return PTG_OK;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_debug_hash(dims, keys, n, out, stream ? (cudaStream_t)stream : ctx->stream);
+    return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "debug_hash");
+}
+
+int ptg_debug_axis(ptg_ctx* ctx, int64_t origin, int64_t spc, int32_t octave, const int64_t* j, int64_t n,
+                   uint32_t* cell, float* t, void* stream)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+    const int s = log2_exact(spc);
+    if (s < 0) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "spc must be a power of two");
+    if (octave < 0 || octave >= kMaxOctaves || n < 0 || (n > 0 && (!j || !cell || !t)))
+        return ptg_fail(ctx, PTG_ERR_INVALID, "bad debug_axis arguments");
+    if (n == 0) return PTG_OK;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_debug_axis((long long)origin, s, octave, (const long long*)j, (long long)n, cell, t,
+                                      stream ? (cudaStream_t)stream : ctx->stream);
+    return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "debug_axis");
+}
+
+}  // extern "C"

@@ -1,0 +1,170 @@
+// ptg_device.cuh -- device building blocks shared by the generator kernels:
+// the corner hash, the hash-word -> [-1, 1) map, the per-axis polynomial
+// bases of each method, and the launch plan that the host fills per field.
+//
+// Method: Thorimbert & Chopard, arXiv:1610.03525.
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+
+namespace ptg {
+
+// Method codes of the generator kernels.
+enum : int {
+    kC1 = 1,        // D?M1N3, zero twist: tensor cubic Hermite (Sec. 3.1, 3.4)
+    kC2 = 2,        // D?M2N5, zero 2nd derivatives: tensor quintic Hermite (Sec. 3.4)
+    kPerlinS5 = 10, // Perlin's polynomial, smootherstep blend (Sec. 3.2, 5.1)
+    kPerlinS3 = 11  // Perlin's polynomial, smoothstep blend (Sec. 3.2)
+};
+
+// Octave modes.  A staged octave (cells at least two samples wide) keeps the
+// corner data of the CTA tile's cells in shared memory; the number names how
+// many samples of a thread's run share one cell along x.  A lattice octave
+// (cells one sample wide or narrower) puts every sample on a lattice point,
+// where the cell polynomial equals the corner value (Eq. mixedderiv, d = 0).
+enum : int { kModeLattice = 0, kModeRun2 = 2, kModeRun4 = 4, kModeRun8 = 8 };
+
+constexpr int kMaxOctaves = 32;
+
+// Per-octave launch plan (host-filled).
+struct OctPlan {
+    int32_t mode;           // kMode*
+    int32_t k;              // staged: log2(samples per cell); lattice: i - log2(spc)
+    int32_t ncx, ncy, ncz;  // staged corner grid of one CTA tile
+    int32_t coff;           // staged: first corner (float4 units) in shared memory
+    uint32_t key;           // hash word: seed << 8 | octave
+    uint32_t ox, oy, oz;    // origin * 2^i (mod 2^32)
+    float amp;              // persistence^i
+    float ampw;             // persistence^i * grad_weight
+    int32_t pad;
+};
+
+// One field (2D or 3D) as the kernels see it.
+struct FieldPlan {
+    void* out;
+    int32_t W, H, D;        // samples along x, y, z (D = 1 in 2D)
+    int32_t dtype;          // 0 = FP32, 1 = FP16
+    int32_t N;              // octaves
+    int32_t nst;            // staged octaves = min(N, log2 spc); they are 0 .. nst-1
+    int32_t ncorner;        // staged corners of one tile, all octaves
+    int32_t vec_ok;         // 16-byte vector stores allowed (alignment, row length)
+    int32_t tiles_x, tiles_y, tiles_z;
+    int32_t jx0, jy0, jz0;  // sample index of output element 0 (bands of a larger field)
+    OctPlan oct[kMaxOctaves];
+};
+
+// ---------------------------------------------------------------------------
+// Hash: pcg3d and pcg4d of Jarzynski & Olano ("Hash Functions for GPU
+// Rendering", JCGT 9(3), 2020): an LCG step per word, cross-word multiply-adds,
+// a 16-bit xorshift, and a second round of cross-word multiply-adds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pcg3d(uint32_t& x, uint32_t& y, uint32_t& z)
+{
+    x = x * 1664525u + 1013904223u;
+    y = y * 1664525u + 1013904223u;
+    z = z * 1664525u + 1013904223u;
+    x += y * z;
+    y += z * x;
+    z += x * y;
+    x ^= x >> 16;
+    y ^= y >> 16;
+    z ^= z >> 16;
+    x += y * z;
+    y += z * x;
+    z += x * y;
+}
+
+// Word 0 of pcg3d only (the corner value); the compiler drops the rest.
+__device__ __forceinline__ uint32_t pcg3d_value(uint32_t x, uint32_t y, uint32_t z)
+{
+    pcg3d(x, y, z);
+    return x;
+}
+
+__device__ __forceinline__ void pcg4d(uint32_t& x, uint32_t& y, uint32_t& z, uint32_t& w)
+{
+    x = x * 1664525u + 1013904223u;
+    y = y * 1664525u + 1013904223u;
+    z = z * 1664525u + 1013904223u;
+    w = w * 1664525u + 1013904223u;
+    x += y * w;
+    y += z * x;
+    z += x * y;
+    w += y * z;
+    x ^= x >> 16;
+    y ^= y >> 16;
+    z ^= z >> 16;
+    w ^= w >> 16;
+    x += y * w;
+    y += z * x;
+    z += x * y;
+    w += y * z;
+}
+
+__device__ __forceinline__ uint32_t pcg4d_value(uint32_t x, uint32_t y, uint32_t z, uint32_t w)
+{
+    pcg4d(x, y, z, w);
+    return x;
+}
+
+// Hash word -> (u >> 9) 2^-22 - 1, exactly: the float with exponent of 2 and
+// the top 23 bits of u as mantissa lies in [2, 4); subtracting 3 is exact.
+__device__ __forceinline__ float unit_value(uint32_t u)
+{
+    return __uint_as_float(0x40000000u | (u >> 9)) - 3.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Per-axis bases.  Every method's octave term is, inside a cell,
+//   sum over corners of  V * A_a(x) A_b(y) [A_c(z)]  plus gradient terms,
+// with A_0 = 1 - S, A_1 = S (value blend) and two "slope" functions B0, B1
+// that carry the corner gradients.  Returned as (S, B0, B1, 0).
+//   C1: cubic Hermite:   S = 3t^2 - 2t^3, B0 = t (1-t)^2, B1 = t^2 (t-1)
+//   C2: quintic Hermite: S = 6t^5 - 15t^4 + 10t^3,
+//       B0 = t (1-t)^3 (1+3t), B1 = t^3 (t-1) (4-3t)
+//   Perlin (Sec. 3.2): v_ab = f (x-a) + g (y-b) blended by S, so along x the
+//       gradient f_0b multiplies (1-S) x and f_1b multiplies S (x-1):
+//       B0 = (1-S) t, B1 = S (t-1); the corner value is zero.
+// ---------------------------------------------------------------------------
+template <int METHOD>
+__device__ __forceinline__ float4 axis_basis(float t)
+{
+    const float t2 = t * t;
+    const float u = t - 1.0f;
+    if (METHOD == kC1) {
+        const float S = t2 * fmaf(-2.0f, t, 3.0f);
+        return make_float4(S, t * u * u, t2 * u, 0.0f);
+    } else if (METHOD == kC2) {
+        const float t3 = t2 * t;
+        const float S = t3 * fmaf(t, fmaf(6.0f, t, -15.0f), 10.0f);
+        const float B0 = t * (u * u) * (-u) * fmaf(3.0f, t, 1.0f);
+        const float B1 = t3 * u * fmaf(-3.0f, t, 4.0f);
+        return make_float4(S, B0, B1, 0.0f);
+    } else {
+        const float S = (METHOD == kPerlinS5) ? t2 * t * fmaf(t, fmaf(6.0f, t, -15.0f), 10.0f)
+                                              : t2 * fmaf(-2.0f, t, 3.0f);
+        return make_float4(S, (1.0f - S) * t, S * u, 0.0f);
+    }
+}
+
+// Fixed-point sample -> lattice map of one axis at octave i (Sec. 2.1, Sec. 4):
+// sample j lies at (origin + j / spc) 2^i, spc = 2^s.  Cell and position t.
+__device__ __forceinline__ uint32_t axis_cell(uint32_t origin_shifted, uint32_t j, int i, int s)
+{
+    return (i < s) ? origin_shifted + (j >> (s - i)) : origin_shifted + (j << (i - s));
+}
+
+__device__ __forceinline__ float axis_t(uint32_t j, int i, int s)
+{
+    if (i >= s) return 0.0f;
+    const int k = s - i;
+    const uint32_t r = j & ((1u << k) - 1u);
+    return (float)r * __uint_as_float((uint32_t)(127 - k) << 23);  // r * 2^-k, exact
+}
+
+// Output stores.
+__device__ __forceinline__ void store1(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store1(__half* p, float v) { *p = __float2half_rn(v); }
+
+}  // namespace ptg

@@ -1,0 +1,64 @@
+// ptg_internal.h -- host-side state behind the C ABI (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "ptg.h"
+#include "ptg_device.cuh"
+#include "ptg_kernels.h"
+
+// Generator kinds behind the ABI calls.
+enum { kKindField = 0, kKindPerlin = 1, kKindSimplex = 2 };
+
+struct PtgServer;
+
+// Makes a device current for the duration of a call, then restores the
+// caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct ptg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;  // default stream of the context
+    uint64_t budget = 0;            // request-loop HBM budget (bytes)
+    std::string err;
+    int num_sms = 0;
+    int max_smem = 0;
+    // banded host-output path
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_gen[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copy[2] = {nullptr, nullptr};
+    // request loop
+    PtgServer* server = nullptr;
+};
+
+int ptg_fail(ptg_ctx* ctx, int code, const char* fmt, ...);
+int ptg_cuda_fail(ptg_ctx* ctx, cudaError_t e, const char* where);
+int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log2);
+int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int s, int64_t band_start,
+                        int64_t band_len, ptg::FieldPlan* P);
+int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int s, int64_t band_start,
+                          int64_t band_len, ptg::SimplexPlan* P);
+int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void* out, int64_t band_start,
+                    int64_t band_len, cudaStream_t st);
+int ptg_kernel_method(int kind, const ptg_field_desc* d);
+
+void ptg_host_release(ptg_ctx* ctx);
+void ptg_serve_shutdown(ptg_ctx* ctx);

@@ -1,0 +1,38 @@
+// ptg_kernels.h -- internal launch entry points of the generator kernels
+// (host side of the CUDA translation units; not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ptg_device.cuh"
+
+namespace ptg {
+
+// Tile shapes (samples) of the fused generators.
+constexpr int kTile2dX = 64, kTile2dY = 64;
+constexpr int kTile3dX = 32, kTile3dY = 16, kTile3dZ = 8;
+
+size_t fbm2d_smem_bytes(const FieldPlan& P);
+cudaError_t launch_fbm2d(const FieldPlan& P, int method, int s, cudaStream_t stream);
+
+size_t fbm3d_smem_bytes(const FieldPlan& P);
+cudaError_t launch_fbm3d(const FieldPlan& P, int method, int s, cudaStream_t stream);
+
+// OpenSimplex-style baseline (2D).  base[i] = (x0, y0) of sample (0, 0) at
+// octave i in lattice units (FP64, computed on the host); step[i] = 2^i / spc.
+struct SimplexPlan {
+    void* out;
+    int32_t W, H, dtype, N, vec_ok, tiles_x, tiles_y;
+    double base_x[kMaxOctaves], base_y[kMaxOctaves];
+    float step[kMaxOctaves];
+    float amp[kMaxOctaves];
+    uint32_t key[kMaxOctaves];
+};
+cudaError_t launch_opensimplex2d(const SimplexPlan& P, cudaStream_t stream);
+
+// Test hooks.
+cudaError_t launch_debug_hash(int dims, const uint32_t* keys, long long n, uint32_t* out, cudaStream_t stream);
+cudaError_t launch_debug_axis(long long origin, int s, int octave, const long long* j, long long n,
+                              uint32_t* cell, float* t, cudaStream_t stream);
+
+}  // namespace ptg

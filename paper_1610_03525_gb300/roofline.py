@@ -1,0 +1,89 @@
+"""Algorithmic work of one generator launch, for the ALU roofline.
+
+The generators are bound by FP32/INT32 issue on the CUDA cores (no dense
+contraction, and the only DRAM traffic is one output write per sample).  The
+work unit is a lane operation (one FP32 or INT32 arithmetic/logic operation of
+one thread).  The counts below follow the kernels' dataflow, counted from
+their formulas (never from compiled code); loads, stores, address arithmetic,
+loop control and barriers are overhead and are NOT counted, so the achieved
+fraction of the issue peak measures how little overhead and stall the kernels
+add on top of the arithmetic they must do.
+
+Per 2D tile of 64 x 64 samples (128 threads x 4 rows x 8 columns):
+  basis tables: 128 entries per staged octave x (5 coordinate + basis ops:
+                C1 7, C2 14, Perlin-S5 9, Perlin-S3 8);
+  corners:      per staged corner 35 (pcg3d 15, three word->float maps 9,
+                three amplitude scalings 3, grid index 8);
+  staged octave per thread, cells of CW x RH samples of the thread's run:
+                per cell 4 (y differences) + RH rows x 9 (row reduction), plus
+                4 per sample (1 add + 3 FMA);
+  lattice octave: per sample 19 (pcg3d word 0: 13, word->float 3, FMA 1,
+                coordinate 2); Perlin's lattice octaves are zero, no work.
+3D tiles of 32 x 16 x 8: per cell additionally 32 (z reduction of the four
+corner columns); corners 48 (pcg4d 20); lattice samples 23.
+OpenSimplex-style: per sample and octave 150 (4 vertices x 33 + 18).
+"""
+from __future__ import annotations
+
+BASIS_OPS = {"c1": 7, "c2": 14, "perlin_s5": 9, "perlin_s3": 8}
+COORD_OPS = 5
+
+
+def _staged(spc: int, octaves: int):
+    """(octave index, samples per cell) of the staged octaves."""
+    s = spc.bit_length() - 1
+    return [(i, spc >> i) for i in range(min(octaves, s))]
+
+
+def lane_ops_2d(kind: str, size, spc: int, octaves: int) -> dict:
+    w, h = size
+    tiles = ((w + 63) // 64) * ((h + 63) // 64)
+    threads = tiles * 128
+    samples_padded = tiles * 64 * 64
+    if kind == "opensimplex":
+        tot = 150 * samples_padded * octaves
+        return dict(total=float(tot), per_sample=tot / (w * h))
+    st = _staged(spc, octaves)
+    lut = tiles * len(st) * 128 * (COORD_OPS + BASIS_OPS[kind])
+    corners = 0
+    evalops = 0
+    for i, spci in st:
+        k = spci.bit_length() - 1
+        ncx = (63 >> min(k, 31)) + 2
+        corners += tiles * ncx * ncx * 35
+        cw, rh = min(8, spci), min(4, spci)
+        cells = (8 // cw) * (4 // rh)
+        evalops += threads * (cells * (4 + rh * 9) + 32 * 4)
+    n_lattice = octaves - len(st)
+    lattice = 0 if kind.startswith("perlin") else samples_padded * n_lattice * 19
+    tot = lut + corners + evalops + lattice
+    return dict(total=float(tot), per_sample=tot / (w * h), lut=lut, corners=corners, eval=evalops,
+                lattice=lattice)
+
+
+def lane_ops_3d(kind: str, size, spc: int, octaves: int) -> dict:
+    w, h, d = size
+    tiles = ((w + 31) // 32) * ((h + 15) // 16) * ((d + 7) // 8)
+    threads = tiles * 128
+    samples_padded = tiles * 32 * 16 * 8
+    st = _staged(spc, octaves)
+    lut = tiles * len(st) * 56 * (COORD_OPS + BASIS_OPS[kind])
+    corners = 0
+    evalops = 0
+    for i, spci in st:
+        k = spci.bit_length() - 1
+        nc = ((31 >> min(k, 31)) + 2) * ((15 >> min(k, 31)) + 2) * ((7 >> min(k, 31)) + 2)
+        corners += tiles * nc * 48
+        cw, rh = min(8, spci), min(4, spci)
+        cells = (8 // cw) * (4 // rh)
+        evalops += threads * (cells * (32 + 4 + rh * 9) + 32 * 4)
+    lattice = samples_padded * (octaves - len(st)) * 23
+    tot = lut + corners + evalops + lattice
+    return dict(total=float(tot), per_sample=tot / (w * h * d), lut=lut, corners=corners, eval=evalops,
+                lattice=lattice)
+
+
+def alu_peak(num_sms: int, clock_mhz: float, lanes_per_sm: int = 128) -> float:
+    """Issue peak in lane operations per second: SMs x 128 FP32/INT32 lanes
+    x clock (one warp instruction per cycle on each of four SM partitions)."""
+    return num_sms * lanes_per_sm * clock_mhz * 1e6

@@ -1,0 +1,89 @@
+"""C-ABI boundary checks that need no GPU: the library loads, exports every
+function include/ptg.h declares, and its host-side argument validation returns
+the documented status codes without touching a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ptg.h")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1610_03525_gb300 import build
+    build.build()
+    import paper_1610_03525_gb300 as P
+    return P
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(ptg_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_expected_calls():
+    names = _declared_functions()
+    for want in ["ptg_create", "ptg_destroy", "ptg_heightmap2d", "ptg_volume3d", "ptg_field", "ptg_perlin",
+                 "ptg_opensimplex", "ptg_submit", "ptg_poll", "ptg_wait", "ptg_last_error", "ptg_batch"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(P):
+    L = ctypes.CDLL(P.LIB_PATH)
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+    # the binding wraps each declared call under the same name
+    for name in _declared_functions():
+        assert hasattr(P, name), name
+
+
+def test_desc_layout_matches_header(P):
+    # struct_size check in the library rejects a mismatched layout
+    d = P.make_desc()
+    assert d.struct_size == ctypes.sizeof(P.ptg_field_desc) == 120
+
+
+@pytest.mark.parametrize("kw,method,code", [
+    (dict(), 0, 0),
+    (dict(size=(0, 5)), 0, -1),
+    (dict(size=(5, 5), spc=0), 0, -1),
+    (dict(size=(5, 5), spc=3), 0, -2),
+    (dict(octaves=0), 0, -1),
+    (dict(octaves=33), 0, -1),
+    (dict(smoothness=3), 0, -1),
+    (dict(lacunarity=3.0), 0, -2),
+    (dict(seed=1 << 24), 0, -1),
+    (dict(dtype=7), 0, -1),
+    (dict(dims=4), 0, -1),
+    (dict(dims=3, size=(32, 32, 32)), 1, -2),
+    (dict(variant=5), 1, -1),
+    (dict(offset=(32, 0, 0)), 0, -2),
+    (dict(offset=(128, 64, 0)), 0, 0),
+    (dict(offset=(-64, 0, 0)), 0, -1),
+    (dict(persistence=float("nan")), 0, -1),
+    (dict(origin=(1 << 40, 0, 0), octaves=12, spc=1024), 2, -2),
+    (dict(size=(1, 1), spc=1, octaves=32), 0, 0),
+])
+def test_validation_codes(P, kw, method, code):
+    d = P.make_desc(**kw)
+    rc, msg = P.ptg_validate(d, method)
+    assert rc == code, msg
+    assert (msg == "") == (code == 0)
+
+
+def test_struct_size_checked(P):
+    d = P.make_desc()
+    d.struct_size = 64
+    assert P.ptg_validate(d)[0] == -1
+
+
+def test_create_without_gpu_fails_cleanly(P):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(P.PtgError):
+        P.ptg_create(0)

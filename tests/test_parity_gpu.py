@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars (Thorimbert & Chopard, arXiv:1610.03525; fractal sum of Sec. 4):
+  - lattice hashes and cell indices: bit-exact;
+  - FP32 heights: max |gpu - oracle| <= 2e-6 * A_tot, A_tot = sum_i p^i;
+  - FP16 output: the FP32 bound plus half an FP16 ulp of the value;
+  - on-lattice octaves (cells one sample wide) are exact corner values.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+import paper_1610_03525_gb300 as P  # noqa: E402
+from paper_1610_03525_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+KIND_ORACLE = {"c1": O.C1, "c2": O.C2, "perlin_s5": O.PERLIN_S5, "perlin_s3": O.PERLIN_S3,
+               "opensimplex": O.OPENSIMPLEX}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_03525_gb300 import build
+    build.build()
+    c = P.ptg_create(0)
+    yield c
+    c.close()
+
+
+def gpu_field(ctx, kind, dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 0, 0), offset=(0, 0, 0),
+              seed=0, persistence=0.5, grad_weight=1.0, dtype=P.PTG_F32):
+    smooth = P.PTG_C2 if kind == "c2" else P.PTG_C1
+    variant = P.PTG_PERLIN_S3 if kind == "perlin_s3" else P.PTG_PERLIN_S5
+    d = P.make_desc(dims=dims, size=size, spc=spc, origin=origin, offset=offset, octaves=octaves,
+                    smoothness=smooth, persistence=persistence, grad_weight=grad_weight, seed=seed, dtype=dtype,
+                    variant=variant)
+    shape = tuple(reversed(size[:dims]))
+    out = torch.full(shape, float("nan"), dtype=torch.float16 if dtype == P.PTG_F16 else torch.float32,
+                     device="cuda")
+    if kind in ("c1", "c2"):
+        P.ptg_field(ctx, d, out)
+    elif kind.startswith("perlin"):
+        P.ptg_perlin(ctx, d, out)
+    else:
+        P.ptg_opensimplex(ctx, d, out)
+    torch.cuda.synchronize()
+    return out
+
+
+def oracle_at(kind, idx, dims=2, spc=64, octaves=6, origin=(0, 0, 0), offset=(0, 0, 0), seed=0,
+              persistence=0.5, grad_weight=1.0):
+    """Oracle values at sample indices idx (n, dims) of the window."""
+    idx = np.asarray(idx, np.int64) + np.asarray(offset[:dims], np.int64)[None, :]
+    size = (spc,) * dims
+    cells = (1,) * dims
+    return O.field_samples(dims, size, cells, idx, octaves=octaves, method=KIND_ORACLE[kind],
+                           persistence=persistence, grad_weight=grad_weight, seed=seed, origin=origin)
+
+
+def tol32(octaves, persistence=0.5):
+    return 2e-6 * W.total_amplitude(octaves, abs(persistence))
+
+
+def half_ulp16(x):
+    a = np.maximum(np.abs(x), 2.0 ** -14)
+    return 0.5 * 2.0 ** (np.floor(np.log2(a)) - 10)
+
+
+def gather(out, idx):
+    a = out.float().cpu().numpy()
+    if idx.shape[1] == 2:
+        return a[idx[:, 1], idx[:, 0]].astype(np.float64)
+    return a[idx[:, 2], idx[:, 1], idx[:, 0]].astype(np.float64)
+
+
+# ---------------------------------------------------------------------------
+# bit-exact hash and coordinates
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dims", [2, 3])
+def test_hash_bit_exact(ctx, dims):
+    n = 1 << 24
+    rng = np.random.default_rng(7 + dims)
+    keys = rng.integers(0, 2**32, size=(n, dims + 1), dtype=np.uint64).astype(np.uint32)
+    m = 1 << 16                                      # structured keys: lattice runs, wrap, octave words
+    keys[:m, 0] = np.arange(m, dtype=np.uint32) - np.uint32(m // 2)
+    keys[:m, 1] = np.uint32(0xFFFFFFF0)
+    keys[:m, dims] = (np.arange(m, dtype=np.uint32) % 24) | (np.uint32(5) << 8)
+    kd = torch.from_numpy(keys.view(np.int32)).cuda()
+    od = torch.empty_like(kd)
+    P.ptg_debug_hash(ctx, dims, kd, od)
+    torch.cuda.synchronize()
+    got = od.cpu().numpy().view(np.uint32)
+    want = O.hash_batch(dims, keys)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("spc", [1, 2, 64, 1024])
+def test_axis_bit_exact(ctx, spc):
+    rng = np.random.default_rng(spc)
+    j = np.concatenate([np.arange(4096), rng.integers(0, 1 << 30, 1 << 16)]).astype(np.int64)
+    jd = torch.from_numpy(j).cuda()
+    cell = torch.empty(j.size, dtype=torch.int32, device="cuda")
+    t = torch.empty(j.size, dtype=torch.float32, device="cuda")
+    for origin in (0, -5, 1 << 20, -(1 << 31) + 7):
+        for octave in (0, 1, 5, 10, 11, 20, 31):
+            P.ptg_debug_axis(ctx, origin, spc, octave, jd, cell, t)
+            torch.cuda.synchronize()
+            oc, ot = O.axis(origin, spc, j, octave)
+            assert np.array_equal(cell.cpu().numpy().view(np.uint32), oc)
+            assert np.array_equal(t.cpu().numpy().astype(np.float64), ot)
+
+
+def test_lattice_octaves_are_exact_corner_values(ctx):
+    """spc = 1: every octave samples lattice points; heights are sums of
+    exactly representable corner values times powers of two."""
+    for dims, size in [(2, (300, 70)), (3, (40, 24, 9))]:
+        for octaves in (1, 3):
+            out = gpu_field(ctx, "c1", dims=dims, size=size, spc=1, octaves=octaves, origin=(-3, 1 << 20, 7),
+                            seed=99)
+            idx = W.grid_indices_2d(*size) if dims == 2 else W.grid_indices_3d(*size)
+            ref = oracle_at("c1", idx, dims=dims, spc=1, octaves=octaves, origin=(-3, 1 << 20, 7), seed=99)
+            assert np.array_equal(gather(out, idx), ref)
+
+
+# ---------------------------------------------------------------------------
+# full-field parity, 256^2 6-octave configuration and every method
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3", "opensimplex"])
+def test_cfg1_full_field(ctx, kind):
+    cfg = W.CONFIGS["cfg1_2d_256_c1_n6"]
+    out = gpu_field(ctx, kind, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"], seed=0)
+    idx = W.grid_indices_2d(*cfg["size"])
+    ref = oracle_at(kind, idx, spc=cfg["spc"], octaves=cfg["octaves"], seed=0)
+    err = np.abs(gather(out, idx) - ref).max()
+    assert err <= tol32(cfg["octaves"]), err
+
+
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "opensimplex"])
+def test_cfg1_fp16_output(ctx, kind):
+    out = gpu_field(ctx, kind, size=(256, 256), spc=64, octaves=6, seed=0, dtype=P.PTG_F16)
+    idx = W.grid_indices_2d(256, 256)
+    ref = oracle_at(kind, idx, spc=64, octaves=6, seed=0)
+    err = np.abs(gather(out, idx) - ref)
+    assert np.all(err <= tol32(6) + half_ulp16(ref))
+
+
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "opensimplex"])
+@pytest.mark.parametrize("size,spc,octaves", [
+    ((1, 1), 1, 1), ((3, 5), 1, 4), ((17, 13), 2, 3), ((200, 136), 8, 7), ((65, 130), 32, 9),
+    ((64, 64), 64, 1), ((129, 3), 4, 32),
+])
+def test_ragged_and_tiny(ctx, kind, size, spc, octaves):
+    if kind == "opensimplex" and octaves > 20:
+        octaves = 20
+    origin = (-(1 << 20) + 3, 12345, 0)
+    if kind == "opensimplex":
+        origin = (-3, 5, 0)
+    out = gpu_field(ctx, kind, size=size, spc=spc, octaves=octaves, origin=origin, seed=17, persistence=0.6,
+                    grad_weight=0.75)
+    idx = W.grid_indices_2d(*size)
+    ref = oracle_at(kind, idx, spc=spc, octaves=octaves, origin=origin, seed=17, persistence=0.6,
+                    grad_weight=0.75)
+    err = np.abs(gather(out, idx) - ref).max()
+    assert err <= tol32(octaves, 0.6), err
+
+
+@pytest.mark.parametrize("kind", ["c1", "c2"])
+@pytest.mark.parametrize("dtype", [P.PTG_F32, P.PTG_F16])
+def test_3d_world_offset(ctx, kind, dtype):
+    size, spc, N, origin = (48, 40, 24), 8, 6, (1 << 20, 1 << 20, 0)
+    out = gpu_field(ctx, kind, dims=3, size=size, spc=spc, octaves=N, origin=origin, seed=5, dtype=dtype)
+    idx = W.grid_indices_3d(*size)
+    ref = oracle_at(kind, idx, dims=3, spc=spc, octaves=N, origin=origin, seed=5)
+    err = np.abs(gather(out, idx) - ref)
+    bound = tol32(N) + (half_ulp16(ref) if dtype == P.PTG_F16 else 0.0)
+    assert np.all(err <= bound), err.max()
+
+
+def test_3d_ragged(ctx):
+    size, spc, N = (37, 19, 11), 4, 5
+    for kind in ("c1", "c2"):
+        out = gpu_field(ctx, kind, dims=3, size=size, spc=spc, octaves=N, origin=(-7, 3, -(1 << 30)), seed=2)
+        idx = W.grid_indices_3d(*size)
+        ref = oracle_at(kind, idx, dims=3, spc=spc, octaves=N, origin=(-7, 3, -(1 << 30)), seed=2)
+        assert np.abs(gather(out, idx) - ref).max() <= tol32(N)
+
+
+# ---------------------------------------------------------------------------
+# full-size configurations in the benchmark's launch configuration, sampled
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,seed,dtype", [("c1", 0, P.PTG_F32), ("c2", 3, P.PTG_F32), ("c1", 1, P.PTG_F16),
+                                             ("perlin_s5", 2, P.PTG_F32), ("opensimplex", 0, P.PTG_F32)])
+def test_cfg2_sampled(ctx, kind, seed, dtype):
+    cfg = W.CONFIGS["cfg2_2d_8192_n12"]
+    out = gpu_field(ctx, kind, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"], seed=seed, dtype=dtype)
+    idx = W.subsample(cfg["size"], every=1024, n_random=1 << 15, seed=seed)
+    ref = oracle_at(kind, idx, spc=cfg["spc"], octaves=cfg["octaves"], seed=seed)
+    err = np.abs(gather(out, idx) - ref)
+    bound = tol32(cfg["octaves"]) + (half_ulp16(ref) if dtype == P.PTG_F16 else 0.0)
+    assert np.all(err <= bound), err.max()
+    # range bound |H| <= (1 + D w beta) A_tot holds on the whole field
+    if kind == "c1":
+        assert float(out.float().abs().max()) <= 1.5 * W.total_amplitude(12) + 1e-5
+
+
+def test_cfg3_sampled(ctx):
+    cfg = W.CONFIGS["cfg3_3d_512_n8"]
+    out = gpu_field(ctx, "c1", dims=3, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"],
+                    origin=cfg["origin"], seed=0, dtype=P.PTG_F16)
+    idx = W.subsample(cfg["size"], every=256, n_random=1 << 15, seed=1)
+    ref = oracle_at("c1", idx, dims=3, spc=cfg["spc"], octaves=cfg["octaves"], origin=cfg["origin"], seed=0)
+    err = np.abs(gather(out, idx) - ref)
+    assert np.all(err <= tol32(cfg["octaves"]) + half_ulp16(ref)), err.max()
+
+
+# ---------------------------------------------------------------------------
+# locality (Sec. 1): windows tile the world exactly; determinism; host path
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5"])
+def test_chunk_mosaic_bit_exact(ctx, kind):
+    big = gpu_field(ctx, kind, size=(512, 384), spc=128, octaves=9, origin=(11, -4, 0), seed=8)
+    for oy in (0, 192):
+        for ox in (0, 256):
+            part = gpu_field(ctx, kind, size=(256, 192), spc=128, octaves=9, origin=(11, -4, 0),
+                             offset=(ox, oy, 0), seed=8)
+            assert torch.equal(part, big[oy:oy + 192, ox:ox + 256])
+
+
+def test_3d_chunk_mosaic_bit_exact(ctx):
+    big = gpu_field(ctx, "c1", dims=3, size=(64, 32, 16), spc=16, octaves=7, seed=4)
+    part = gpu_field(ctx, "c1", dims=3, size=(32, 16, 8), spc=16, octaves=7, offset=(32, 16, 8), seed=4)
+    assert torch.equal(part, big[8:16, 16:32, 32:64])
+
+
+def test_deterministic(ctx):
+    a = gpu_field(ctx, "c2", size=(1024, 512), spc=256, octaves=10, seed=3)
+    b = gpu_field(ctx, "c2", size=(1024, 512), spc=256, octaves=10, seed=3)
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("method,dims,size,dtype", [
+    (0, 2, (2048, 1536), P.PTG_F32), (0, 2, (1000, 777), P.PTG_F16), (1, 2, (2048, 1100), P.PTG_F32),
+    (2, 2, (700, 900), P.PTG_F32), (0, 3, (128, 96, 80), P.PTG_F16),
+])
+def test_generate_host_matches_device(ctx, method, dims, size, dtype):
+    kind = ["c1", "perlin_s5", "opensimplex"][method]
+    spc = 64 if dims == 2 else 16
+    dev = gpu_field(ctx, kind, dims=dims, size=size, spc=spc, octaves=9, seed=6, dtype=dtype)
+    d = P.make_desc(dims=dims, size=size, spc=spc, octaves=9, seed=6, dtype=dtype)
+    host = torch.empty(dev.shape, dtype=dev.dtype).pin_memory()
+    P.ptg_generate_host(ctx, d, method, host)
+    assert torch.equal(host, dev.cpu())
+
+
+def test_short_forms(ctx):
+    out = torch.empty((200, 300), dtype=torch.float32, device="cuda")
+    P.ptg_heightmap2d(ctx, (300, 200), 5, P.PTG_C2, 0.5, 2.0, 9, out)
+    ref = gpu_field(ctx, "c2", size=(300, 200), spc=64, octaves=5, seed=9)
+    assert torch.equal(out, ref)
+    vol = torch.empty((40, 30, 20), dtype=torch.float32, device="cuda")
+    P.ptg_volume3d(ctx, (20, 30, 40), 4, P.PTG_C1, 0.5, 2.0, 9, vol)
+    ref3 = gpu_field(ctx, "c1", dims=3, size=(20, 30, 40), spc=64, octaves=4, seed=9)
+    assert torch.equal(vol, ref3)
+
+
+# ---------------------------------------------------------------------------
+# argument errors write nothing
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kw,code", [
+    (dict(size=(0, 16)), P.PTG_ERR_INVALID), (dict(spc=3), P.PTG_ERR_UNSUPPORTED),
+    (dict(octaves=0), P.PTG_ERR_INVALID), (dict(lacunarity=2.5), P.PTG_ERR_UNSUPPORTED),
+    (dict(smoothness=9), P.PTG_ERR_INVALID), (dict(seed=1 << 24), P.PTG_ERR_INVALID),
+])
+def test_invalid_arguments_write_nothing(ctx, kw, code):
+    args = dict(size=(64, 64), spc=16, octaves=3)
+    args.update(kw)
+    d = P.make_desc(**args)
+    out = torch.full((64, 64), 7.0, device="cuda")
+    with pytest.raises(P.PtgError) as e:
+        P.ptg_field(ctx, d, out.data_ptr())
+    assert e.value.code == code
+    torch.cuda.synchronize()
+    assert bool((out == 7.0).all())
