@@ -134,12 +134,29 @@ int ptg_opensimplex(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, void* s
  * Uses context-owned device staging (allocated on first use, kept). */
 int ptg_generate_host(ptg_ctx* ctx, const ptg_field_desc* desc, int32_t method, void* host_out);
 
-/* Batched generation: n independent fields (any mix of 2D sizes, octave
- * counts, C1/C2, seeds, origins) in ONE persistent launch.  descs: host array
- * of n descriptors; outs: host array of n device output pointers.  Work is
- * split into tiles pulled from a device work list by resident CTAs.
- * Uses context-owned device memory for the work list (grown on demand). */
+/* Batched generation: n independent 2D fields (any mix of sizes, octave
+ * counts, C1/C2 polynomial noise, seeds, origins, offsets, FP32/FP16) in ONE
+ * persistent launch: resident CTAs pull 64 x 64 tiles of all fields from a
+ * device work counter.  descs: host array of n descriptors; outs: host array
+ * of n device output pointers.  Results equal n separate ptg_field calls
+ * bit for bit.  Uses context-owned device memory for the launch plans and
+ * the counter (grown on demand, kept).  Asynchronous on `stream`. */
 int ptg_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n, void* stream);
+
+/* A prepared batch: plans uploaded once and the launch (counter reset plus
+ * the persistent kernel) captured in a CUDA graph, for batches that repeat
+ * with the same fields and outputs. */
+typedef struct ptg_batch_plan ptg_batch_plan;
+
+/* Validate, upload and capture a batch (blocking).  *plan receives it. */
+int ptg_batch_prepare(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n,
+                      ptg_batch_plan** plan);
+
+/* Launch a prepared batch (one graph launch) on `stream` (NULL = ctx). */
+int ptg_batch_launch(ptg_batch_plan* plan, void* stream);
+
+/* Free a prepared batch after its launches have completed. */
+int ptg_batch_free(ptg_batch_plan* plan);
 
 /* Request loop.  Queue one field for asynchronous generation into device
  * memory `out`.  Requests are admitted in arrival order while the admitted
@@ -155,8 +172,14 @@ int ptg_submit(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, uint64_t* re
 int ptg_poll(ptg_ctx* ctx, uint64_t req_id, ptg_status* st, uint64_t ts_ns[4]);
 
 /* Wait at most timeout_ns for a request; returns its final status or
- * PTG_ERR_TIMEOUT. */
+ * PTG_ERR_TIMEOUT.  The record stays until ptg_poll has returned the final
+ * status (ptg_poll releases it). */
 int ptg_wait(ptg_ctx* ctx, uint64_t req_id, uint64_t timeout_ns);
+
+/* Cancel a request that is still queued (not yet admitted): its final status
+ * becomes PTG_ERR_CANCELLED.  Returns PTG_OK, or PTG_ERR_INVALID if the
+ * request is unknown or already admitted. */
+int ptg_cancel(ptg_ctx* ctx, uint64_t req_id);
 
 /* Check a descriptor for generator `method` (0 = ptg_field, 1 = ptg_perlin,
  * 2 = ptg_opensimplex) without touching any device: returns the status the
@@ -173,6 +196,11 @@ const char* ptg_last_error(ptg_ctx* ctx);
 /* Hash n keys of dims+1 words (dims 2: pcg3d, 3: pcg4d) on the device.
  * keys, out: device arrays of n*(dims+1) uint32. */
 int ptg_debug_hash(ptg_ctx* ctx, int32_t dims, const uint32_t* keys, int64_t n, uint32_t* out, void* stream);
+
+/* Failure-injection hook for the request loop: hold = 1 makes the next
+ * admitted request's stream wait on the host (never on the device) until
+ * hold = 0 is set or 5 s pass, simulating a stalled device. */
+int ptg_debug_hold(ptg_ctx* ctx, int32_t hold);
 
 /* Cell index and in-cell position of n sample indices j (device int64) on
  * one axis at octave i, with the generators' fixed-point map:

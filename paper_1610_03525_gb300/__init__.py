@@ -76,9 +76,14 @@ def lib():
             "ptg_opensimplex": ([P, P, P, P], ctypes.c_int),
             "ptg_generate_host": ([P, P, I32, P], ctypes.c_int),
             "ptg_batch": ([P, P, P, I32, P], ctypes.c_int),
+            "ptg_batch_prepare": ([P, P, P, I32, ctypes.POINTER(P)], ctypes.c_int),
+            "ptg_batch_launch": ([P, P], ctypes.c_int),
+            "ptg_batch_free": ([P], ctypes.c_int),
             "ptg_submit": ([P, P, P, ctypes.POINTER(U64)], ctypes.c_int),
             "ptg_poll": ([P, U64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(U64)], ctypes.c_int),
             "ptg_wait": ([P, U64, U64], ctypes.c_int),
+            "ptg_cancel": ([P, U64], ctypes.c_int),
+            "ptg_debug_hold": ([P, I32], ctypes.c_int),
             "ptg_last_error": ([P], ctypes.c_char_p),
             "ptg_validate": ([P, I32, ctypes.c_char_p, I32], ctypes.c_int),
             "ptg_debug_hash": ([P, I32, P, I64, P, P], ctypes.c_int),
@@ -235,6 +240,33 @@ def ptg_batch(ctx: Context, descs, outs, stream=None) -> int:
     return _check(ctx, lib().ptg_batch(ctx.handle, arr, ptrs, n, _stream(stream)))
 
 
+class BatchPlan:
+    """Prepared batch (ptg_batch_plan): uploaded plans plus a captured graph."""
+
+    def __init__(self, ctx: Context, handle: int):
+        self.ctx = ctx
+        self.handle = handle
+
+
+def ptg_batch_prepare(ctx: Context, descs, outs) -> BatchPlan:
+    n = len(descs)
+    arr = (ptg_field_desc * n)(*descs)
+    ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+    h = ctypes.c_void_p()
+    _check(ctx, lib().ptg_batch_prepare(ctx.handle, arr, ptrs, n, ctypes.byref(h)))
+    return BatchPlan(ctx, h.value)
+
+
+def ptg_batch_launch(plan: BatchPlan, stream=None) -> int:
+    return _check(plan.ctx, lib().ptg_batch_launch(plan.handle, _stream(stream)))
+
+
+def ptg_batch_free(plan: BatchPlan) -> None:
+    if plan.handle:
+        lib().ptg_batch_free(plan.handle)
+        plan.handle = None
+
+
 def ptg_submit(ctx: Context, desc: ptg_field_desc, out) -> int:
     rid = ctypes.c_uint64()
     _check(ctx, lib().ptg_submit(ctx.handle, ctypes.byref(desc), _ptr(out), ctypes.byref(rid)))
@@ -250,6 +282,14 @@ def ptg_poll(ctx: Context, req_id: int):
 
 def ptg_wait(ctx: Context, req_id: int, timeout_ns: int) -> int:
     return lib().ptg_wait(ctx.handle, req_id, timeout_ns)
+
+
+def ptg_cancel(ctx: Context, req_id: int) -> int:
+    return _check(ctx, lib().ptg_cancel(ctx.handle, req_id))
+
+
+def ptg_debug_hold(ctx: Context, hold: int) -> int:
+    return _check(ctx, lib().ptg_debug_hold(ctx.handle, hold))
 
 
 def ptg_debug_hash(ctx: Context, dims: int, keys, out, stream=None) -> int:

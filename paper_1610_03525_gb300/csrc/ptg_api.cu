@@ -144,7 +144,8 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
         amp *= p;
     }
     P->ncorner = coff;
-    (void)method;
+    P->method = method;
+    P->s = s;
     const size_t smem = is3d ? fbm3d_smem_bytes(*P) : fbm2d_smem_bytes(*P);
     if (smem > (size_t)ctx->max_smem)
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "staging needs %zu bytes of shared memory (max %d)", smem,
@@ -288,6 +289,7 @@ int ptg_destroy(ptg_ctx* ctx)
     ptg_serve_shutdown(ctx);
     cudaStreamSynchronize(ctx->stream);
     ptg_host_release(ctx);
+    ptg_batch_release(ctx);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
     return PTG_OK;

@@ -1,0 +1,186 @@
+// ptg_batch.cu -- host side of batched generation: many 2D fields in one
+// persistent launch (ptg_batch), and prepared batches replayed as a CUDA graph
+// (ptg_batch_prepare / ptg_batch_launch / ptg_batch_free).
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ptg_internal.h"
+
+using namespace ptg;
+
+struct ptg_batch_plan {
+    ptg_ctx* ctx = nullptr;
+    FieldPlan* dplans = nullptr;
+    long long* dtiles = nullptr;
+    unsigned long long* dcounter = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+// Validates the fields and fills plans / tile prefix sums; returns the
+// largest dynamic shared memory any field needs in *smem.
+int build_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int n, FieldPlan* plans,
+                long long* tiles, size_t* smem)
+{
+    *smem = 0;
+    long long acc = 0;
+    for (int f = 0; f < n; ++f) {
+        const ptg_field_desc* d = descs + f;
+        int s = 0;
+        int rc = ptg_check_desc(ctx, d, kKindField, &s);
+        if (rc != PTG_OK) return ptg_fail(ctx, rc, "batch field %d: %s", f, ctx->err.c_str());
+        if (d->dims != 2) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "batch field %d: batches are 2D", f);
+        if (!outs[f]) return ptg_fail(ctx, PTG_ERR_INVALID, "batch field %d: out is NULL", f);
+        rc = ptg_make_field_plan(ctx, d, ptg_kernel_method(kKindField, d), outs[f], s, 0, d->size[1], plans + f);
+        if (rc != PTG_OK) return ptg_fail(ctx, rc, "batch field %d: %s", f, ctx->err.c_str());
+        const size_t sm = fbm2d_smem_bytes(plans[f]);
+        if (sm > *smem) *smem = sm;
+        tiles[f] = acc;
+        acc += (long long)plans[f].tiles_x * plans[f].tiles_y;
+    }
+    tiles[n] = acc;
+    return PTG_OK;
+}
+
+int batch_grid(ptg_ctx* ctx, size_t smem, long long total_tiles)
+{
+    const long long resident = (long long)ctx->num_sms * fbm2d_batch_blocks_per_sm(smem);
+    return (int)(total_tiles < resident ? total_tiles : resident);
+}
+
+}  // namespace
+
+void ptg_batch_release(ptg_ctx* ctx)
+{
+    if (ctx->batch_dplans) cudaFree(ctx->batch_dplans);
+    if (ctx->batch_dtiles) cudaFree(ctx->batch_dtiles);
+    if (ctx->batch_dcounter) cudaFree(ctx->batch_dcounter);
+    if (ctx->batch_hplans) cudaFreeHost(ctx->batch_hplans);
+    if (ctx->batch_htiles) cudaFreeHost(ctx->batch_htiles);
+    if (ctx->batch_uploaded) cudaEventDestroy(ctx->batch_uploaded);
+    ctx->batch_dplans = nullptr;
+    ctx->batch_dtiles = nullptr;
+    ctx->batch_dcounter = nullptr;
+    ctx->batch_hplans = nullptr;
+    ctx->batch_htiles = nullptr;
+    ctx->batch_uploaded = nullptr;
+    ctx->batch_cap = 0;
+}
+
+extern "C" {
+
+int ptg_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n, void* stream)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+    ctx->err.clear();
+    if (n < 0 || (n > 0 && (!descs || !outs))) return ptg_fail(ctx, PTG_ERR_INVALID, "bad batch arguments");
+    if (n == 0) return PTG_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return ptg_fail(ctx, PTG_ERR_CUDA, "cudaSetDevice failed");
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ptg_cuda_fail(ctx, e, "earlier asynchronous error");
+    if (ctx->batch_uploaded) cudaEventSynchronize(ctx->batch_uploaded);  // staging buffers free again
+    if (ctx->batch_cap < n) {
+        ptg_batch_release(ctx);
+        const int cap = n < 64 ? 64 : n;
+        if (cudaMalloc(&ctx->batch_dplans, sizeof(FieldPlan) * cap) != cudaSuccess ||
+            cudaMalloc(&ctx->batch_dtiles, sizeof(long long) * (cap + 1)) != cudaSuccess ||
+            cudaMalloc(&ctx->batch_dcounter, 256) != cudaSuccess ||
+            cudaMallocHost(&ctx->batch_hplans, sizeof(FieldPlan) * cap) != cudaSuccess ||
+            cudaMallocHost(&ctx->batch_htiles, sizeof(long long) * (cap + 1)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->batch_uploaded, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            ptg_batch_release(ctx);
+            return ptg_fail(ctx, PTG_ERR_NOMEM, "cannot allocate batch buffers for %d fields", n);
+        }
+        ctx->batch_cap = cap;
+    }
+    size_t smem = 0;
+    int rc = build_batch(ctx, descs, outs, n, ctx->batch_hplans, ctx->batch_htiles, &smem);
+    if (rc != PTG_OK) return rc;
+    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    cudaMemcpyAsync(ctx->batch_dplans, ctx->batch_hplans, sizeof(FieldPlan) * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ctx->batch_dtiles, ctx->batch_htiles, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st);
+    cudaEventRecord(ctx->batch_uploaded, st);
+    cudaMemsetAsync(ctx->batch_dcounter, 0, sizeof(unsigned long long), st);
+    const long long total = ctx->batch_htiles[n];
+    if (total == 0) return PTG_OK;
+    e = launch_fbm2d_batch(ctx->batch_dplans, ctx->batch_dtiles, n, ctx->batch_dcounter, smem,
+                           batch_grid(ctx, smem, total), st);
+    return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "batch launch");
+}
+
+int ptg_batch_prepare(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n,
+                      ptg_batch_plan** out)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+    ctx->err.clear();
+    if (!out || n <= 0 || !descs || !outs) return ptg_fail(ctx, PTG_ERR_INVALID, "bad batch arguments");
+    *out = nullptr;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return ptg_fail(ctx, PTG_ERR_CUDA, "cudaSetDevice failed");
+    std::vector<FieldPlan> plans((size_t)n);
+    std::vector<long long> tiles((size_t)n + 1);
+    size_t smem = 0;
+    int rc = build_batch(ctx, descs, outs, n, plans.data(), tiles.data(), &smem);
+    if (rc != PTG_OK) return rc;
+    ptg_batch_plan* p = new (std::nothrow) ptg_batch_plan();
+    if (!p) return ptg_fail(ctx, PTG_ERR_NOMEM, "out of host memory");
+    p->ctx = ctx;
+    if (cudaMalloc(&p->dplans, sizeof(FieldPlan) * n) != cudaSuccess ||
+        cudaMalloc(&p->dtiles, sizeof(long long) * (n + 1)) != cudaSuccess ||
+        cudaMalloc(&p->dcounter, 256) != cudaSuccess) {
+        cudaGetLastError();
+        ptg_batch_free(p);
+        return ptg_fail(ctx, PTG_ERR_NOMEM, "cannot allocate batch plan for %d fields", n);
+    }
+    cudaMemcpy(p->dplans, plans.data(), sizeof(FieldPlan) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->dtiles, tiles.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice);
+    const int blocks = batch_grid(ctx, smem, tiles[n]);
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // configure the kernel outside the capture, then capture reset + launch
+        fbm2d_batch_blocks_per_sm(smem);
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(p->dcounter, 0, sizeof(unsigned long long), cs);
+            if (tiles[n] > 0) launch_fbm2d_batch(p->dplans, p->dtiles, n, p->dcounter, smem, blocks, cs);
+            e = cudaStreamEndCapture(cs, &p->graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+        cudaStreamDestroy(cs);
+    }
+    if (e != cudaSuccess) {
+        ptg_batch_free(p);
+        return ptg_cuda_fail(ctx, e, "batch graph capture");
+    }
+    *out = p;
+    return PTG_OK;
+}
+
+int ptg_batch_launch(ptg_batch_plan* p, void* stream)
+{
+    if (!p || !p->exec) return PTG_ERR_INVALID;
+    DeviceGuard g(p->ctx->device);
+    cudaError_t e = cudaGraphLaunch(p->exec, stream ? (cudaStream_t)stream : p->ctx->stream);
+    return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(p->ctx, e, "batch graph launch");
+}
+
+int ptg_batch_free(ptg_batch_plan* p)
+{
+    if (!p) return PTG_OK;
+    DeviceGuard g(p->ctx->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->dplans) cudaFree(p->dplans);
+    if (p->dtiles) cudaFree(p->dtiles);
+    if (p->dcounter) cudaFree(p->dcounter);
+    delete p;
+    return PTG_OK;
+}
+
+}  // extern "C"

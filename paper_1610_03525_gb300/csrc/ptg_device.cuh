@@ -51,8 +51,12 @@ struct FieldPlan {
     int32_t vec_ok;         // 16-byte vector stores allowed (alignment, row length)
     int32_t tiles_x, tiles_y, tiles_z;
     int32_t jx0, jy0, jz0;  // sample index of output element 0 (bands of a larger field)
+    int32_t method;         // kC1, kC2, kPerlinS5, kPerlinS3
+    int32_t s;              // log2(samples per cell)
+    int32_t pad[6];
     OctPlan oct[kMaxOctaves];
 };
+static_assert(sizeof(FieldPlan) % 16 == 0, "FieldPlan is copied in 16-byte words");
 
 // ---------------------------------------------------------------------------
 // Hash: pcg3d and pcg4d of Jarzynski & Olano ("Hash Functions for GPU

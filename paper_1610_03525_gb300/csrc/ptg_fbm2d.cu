@@ -189,7 +189,90 @@ __global__ void __launch_bounds__(kThreads) fbm2d_kernel(const __grid_constant__
     fbm2d_tile<METHOD, OutT>(P, sm, s, blockIdx.x, blockIdx.y);
 }
 
+// Persistent batched generator: resident CTAs pull tiles of many fields from
+// one work counter.  Field f owns tiles [tile_start[f], tile_start[f+1]); its
+// plan is copied to shared memory when a CTA moves to it.  Every tile runs the
+// same code as the single-field kernel, so results are identical.
+__global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* __restrict__ plans,
+                                                               const long long* __restrict__ tile_start, int n,
+                                                               unsigned long long* __restrict__ counter)
+{
+    extern __shared__ float4 sm[];
+    __shared__ FieldPlan plan;
+    __shared__ long long s_tile;
+    __shared__ int s_field;
+    const long long total = tile_start[n];
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long t = (long long)atomicAdd(counter, 1ULL);
+            s_tile = t;
+            if (t < total) {
+                int lo = 0, hi = n - 1;  // last field whose first tile is <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (tile_start[mid] <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_field = lo;
+            }
+        }
+        __syncthreads();
+        const long long t = s_tile;
+        if (t >= total) break;
+        const int f = s_field;
+        if (f != cur) {
+            const int4* src = reinterpret_cast<const int4*>(plans + f);
+            int4* dst = reinterpret_cast<int4*>(&plan);
+            for (int q = threadIdx.x; q < (int)(sizeof(FieldPlan) / 16); q += kThreads) dst[q] = src[q];
+            cur = f;
+            __syncthreads();
+        }
+        const long long local = t - tile_start[f];
+        const int bx = (int)(local % plan.tiles_x), by = (int)(local / plan.tiles_x);
+        const int s = plan.s;
+        const bool f16 = plan.dtype == 1;
+        switch (plan.method) {
+        case kC1:
+            if (f16) fbm2d_tile<kC1, __half>(plan, sm, s, bx, by);
+            else fbm2d_tile<kC1, float>(plan, sm, s, bx, by);
+            break;
+        case kC2:
+            if (f16) fbm2d_tile<kC2, __half>(plan, sm, s, bx, by);
+            else fbm2d_tile<kC2, float>(plan, sm, s, bx, by);
+            break;
+        case kPerlinS5:
+            if (f16) fbm2d_tile<kPerlinS5, __half>(plan, sm, s, bx, by);
+            else fbm2d_tile<kPerlinS5, float>(plan, sm, s, bx, by);
+            break;
+        default:
+            if (f16) fbm2d_tile<kPerlinS3, __half>(plan, sm, s, bx, by);
+            else fbm2d_tile<kPerlinS3, float>(plan, sm, s, bx, by);
+            break;
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_fbm2d_batch(const FieldPlan* plans, const long long* tile_start, int n,
+                               unsigned long long* counter, size_t smem, int blocks, cudaStream_t stream)
+{
+    cudaError_t e = cudaFuncSetAttribute(fbm2d_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fbm2d_batch_kernel<<<blocks, kThreads, smem, stream>>>(plans, tile_start, n, counter);
+    return cudaGetLastError();
+}
+
+int fbm2d_batch_blocks_per_sm(size_t smem)
+{
+    int nb = 0;
+    cudaFuncSetAttribute(fbm2d_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fbm2d_batch_kernel, kThreads, smem) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
 
 size_t fbm2d_smem_bytes(const FieldPlan& P) { return sizeof(float4) * (size_t)(P.nst * 128 + P.ncorner); }
 

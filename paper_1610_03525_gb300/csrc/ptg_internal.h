@@ -45,6 +45,14 @@ struct ptg_ctx {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_gen[2] = {nullptr, nullptr};
     cudaEvent_t ev_copy[2] = {nullptr, nullptr};
+    // batched generation (ptg_batch)
+    ptg::FieldPlan* batch_dplans = nullptr;
+    long long* batch_dtiles = nullptr;
+    unsigned long long* batch_dcounter = nullptr;
+    ptg::FieldPlan* batch_hplans = nullptr;  // pinned staging of the plans
+    long long* batch_htiles = nullptr;
+    int batch_cap = 0;
+    cudaEvent_t batch_uploaded = nullptr;
     // request loop
     PtgServer* server = nullptr;
 };
@@ -61,4 +69,5 @@ int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void
 int ptg_kernel_method(int kind, const ptg_field_desc* d);
 
 void ptg_host_release(ptg_ctx* ctx);
+void ptg_batch_release(ptg_ctx* ctx);
 void ptg_serve_shutdown(ptg_ctx* ctx);

@@ -16,8 +16,13 @@
 // branch-free (max(0, 2 - r^2)).
 //
 // Precision: the octave-i position of the CTA tile's first sample is formed in
-// FP64 once per octave and split into an integer vertex and a fraction; the
-// per-sample offsets inside the tile are small and exact in FP32.
+// FP64 once per octave and split into an integer vertex and a fraction.  A
+// sample's offset (cs, rs) from it is exact in FP32 (multiples of 2^i / spc);
+// its stretched coordinates add K r with K = cs + rs, where the product with the
+// irrational r is taken in two pieces, r = r_hi + r_lo, with the rounding error
+// of K r_hi recovered by an FMA, and integer parts are removed before any
+// fractions are summed, so the in-cell position keeps full FP32 accuracy at
+// every octave.
 #include <cstdint>
 
 #include "ptg_device.cuh"
@@ -28,8 +33,9 @@ namespace {
 
 constexpr int kTW = 64, kTH = 64, kThreads = 128, kCols = 8, kRows = 4;
 constexpr float kSquish = 0.36602540378443865f;   // (sqrt(3) - 1) / 2
-constexpr float kStretch = -0.21132486540518713f; // (1/sqrt(3) - 1) / 2
-constexpr double kStretchD = -0.21132486540518713;
+constexpr double kStretchD = -0.21132486540518713; // (1/sqrt(3) - 1) / 2
+constexpr float kStretchHi = (float)kStretchD;
+constexpr float kStretchLo = (float)(kStretchD - (double)kStretchHi);
 constexpr float kScale = 0.125f;
 
 struct TileOctave {
@@ -84,17 +90,34 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
         const TileOctave T = tile[i];
         const float step = P.step[i], amp = P.amp[i] * kScale;
         const uint32_t key = P.key[i];
+        float cs[kCols], fxc[kCols];
+        int32_t icx[kCols];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+            cs[c] = (float)(tx * kCols + c) * step;  // exact
+            const float fl = floorf(cs[c]);
+            icx[c] = (int32_t)fl;
+            fxc[c] = T.fx + (cs[c] - fl);
+        }
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
-            const float oy = (float)(ty * kRows + r) * step;
+            const float rs = (float)(ty * kRows + r) * step;  // exact
+            const float fl = floorf(rs);
+            const int32_t iry = (int32_t)fl;
+            const float fyr = T.fy + (rs - fl);
 #pragma unroll
             for (int c = 0; c < kCols; ++c) {
-                const float ox = (float)(tx * kCols + c) * step;
-                const float sh = (ox + oy) * kStretch;
-                const float xs = T.fx + (ox + sh), ys = T.fy + (oy + sh);
-                const float fxs = floorf(xs), fys = floorf(ys);
-                const int32_t a = T.a0 + (int32_t)fxs, b = T.b0 + (int32_t)fys;
-                const float xi = xs - fxs, yi = ys - fys;
+                const float K = cs[c] + rs;                      // exact
+                const float p = K * kStretchHi;
+                const float e = fmaf(K, kStretchHi, -p);         // exact rounding error of p
+                const float ip = floorf(p);
+                const float t = (p - ip) + (e + K * kStretchLo);
+                const float sx = fxc[c] + t, sy = fyr + t;
+                const float flx = floorf(sx), fly = floorf(sy);
+                const float xi = sx - flx, yi = sy - fly;
+                const int32_t iip = (int32_t)ip;
+                const int32_t a = T.a0 + icx[c] + iip + (int32_t)flx;
+                const int32_t b = T.b0 + iry + iip + (int32_t)fly;
                 float h;
                 if (xi + yi < 1.0f) {
                     h = vertex_at(a, b, 0, 0, key, xi, yi) + vertex_at(a, b, 1, 0, key, xi, yi) +

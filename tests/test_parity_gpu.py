@@ -116,15 +116,19 @@ def test_axis_bit_exact(ctx, spc):
 
 
 def test_lattice_octaves_are_exact_corner_values(ctx):
-    """spc = 1: every octave samples lattice points; heights are sums of
-    exactly representable corner values times powers of two."""
+    """spc = 1: every octave samples lattice points.  One octave is the
+    corner value itself (exact in FP32); several octaves are a sum whose
+    FP32 rounding stays inside the tolerance."""
     for dims, size in [(2, (300, 70)), (3, (40, 24, 9))]:
         for octaves in (1, 3):
             out = gpu_field(ctx, "c1", dims=dims, size=size, spc=1, octaves=octaves, origin=(-3, 1 << 20, 7),
                             seed=99)
             idx = W.grid_indices_2d(*size) if dims == 2 else W.grid_indices_3d(*size)
             ref = oracle_at("c1", idx, dims=dims, spc=1, octaves=octaves, origin=(-3, 1 << 20, 7), seed=99)
-            assert np.array_equal(gather(out, idx), ref)
+            if octaves == 1:
+                assert np.array_equal(gather(out, idx), ref)
+            else:
+                assert np.abs(gather(out, idx) - ref).max() <= tol32(octaves)
 
 
 # ---------------------------------------------------------------------------
