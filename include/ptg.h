@@ -34,7 +34,7 @@
  *   - Device pointers are caller-owned device memory of at least
  *     prod(size) * sizeof(dtype) bytes; the library never frees or keeps them
  *     past the completion of the call's work.
- *   - stream is a cudaStream_t, or NULL for the context's own stream.  Calls
+ *   - stream is a cudaStream_t; NULL is the CUDA default stream.  Calls
  *     return after enqueueing; results are ready when the stream is.
  *   - Argument errors return synchronously and write nothing.  Asynchronous
  *     CUDA errors are reported as PTG_ERR_CUDA by the next call.
@@ -152,7 +152,7 @@ typedef struct ptg_batch_plan ptg_batch_plan;
 int ptg_batch_prepare(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n,
                       ptg_batch_plan** plan);
 
-/* Launch a prepared batch (one graph launch) on `stream` (NULL = ctx). */
+/* Launch a prepared batch (one graph launch) on `stream` (NULL = default). */
 int ptg_batch_launch(ptg_batch_plan* plan, void* stream);
 
 /* Free a prepared batch after its launches have completed. */

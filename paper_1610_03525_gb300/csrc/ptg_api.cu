@@ -227,7 +227,7 @@ static int generate(ptg_ctx* ctx, const ptg_field_desc* d, int kind, void* out, 
     if (!g.ok) return ptg_fail(ctx, PTG_ERR_CUDA, "cudaSetDevice(%d) failed", ctx->device);
     cudaError_t pending = cudaGetLastError();
     if (pending != cudaSuccess) return ptg_cuda_fail(ctx, pending, "earlier asynchronous error");
-    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    cudaStream_t st = (cudaStream_t)stream;
     const int64_t slow = d->dims == 3 ? d->size[2] : d->size[1];
     return ptg_launch_plan(ctx, kind, d, s, out, 0, slow, st);
 }
@@ -361,7 +361,7 @@ int ptg_debug_hash(ptg_ctx* ctx, int32_t dims, const uint32_t* keys, int64_t n, 
         return ptg_fail(ctx, PTG_ERR_INVALID, "bad debug_hash arguments");
     if (n == 0) return PTG_OK;
     DeviceGuard g(ctx->device);
-    cudaError_t e = launch_debug_hash(dims, keys, n, out, stream ? (cudaStream_t)stream : ctx->stream);
+    cudaError_t e = launch_debug_hash(dims, keys, n, out, (cudaStream_t)stream);
     return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "debug_hash");
 }
 
@@ -376,7 +376,7 @@ int ptg_debug_axis(ptg_ctx* ctx, int64_t origin, int64_t spc, int32_t octave, co
     if (n == 0) return PTG_OK;
     DeviceGuard g(ctx->device);
     cudaError_t e = launch_debug_axis((long long)origin, s, octave, (const long long*)j, (long long)n, cell, t,
-                                      stream ? (cudaStream_t)stream : ctx->stream);
+                                      (cudaStream_t)stream);
     return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "debug_axis");
 }
 

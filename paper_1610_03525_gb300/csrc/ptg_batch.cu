@@ -101,7 +101,7 @@ int ptg_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int3
     size_t smem = 0;
     int rc = build_batch(ctx, descs, outs, n, ctx->batch_hplans, ctx->batch_htiles, &smem);
     if (rc != PTG_OK) return rc;
-    cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    cudaStream_t st = (cudaStream_t)stream;
     cudaMemcpyAsync(ctx->batch_dplans, ctx->batch_hplans, sizeof(FieldPlan) * n, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(ctx->batch_dtiles, ctx->batch_htiles, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st);
     cudaEventRecord(ctx->batch_uploaded, st);
@@ -166,7 +166,7 @@ int ptg_batch_launch(ptg_batch_plan* p, void* stream)
 {
     if (!p || !p->exec) return PTG_ERR_INVALID;
     DeviceGuard g(p->ctx->device);
-    cudaError_t e = cudaGraphLaunch(p->exec, stream ? (cudaStream_t)stream : p->ctx->stream);
+    cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
     return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(p->ctx, e, "batch graph launch");
 }
 

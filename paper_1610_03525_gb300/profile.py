@@ -1,0 +1,46 @@
+"""Run one generator configuration a few times on cuda:0 (a target for ncu).
+
+    python -m paper_1610_03525_gb300.profile --kind c1 --size 8192 8192 --spc 1024 --octaves 12 --reps 3
+
+Kinds: c1, c2, perlin_s5, perlin_s3, opensimplex (2D), c1/c2 with three sizes
+for 3D.  No timing is done here; numbers come from the profiler.
+"""
+from __future__ import annotations
+
+import argparse
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kind", default="c1", choices=["c1", "c2", "perlin_s5", "perlin_s3", "opensimplex"])
+    ap.add_argument("--size", type=int, nargs="+", default=[8192, 8192])
+    ap.add_argument("--spc", type=int, default=1024)
+    ap.add_argument("--octaves", type=int, default=12)
+    ap.add_argument("--origin", type=int, nargs="+", default=[0, 0, 0])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f16"])
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+
+    import torch
+
+    import paper_1610_03525_gb300 as P
+
+    dims = len(args.size)
+    dtype = P.PTG_F16 if args.dtype == "f16" else P.PTG_F32
+    d = P.make_desc(dims=dims, size=tuple(args.size), spc=args.spc, origin=tuple(args.origin) + (0,) * 3,
+                    octaves=args.octaves, smoothness=P.PTG_C2 if args.kind == "c2" else P.PTG_C1,
+                    variant=P.PTG_PERLIN_S3 if args.kind == "perlin_s3" else P.PTG_PERLIN_S5, dtype=dtype)
+    out = torch.empty(tuple(reversed(args.size)), dtype=torch.float16 if dtype == P.PTG_F16 else torch.float32,
+                      device="cuda")
+    ctx = P.ptg_create(0)
+    fn = {"c1": P.ptg_field, "c2": P.ptg_field, "perlin_s5": P.ptg_perlin, "perlin_s3": P.ptg_perlin,
+          "opensimplex": P.ptg_opensimplex}[args.kind]
+    for _ in range(args.reps):
+        fn(ctx, d, out)
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ran %d x %s %s" % (args.reps, args.kind, "x".join(map(str, args.size))))
+
+
+if __name__ == "__main__":
+    main()
