@@ -158,6 +158,22 @@ int ptg_batch_launch(ptg_batch_plan* plan, void* stream);
 /* Free a prepared batch after its launches have completed. */
 int ptg_batch_free(ptg_batch_plan* plan);
 
+/* Batched generation for callers that cannot allocate device memory -- an
+ * engine that hands out all device memory from its own fixed arena, or a
+ * real-time loop in which cudaMalloc's implicit device synchronisation would
+ * stall every other stream.  Same fields, outputs and results as ptg_batch,
+ * but the launch plans and the work counter live in one fixed device array
+ * inside the library (file-scope, at most 256 fields, about 450 KB, held by
+ * every device that loads the library until the process exits) instead of
+ * context-owned allocations; no cudaMalloc, cudaFree or other allocator is
+ * called.  The caller owns every output buffer.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array and clear its
+ * counter: calls that overlap on the GPU race, so order them (one stream, or
+ * events).  n > 256 returns PTG_ERR_INVALID.  The paper has no counterpart;
+ * this is a deployment aid. */
+int ptg_batch_noalloc(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n, void* stream);
+
 /* Request loop.  Queue one field for asynchronous generation into device
  * memory `out`.  Requests are admitted in arrival order while the admitted
  * output bytes stay within the context's HBM budget; admitted requests run

@@ -79,6 +79,7 @@ def lib():
             "ptg_batch_prepare": ([P, P, P, I32, ctypes.POINTER(P)], ctypes.c_int),
             "ptg_batch_launch": ([P, P], ctypes.c_int),
             "ptg_batch_free": ([P], ctypes.c_int),
+            "ptg_batch_noalloc": ([P, P, P, I32, P], ctypes.c_int),
             "ptg_submit": ([P, P, P, ctypes.POINTER(U64)], ctypes.c_int),
             "ptg_poll": ([P, U64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(U64)], ctypes.c_int),
             "ptg_wait": ([P, U64, U64], ctypes.c_int),
@@ -238,6 +239,15 @@ def ptg_batch(ctx: Context, descs, outs, stream=None) -> int:
     arr = (ptg_field_desc * n)(*descs)
     ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
     return _check(ctx, lib().ptg_batch(ctx.handle, arr, ptrs, n, _stream(stream)))
+
+
+def ptg_batch_noalloc(ctx: Context, descs, outs, stream=None) -> int:
+    """ptg_batch without any allocation: plans and work counter live in the
+    library's fixed device array (at most 256 fields; see include/ptg.h)."""
+    n = len(descs)
+    arr = (ptg_field_desc * max(n, 1))(*descs)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[_ptr(o) for o in outs])
+    return _check(ctx, lib().ptg_batch_noalloc(ctx.handle, arr, ptrs, n, _stream(stream)))
 
 
 class BatchPlan:
