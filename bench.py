@@ -165,6 +165,138 @@ def oracle_sample_rate(rows: int, seed: int = 0):
     return idx.shape[0] / dt, idx.shape[0], dt, O.num_threads()
 
 
+def bench_3d(P, R, ctx, stream, torch, reps=10):
+    """512^3, 8 octaves, spc 128, C1, FP16 output, origin (2^20, 2^20, 0)."""
+    size = (512, 512, 512)
+    d = P.make_desc(dims=3, size=size, spc=128, origin=(1 << 20, 1 << 20, 0), octaves=8, smoothness=P.PTG_C1,
+                    seed=0, dtype=P.PTG_F16)
+    out = torch.empty((512, 512, 512), dtype=torch.float16, device="cuda")
+    for _ in range(3):
+        P.ptg_field(ctx, d, out, stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        P.ptg_field(ctx, d, out, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    n = 512 ** 3
+    ops = R.lane_ops_3d("c1", size, 128, 8)
+    del out
+    return {"workload": "3D 512^3, 8 octaves, spc 128 (4^3 base cells), C1, FP16 out, origin (2^20, 2^20, 0)",
+            "gsamples_s": n / ms / 1e6, "ms": ms, "ops_per_sample": ops["per_sample"],
+            "alu_frac": ops["total"] / (ms / 1e3) / R.alu_peak(torch.cuda.get_device_properties(0).multi_processor_count,
+                                                               2070.0)}
+
+
+def bench_batched(P, ctx, stream, torch, n_chunks=4096, reps=5):
+    """4096 2D chunks (side 64..1024, octaves 4..12, C1/C2) in one persistent
+    launch replayed from a CUDA graph, against one ptg_field launch per chunk."""
+    from paper_1610_03525_gb300 import workloads as Wl
+    chunks = Wl.chunk_batch(n_chunks)
+    descs, outs = [], []
+    for c in chunks:
+        descs.append(P.make_desc(dims=2, size=c["size"], spc=c["spc"], origin=c["origin"], octaves=c["octaves"],
+                                 smoothness=c["smoothness"], seed=c["seed"]))
+        outs.append(torch.empty((c["size"][1], c["size"][0]), dtype=torch.float32, device="cuda"))
+    n_samples = sum(c["size"][0] * c["size"][1] for c in chunks)
+    plan = P.ptg_batch_prepare(ctx, descs, outs)
+    for _ in range(2):
+        P.ptg_batch_launch(plan, stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        P.ptg_batch_launch(plan, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = a.elapsed_time(b) / reps
+    P.ptg_batch_free(plan)
+
+    def per_chunk():
+        for d, o in zip(descs, outs):
+            P.ptg_field(ctx, d, o, stream)
+    per_chunk()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a.record(stream)
+    for _ in range(reps):
+        per_chunk()
+    b.record(stream)
+    torch.cuda.synchronize()
+    wall_single = (time.perf_counter() - t0) * 1e3 / reps
+    ms_single = a.elapsed_time(b) / reps
+    del outs
+    return {"workload": "%d 2D chunks, side log-uniform 64..1024, octaves 4..12, C1/C2 50/50, spc 1024, "
+                        "seeds = chunk id, origins uniform in +-2^20 cells, FP32 out" % n_chunks,
+            "samples": n_samples,
+            "batched_graph_ms": ms_batch, "batched_gsamples_s": n_samples / ms_batch / 1e6,
+            "per_chunk_launches_ms": ms_single, "per_chunk_gsamples_s": n_samples / ms_single / 1e6,
+            "per_chunk_host_wall_ms": wall_single,
+            "speedup": ms_single / ms_batch}
+
+
+def bench_serving(P, torch, duration_s=2.0, warmup_s=0.5, rate_hz=20000.0, budget=40 << 30, slots=256):
+    """Poisson request stream through ptg_submit / ptg_poll (80% 2D 128..2048,
+    20% 3D 32..256, octaves 4..12, C1/C2) under a 40 GB budget."""
+    from paper_1610_03525_gb300 import workloads as Wl
+    ctx = P.ptg_create(torch.cuda.current_device(), budget)
+    reqs = Wl.request_stream(rate_hz=rate_hz, duration_s=duration_s + warmup_s)
+    slot_bytes = 256 ** 3 * 4
+    pool = torch.empty((slots, slot_bytes // 4), dtype=torch.float32, device="cuda")
+    descs = [P.make_desc(dims=r["dims"], size=r["size"], spc=r["spc"], origin=r["origin"], octaves=r["octaves"],
+                         smoothness=r["smoothness"], seed=r["seed"]) for r in reqs]
+    # warm the kernels
+    for d in descs[:64]:
+        P.ptg_field(ctx, d, pool[0].data_ptr(), 0)
+    torch.cuda.synchronize()
+    free = list(range(slots))
+    inflight = {}
+    lat = []
+    samples_done = 0
+    stalls = 0
+    t0 = time.perf_counter()
+    k = 0
+    first_measured = None
+    last_end_ns = 0
+    first_submit_ns = None
+    while k < len(reqs) or inflight:
+        now = time.perf_counter() - t0
+        while k < len(reqs) and reqs[k]["t"] <= now:
+            if not free:
+                stalls += 1
+                break
+            sl = free.pop()
+            rid = P.ptg_submit(ctx, descs[k], pool[sl].data_ptr())
+            inflight[rid] = (sl, k)
+            k += 1
+        for rid in list(inflight.keys()):
+            st, ts = P.ptg_poll(ctx, rid)
+            if st == P.PTG_PENDING:
+                continue
+            sl, kk = inflight.pop(rid)
+            free.append(sl)
+            if reqs[kk]["t"] >= warmup_s:
+                lat.append((ts[3] - ts[0]) / 1e6)
+                n = 1
+                for v in reqs[kk]["size"]:
+                    n *= v
+                samples_done += n
+                if first_submit_ns is None:
+                    first_submit_ns = ts[0]
+                last_end_ns = max(last_end_ns, ts[3])
+    ctx.close()
+    del pool
+    lat.sort()
+    span_s = (last_end_ns - first_submit_ns) / 1e9 if first_submit_ns else float("nan")
+    return {"workload": "Poisson %g req/s for %.1f s after %.1f s warm-up; 80%% 2D side 128..2048 (spc 1024), "
+                        "20%% 3D side 32..256 (spc 128); octaves 4..12; C1/C2 50/50; 40 GB budget" % (
+                            rate_hz, duration_s, warmup_s),
+            "requests": len(lat), "p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(0.99 * (len(lat) - 1))],
+            "sustained_gsamples_s": samples_done / span_s / 1e9, "client_slot_stalls": stalls}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -206,6 +338,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=32)
     ap.add_argument("--cpu-rows", type=int, default=1536, help="oracle rows for the cpu_baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip baselines, e2e and the oracle leg")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="measured seconds of the serving stream")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -332,6 +465,10 @@ def main():
                                                  "opensimplex_f32": "opensimplex"}[k], SIZE, SPC,
                                                 OCTAVES)["per_sample"]
         line["baselines"] = extras
+        if rank == 0:
+            line["config3_3d"] = bench_3d(P, R, ctx, stream, torch)
+            line["batched"] = bench_batched(P, ctx, stream, torch)
+            line["serving"] = bench_serving(P, torch, duration_s=args.serve_seconds)
 
         # end to end through the C ABI into pinned host memory
         host = torch.empty((SIZE[1], SIZE[0]), dtype=torch.float32).pin_memory()

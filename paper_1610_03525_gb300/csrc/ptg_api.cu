@@ -117,7 +117,7 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
     const int esz = d->dtype == PTG_F16 ? 2 : 4;
     P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
     P->nst = d->octaves < s ? d->octaves : s;
-    int coff = 0;
+    int coff = 0, count = 0;
     double amp = 1.0;
     const double p = (double)d->persistence, w = (double)d->grad_weight;
     for (int i = 0; i < d->octaves; ++i) {
@@ -130,7 +130,11 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
             o.ncy = ((TH - 1) >> (k < 31 ? k : 31)) + 2;
             o.ncz = is3d ? ((TD - 1) >> (k < 31 ? k : 31)) + 2 : 1;
             o.coff = coff;
-            coff += o.ncx * o.ncy * o.ncz;
+            o.magic = (uint32_t)(((uint64_t{1} << 32) + (uint64_t)o.ncx - 1) / (uint64_t)o.ncx);
+            o.magic2 = (uint32_t)(((uint64_t{1} << 32) + (uint64_t)(o.ncx * o.ncy) - 1) / (uint64_t)(o.ncx * o.ncy));
+            o.rowlen = corner_slot(o.ncx - 1) + 1;
+            coff += o.rowlen * o.ncy * o.ncz;
+            count += o.ncx * o.ncy * o.ncz;
         } else {
             o.mode = kModeLattice;
             o.k = i - s;
@@ -144,6 +148,7 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
         amp *= p;
     }
     P->ncorner = coff;
+    P->ncount = count;
     P->method = method;
     P->s = s;
     const size_t smem = is3d ? fbm3d_smem_bytes(*P) : fbm2d_smem_bytes(*P);

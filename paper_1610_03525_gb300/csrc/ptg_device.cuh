@@ -37,7 +37,9 @@ struct OctPlan {
     uint32_t ox, oy, oz;    // origin * 2^i (mod 2^32)
     float amp;              // persistence^i
     float ampw;             // persistence^i * grad_weight
-    int32_t pad;
+    uint32_t magic;         // staged: ceil(2^32 / ncx), so that e / ncx == umulhi(e, magic) for small e
+    uint32_t magic2;        // staged 3D: ceil(2^32 / (ncx * ncy))
+    int32_t rowlen;         // staged: float4 slots per corner row (rows are swizzled, see corner_slot)
 };
 
 // One field (2D or 3D) as the kernels see it.
@@ -47,13 +49,14 @@ struct FieldPlan {
     int32_t dtype;          // 0 = FP32, 1 = FP16
     int32_t N;              // octaves
     int32_t nst;            // staged octaves = min(N, log2 spc); they are 0 .. nst-1
-    int32_t ncorner;        // staged corners of one tile, all octaves
+    int32_t ncorner;        // staged corner slots of one tile, all octaves (shared memory)
+    int32_t ncount;         // staged corners of one tile, all octaves (hash work)
     int32_t vec_ok;         // 16-byte vector stores allowed (alignment, row length)
     int32_t tiles_x, tiles_y, tiles_z;
     int32_t jx0, jy0, jz0;  // sample index of output element 0 (bands of a larger field)
     int32_t method;         // kC1, kC2, kPerlinS5, kPerlinS3
     int32_t s;              // log2(samples per cell)
-    int32_t pad[6];
+    int32_t pad[1];
     OctPlan oct[kMaxOctaves];
 };
 static_assert(sizeof(FieldPlan) % 16 == 0, "FieldPlan is copied in 16-byte words");
@@ -116,7 +119,7 @@ __device__ __forceinline__ uint32_t pcg4d_value(uint32_t x, uint32_t y, uint32_t
 // the top 23 bits of u as mantissa lies in [2, 4); subtracting 3 is exact.
 __device__ __forceinline__ float unit_value(uint32_t u)
 {
-    return __uint_as_float(0x40000000u | (u >> 9)) - 3.0f;
+    return __uint_as_float(0x40000000u + (u >> 9)) - 3.0f;
 }
 
 // ---------------------------------------------------------------------------
@@ -166,6 +169,12 @@ __device__ __forceinline__ float axis_t(uint32_t j, int i, int s)
     const uint32_t r = j & ((1u << k) - 1u);
     return (float)r * __uint_as_float((uint32_t)(127 - k) << 23);  // r * 2^-k, exact
 }
+
+// Slot of corner column cx inside a staged 2D corner row: one pad slot after
+// every 8 corners, so that the 8 lanes of a quarter warp that read corners 1,
+// 2 or 4 apart (cells of 8, 4 or 2 samples) hit 8 different 16-byte bank
+// groups.
+__host__ __device__ __forceinline__ int corner_slot(int cx) { return cx + (cx >> 3); }
 
 // Output stores.
 __device__ __forceinline__ void store1(float* p, float v) { *p = v; }

@@ -3,15 +3,16 @@
 //
 // One CTA makes a 32 x 16 x 8 tile (x, y, z) with 128 threads; each thread
 // owns 8 consecutive x samples in 4 rows of one z plane (32 sums in
-// registers).  Staged octaves keep the tile's corners (value and gradient,
-// pre-scaled by the amplitude) and the per-axis bases in shared memory.  The
-// cell is separable: for the thread's plane z it is first reduced along z,
+// registers).  The cell is separable: for the thread's plane it is first
+// reduced along z,
 //    W_ab = v_ab0 + S(z) (v_ab1 - v_ab0) + B0(z) e_ab0 + B1(z) e_ab1,
 //    F_ab = f_ab0 + S(z) (f_ab1 - f_ab0),   G_ab = g_ab0 + S(z) (g_ab1 - g_ab0),
-// which leaves exactly the 2D cell with (v, f, g) -> (W, F, G); that one is
-// reduced per row to a 1D function of x and evaluated with 4 operations per
-// sample.  Lattice octaves take one pcg4d corner value per sample.
+// which leaves the 2D cell with (v, f, g) -> (W, F, G), handled as in 2D:
+// octaves whose cells are >= 8 samples wide evaluate node columns only and
+// interpolate once; cells of 4 and 2 samples use constant in-cell positions
+// along x and y; lattice octaves take one pcg4d corner value per sample.
 #include "ptg_device.cuh"
+#include "ptg_eval.cuh"
 #include "ptg_kernels.h"
 
 namespace ptg {
@@ -20,89 +21,157 @@ namespace {
 constexpr int kTW = kTile3dX, kTH = kTile3dY, kTD = kTile3dZ, kThreads = 128;
 constexpr int kCols = 8, kRows = 4;
 
-// float4 units: x-basis [nst][8 c][4 tx], y-basis [nst][4 r][4 ty],
-// z-basis [nst][8 tz], corners.
-__device__ __forceinline__ int xl(int i, int col) { return i * 32 + (col & 7) * 4 + (col >> 3); }
-__device__ __forceinline__ int yl(int nst, int i, int row) { return nst * 32 + i * 16 + (row & 3) * 4 + (row >> 2); }
-__device__ __forceinline__ int zl(int nst, int i, int pl) { return nst * 48 + i * 8 + pl; }
+// Shared memory (float4 units): x-basis at node columns [n8][D+1][4 tx],
+// y-basis [n8][4 r][4 ty], z-basis [n8][8 tz], staged corners (planes of
+// ncy swizzled rows).
+template <int METHOD>
+__host__ __device__ constexpr int xnode_words3(int n8) { return n8 * (Deg<METHOD>::value + 1) * 4; }
 
 template <int METHOD>
-__device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int j0x, int j0y, int j0z, int s)
+__host__ __device__ constexpr int corner_base3(int n8) { return xnode_words3<METHOD>(n8) + n8 * 24; }
+
+__device__ __forceinline__ int n_run8(const FieldPlan& P)
 {
-    const int tid = threadIdx.x, nst = P.nst;
-    for (int e = tid; e < nst * 56; e += kThreads) {
-        const int i = e / 56, r = e - i * 56;
-        if (r < 32) sm[xl(i, r)] = axis_basis<METHOD>(axis_t((uint32_t)(j0x + r), i, s));
-        else if (r < 48) sm[yl(nst, i, r - 32)] = axis_basis<METHOD>(axis_t((uint32_t)(j0y + r - 32), i, s));
-        else sm[zl(nst, i, r - 48)] = axis_basis<METHOD>(axis_t((uint32_t)(j0z + r - 48), i, s));
+    const int n = P.s - 2;
+    return n < 0 ? 0 : (n < P.N ? n : P.N);
+}
+
+template <int METHOD>
+__device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int j0x, int j0y, int j0z)
+{
+    constexpr int NN = Deg<METHOD>::value + 1;
+    const int tid = threadIdx.x, s = P.s, n8 = n_run8(P);
+    float4* xnode = sm;
+    float4* ylut = sm + xnode_words3<METHOD>(n8);
+    float4* zlut = ylut + n8 * 16;
+    float4* corners = sm + corner_base3<METHOD>(n8);
+    for (int e = tid; e < n8 * NN * 4; e += kThreads) {
+        const int i = e / (NN * 4), rem = e - i * (NN * 4);
+        const int q = rem >> 2, tx = rem & 3;
+        xnode[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0x + tx * 8 + node_col<Deg<METHOD>::value>(q)), i, s));
     }
-    float4* corners = sm + nst * 56;
-    for (int e = tid; e < P.ncorner; e += kThreads) {
-        int i = 0;
-        while (i + 1 < nst && e >= P.oct[i + 1].coff) ++i;
+    for (int e = tid; e < n8 * 24; e += kThreads) {
+        const int i = e / 24, slot = e - i * 24;
+        if (slot < 16) {  // y: slot = r * 4 + ty, row 4 ty + r
+            const int row = (slot & 3) * 4 + (slot >> 2);
+            ylut[i * 16 + slot] = axis_basis<METHOD>(axis_t((uint32_t)(j0y + row), i, s));
+        } else {
+            zlut[i * 8 + slot - 16] = axis_basis<METHOD>(axis_t((uint32_t)(j0z + slot - 16), i, s));
+        }
+    }
+    // Corners, octave by octave (uniform loops); octaves with at most 32
+    // corners go to one warp each, in turn (see the 2D generator).
+    const int warp = tid >> 5, lane = tid & 31;
+    int small = 0;
+    for (int i = 0; i < P.nst; ++i) {
         const OctPlan& op = P.oct[i];
-        const int local = e - op.coff;
-        const int nxy = op.ncx * op.ncy;
-        const int cz = local / nxy, rem = local - cz * nxy;
-        const int cy = rem / op.ncx, cx = rem - cy * op.ncx;
-        uint32_t x = op.ox + ((uint32_t)j0x >> op.k) + (uint32_t)cx;
-        uint32_t y = op.oy + ((uint32_t)j0y >> op.k) + (uint32_t)cy;
-        uint32_t z = op.oz + ((uint32_t)j0z >> op.k) + (uint32_t)cz;
-        uint32_t w = op.key;
-        pcg4d(x, y, z, w);
-        corners[e] = make_float4(unit_value(x) * op.amp, unit_value(y) * op.ampw, unit_value(z) * op.ampw,
-                                 unit_value(w) * op.ampw);
+        const int nxy = op.ncx * op.ncy, n = nxy * op.ncz;
+        int e0 = tid, step = kThreads;
+        if (n <= 32) {
+            if ((small++ & 3) != warp) continue;
+            e0 = lane;
+            step = 32;
+        }
+        const uint32_t bx = op.ox + ((uint32_t)j0x >> op.k), by = op.oy + ((uint32_t)j0y >> op.k);
+        const uint32_t bz = op.oz + ((uint32_t)j0z >> op.k);
+        float4* cg = corners + op.coff;
+        for (int e = e0; e < n; e += step) {
+            const int cz = (int)__umulhi((uint32_t)e, op.magic2);
+            const int rem = e - cz * nxy;
+            const int cy = (int)__umulhi((uint32_t)rem, op.magic);
+            const int cx = rem - cy * op.ncx;
+            uint32_t x = bx + (uint32_t)cx, y = by + (uint32_t)cy, z = bz + (uint32_t)cz, w = op.key;
+            pcg4d(x, y, z, w);
+            cg[(cz * op.ncy + cy) * op.rowlen + corner_slot(cx)] =
+                make_float4(unit_value(x) * op.amp, unit_value(y) * op.ampw, unit_value(z) * op.ampw,
+                            unit_value(w) * op.ampw);
+        }
     }
 }
 
-template <int CW, int RH>
-__device__ __forceinline__ void staged_octave3(float (&acc)[kRows][kCols], const float4* __restrict__ sm,
-                                               const FieldPlan& P, int i, int tx, int ty, int tz)
+// The 2D cell (W, F, G per corner) of the thread's plane: reduction along z
+// of the 8 corners of cell (lcx, lcy, lcz) with z-basis zb.
+__device__ __forceinline__ Cell zcell(const float4* __restrict__ cg, const OctPlan& op, int lcx, int lcy, int lcz,
+                                      float4 zb)
+{
+    const int plane = op.ncy * op.rowlen;
+    const float4* p0 = cg + (lcz * op.ncy + lcy) * op.rowlen;
+    const int s0 = corner_slot(lcx), s1 = corner_slot(lcx + 1);
+    float4 r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {  // q = a + 2 b
+        const float4* p = p0 + (q >> 1) * op.rowlen + ((q & 1) ? s1 : s0);
+        const float4 lo = p[0], hi = p[plane];
+        r[q] = make_float4(fmaf(zb.z, hi.w, fmaf(zb.y, lo.w, fmaf(zb.x, hi.x - lo.x, lo.x))),
+                           fmaf(zb.x, hi.y - lo.y, lo.y), fmaf(zb.x, hi.z - lo.z, lo.z), 0.0f);
+    }
+    Cell c;
+    c.c00 = r[0];
+    c.c10 = r[1];
+    c.c01 = r[2];
+    c.c11 = r[3];
+    return c;
+}
+
+template <int METHOD>
+__device__ __forceinline__ void run8_octave3(float (&nacc)[kRows][Deg<METHOD>::value + 1],
+                                             const float4* __restrict__ sm, const FieldPlan& P, int i, int tx,
+                                             int ty, int tz, int n8)
+{
+    constexpr int NN = Deg<METHOD>::value + 1;
+    const OctPlan& op = P.oct[i];
+    const float4* ylut = sm + xnode_words3<METHOD>(n8);
+    const float4* zlut = ylut + n8 * 16;
+    const float4* cg = sm + corner_base3<METHOD>(n8) + op.coff;
+    const Cell c = zcell(cg, op, (tx * kCols) >> op.k, (ty * kRows) >> op.k, tz >> op.k, zlut[i * 8 + tz]);
+    float4 xb[NN];
+#pragma unroll
+    for (int q = 0; q < NN; ++q) xb[q] = sm[(i * NN + q) * 4 + tx];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const float4 yb = ylut[i * 16 + r * 4 + ty];
+        const Row R = row_of(c, yb.x, yb.y, yb.z);
+#pragma unroll
+        for (int q = 0; q < NN; ++q) nacc[r][q] += eval_row(R, xb[q].x, xb[q].y, xb[q].z);
+    }
+}
+
+// Cells of CW = 4 or 2 samples: in-cell positions along x and y are constants;
+// along z the thread's plane has position (tz mod CW) / CW.
+template <int METHOD, int CW>
+__device__ __forceinline__ void small_octave3(float (&acc)[kRows][kCols], const float4* __restrict__ sm,
+                                              const FieldPlan& P, int i, int tx, int ty, int tz, int n8)
 {
     const OctPlan& op = P.oct[i];
-    const int nst = P.nst, k = op.k, ncx = op.ncx, nxy = op.ncx * op.ncy;
-    const float4* cg = sm + nst * 56 + op.coff;
-    float4 xb[kCols];
+    const float4* cg = sm + corner_base3<METHOD>(n8) + op.coff;
+    constexpr float inv = 1.0f / CW;
+    const float4 zb = axis_basis<METHOD>((float)(tz & (CW - 1)) * inv);
+    const int lcz = tz / CW;
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) xb[c] = sm[xl(i, tx * 8 + c)];
-    const float4 zb = sm[zl(nst, i, tz)];
-    const int lcz = tz >> k;
-#pragma unroll
-    for (int yq = 0; yq < kRows / RH; ++yq) {
-        const int lcy = (ty * kRows + yq * RH) >> k;
-        float4 yb[RH];
-#pragma unroll
-        for (int r = 0; r < RH; ++r) yb[r] = sm[yl(nst, i, ty * kRows + yq * RH + r)];
+    for (int yq = 0; yq < kRows / CW; ++yq) {
+        const int lcy = (ty * kRows + yq * CW) / CW;
 #pragma unroll
         for (int xq = 0; xq < kCols / CW; ++xq) {
-            const int lcx = (tx * kCols + xq * CW) >> k;
-            const float4* c = cg + (lcz * op.ncy + lcy) * ncx + lcx;
-            // z reduction of the four (a, b) corner columns
-            float Wv[2][2], Fv[2][2], Gv[2][2];
+            const Cell c = zcell(cg, op, (tx * kCols + xq * CW) / CW, lcy, lcz, zb);
 #pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    const float4 lo = c[b * ncx + a], hi = c[nxy + b * ncx + a];
-                    Wv[a][b] = fmaf(zb.z, hi.w, fmaf(zb.y, lo.w, fmaf(zb.x, hi.x - lo.x, lo.x)));
-                    Fv[a][b] = fmaf(zb.x, hi.y - lo.y, lo.y);
-                    Gv[a][b] = fmaf(zb.x, hi.z - lo.z, lo.z);
+            for (int rr = 0; rr < CW; ++rr) {
+                Row R;
+                if (rr == 0) {
+                    R = row_at_zero(c);
+                } else {
+                    const float4 yb = axis_basis<METHOD>(rr * inv);
+                    R = row_of(c, yb.x, yb.y, yb.z);
                 }
-            const float dv0 = Wv[0][1] - Wv[0][0], dv1 = Wv[1][1] - Wv[1][0];
-            const float df0 = Fv[0][1] - Fv[0][0], df1 = Fv[1][1] - Fv[1][0];
-#pragma unroll
-            for (int r = 0; r < RH; ++r) {
-                const float Sy = yb[r].x, B0y = yb[r].y, B1y = yb[r].z;
-                const float V0 = fmaf(B1y, Gv[0][1], fmaf(B0y, Gv[0][0], fmaf(Sy, dv0, Wv[0][0])));
-                const float V1 = fmaf(B1y, Gv[1][1], fmaf(B0y, Gv[1][0], fmaf(Sy, dv1, Wv[1][0])));
-                const float F0 = fmaf(Sy, df0, Fv[0][0]);
-                const float F1 = fmaf(Sy, df1, Fv[1][0]);
-                const float dV = V1 - V0;
 #pragma unroll
                 for (int q = 0; q < CW; ++q) {
-                    const int col = xq * CW + q;
-                    const float h = fmaf(xb[col].z, F1, fmaf(xb[col].y, F0, fmaf(xb[col].x, dV, V0)));
-                    acc[yq * RH + r][col] += h;
+                    float h;
+                    if (q == 0) {
+                        h = R.V0;
+                    } else {
+                        const float4 xb = axis_basis<METHOD>(q * inv);
+                        h = eval_row(R, xb.x, xb.y, xb.z);
+                    }
+                    acc[yq * CW + rr][xq * CW + q] += h;
                 }
             }
         }
@@ -156,36 +225,62 @@ __device__ __forceinline__ void store_tile3(const FieldPlan& P, const float (&ac
 }
 
 template <int METHOD, typename OutT>
-__global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__ FieldPlan P, int s)
+__global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__ FieldPlan P)
 {
+    constexpr int D = Deg<METHOD>::value, NN = D + 1;
     extern __shared__ float4 sm[];
     const int tid = threadIdx.x, tx = tid & 3, ty = (tid >> 2) & 3, tz = tid >> 4;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH, z0 = blockIdx.z * kTD;  // output tile
     const int j0x = x0 + P.jx0, j0y = y0 + P.jy0, j0z = z0 + P.jz0;                  // sample indices
-    stage_tile3<METHOD>(P, sm, j0x, j0y, j0z, s);
+    const int s = P.s, N = P.N, n8 = n_run8(P);
+    stage_tile3<METHOD>(P, sm, j0x, j0y, j0z);
     __syncthreads();
+
+    float nacc[kRows][NN];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+#pragma unroll
+        for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
+    for (int i = 0; i < n8; ++i) run8_octave3<METHOD>(nacc, sm, P, i, tx, ty, tz, n8);
     float acc[kRows][kCols];
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) acc[r][c] = 0.0f;
-    for (int i = 0; i < P.N; ++i) {
-        const int mode = P.oct[i].mode;
-        if (mode == kModeRun8) staged_octave3<8, 4>(acc, sm, P, i, tx, ty, tz);
-        else if (mode == kModeRun4) staged_octave3<4, 4>(acc, sm, P, i, tx, ty, tz);
-        else if (mode == kModeRun2) staged_octave3<2, 2>(acc, sm, P, i, tx, ty, tz);
-        else
-            lattice_octave3(acc, P.oct[i], (uint32_t)(j0x + tx * kCols), (uint32_t)(j0y + ty * kRows),
-                            (uint32_t)(j0z + tz));
-    }
+        for (int c = 0; c < kCols; ++c) {
+            const int q = node_of_col<D>(c);
+            if (q >= 0) {
+                acc[r][c] = nacc[r][q];
+            } else {
+                float v = 0.0f;
+#pragma unroll
+                for (int m = 0; m < NN; ++m) v = fmaf(lagrange<D>(c, m), nacc[r][m], v);
+                acc[r][c] = v;
+            }
+        }
+    if (s >= 2 && s - 2 < N) small_octave3<METHOD, 4>(acc, sm, P, s - 2, tx, ty, tz, n8);
+    if (s >= 1 && s - 1 < N) small_octave3<METHOD, 2>(acc, sm, P, s - 1, tx, ty, tz, n8);
+    for (int i = s; i < N; ++i)
+        lattice_octave3(acc, P.oct[i], (uint32_t)(j0x + tx * kCols), (uint32_t)(j0y + ty * kRows),
+                        (uint32_t)(j0z + tz));
     store_tile3<OutT>(P, acc, x0 + tx * kCols, y0 + ty * kRows, z0 + tz);
+}
+
+template <int METHOD>
+size_t smem_words3(const FieldPlan& P)
+{
+    int n8 = P.s - 2;
+    n8 = n8 < 0 ? 0 : (n8 < P.N ? n8 : P.N);
+    return (size_t)corner_base3<METHOD>(n8) + (size_t)P.ncorner;
 }
 
 }  // namespace
 
-size_t fbm3d_smem_bytes(const FieldPlan& P) { return sizeof(float4) * (size_t)(P.nst * 56 + P.ncorner); }
+size_t fbm3d_smem_bytes(const FieldPlan& P)
+{
+    return sizeof(float4) * (P.method == kC2 ? smem_words3<kC2>(P) : smem_words3<kC1>(P));
+}
 
-cudaError_t launch_fbm3d(const FieldPlan& P, int method, int s, cudaStream_t stream)
+cudaError_t launch_fbm3d(const FieldPlan& P, int method, int /*s*/, cudaStream_t stream)
 {
     const dim3 grid(P.tiles_x, P.tiles_y, P.tiles_z);
     const size_t smem = fbm3d_smem_bytes(P);
@@ -196,7 +291,10 @@ cudaError_t launch_fbm3d(const FieldPlan& P, int method, int s, cudaStream_t str
         cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                                              (int)smem);                                             \
         if (e != cudaSuccess) return e;                                                              \
-        kfn<<<grid, kThreads, smem, stream>>>(P, s);                                                 \
+        e = cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout,                \
+                                 cudaSharedmemCarveoutMaxShared);                                    \
+        if (e != cudaSuccess) return e;                                                              \
+        kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
         return cudaGetLastError();                                                                   \
     } while (0)
     switch (method) {

@@ -9,18 +9,24 @@ loop control and barriers are overhead and are NOT counted, so the achieved
 fraction of the issue peak measures how little overhead and stall the kernels
 add on top of the arithmetic they must do.
 
-Per 2D tile of 64 x 64 samples (128 threads x 4 rows x 8 columns):
-  basis tables: 128 entries per staged octave x (5 coordinate + basis ops:
+Per 2D tile of 64 x 64 samples (128 threads x 4 rows x 8 columns), with
+d = 3 (C1), 5 (C2), 4 (Perlin-S3), 6 (Perlin-S5) and n8 = octaves whose cells
+are at least 8 samples wide:
+  basis tables: n8 x (8 (d+1) + 64) entries x (5 coordinate + basis ops:
                 C1 7, C2 14, Perlin-S5 9, Perlin-S3 8);
-  corners:      per staged corner 35 (pcg3d 15, three word->float maps 9,
-                three amplitude scalings 3, grid index 8);
-  staged octave per thread, cells of CW x RH samples of the thread's run:
-                per cell 4 (y differences) + RH rows x 9 (row reduction), plus
-                4 per sample (1 add + 3 FMA);
+  corners:      per staged corner 31 (pcg3d 15, three word->float maps 9,
+                three amplitude scalings 3, grid index 4);
+  cells >= 8 samples, per thread and octave: 4 (y differences) + 4 rows x
+                (9 row reduction + 4 (d+1) at the node columns); once per
+                thread, 4 rows x (7 - d) columns x (d+1) FMA of interpolation;
+  cells of 4 samples, per thread: 2 cells x 32 + 24 samples x 4 + 8 x 1;
+  cells of 2 samples, per thread: 8 cells x (14 + 10);
   lattice octave: per sample 19 (pcg3d word 0: 13, word->float 3, FMA 1,
                 coordinate 2); Perlin's lattice octaves are zero, no work.
-3D tiles of 32 x 16 x 8: per cell additionally 32 (z reduction of the four
-corner columns); corners 48 (pcg4d 20); lattice samples 23.
+3D tiles of 32 x 16 x 8 (each thread 8 x 4 x 1): the same regimes, with a
+reduction along z of the cell's four corner columns (32 ops) before each cell
+is used, basis tables of n8 x (4 (d+1) + 24) entries, corners 42 (pcg4d 20,
+four word->float maps 12, four scalings 4, index 6) and lattice samples 23.
 OpenSimplex-style: per sample and octave 150 (4 vertices x 33 + 18).
 """
 from __future__ import annotations
@@ -35,6 +41,9 @@ def _staged(spc: int, octaves: int):
     return [(i, spc >> i) for i in range(min(octaves, s))]
 
 
+DEG = {"c1": 3, "c2": 5, "perlin_s3": 4, "perlin_s5": 6}
+
+
 def lane_ops_2d(kind: str, size, spc: int, octaves: int) -> dict:
     w, h = size
     tiles = ((w + 63) // 64) * ((h + 63) // 64)
@@ -43,17 +52,22 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int) -> dict:
     if kind == "opensimplex":
         tot = 150 * samples_padded * octaves
         return dict(total=float(tot), per_sample=tot / (w * h))
+    d = DEG[kind]
     st = _staged(spc, octaves)
-    lut = tiles * len(st) * 128 * (COORD_OPS + BASIS_OPS[kind])
+    n8 = sum(1 for _, spci in st if spci >= 8)
+    lut = tiles * n8 * (8 * (d + 1) + 64) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
-    evalops = 0
+    evalops = threads * 4 * (7 - d) * (d + 1)
     for i, spci in st:
         k = spci.bit_length() - 1
         ncx = (63 >> min(k, 31)) + 2
-        corners += tiles * ncx * ncx * 35
-        cw, rh = min(8, spci), min(4, spci)
-        cells = (8 // cw) * (4 // rh)
-        evalops += threads * (cells * (4 + rh * 9) + 32 * 4)
+        corners += tiles * ncx * ncx * 31
+        if spci >= 8:
+            evalops += threads * (4 + 4 * (9 + 4 * (d + 1)))
+        elif spci == 4:
+            evalops += threads * (2 * 32 + 24 * 4 + 8)
+        else:
+            evalops += threads * 8 * (14 + 10)
     n_lattice = octaves - len(st)
     lattice = 0 if kind.startswith("perlin") else samples_padded * n_lattice * 19
     tot = lut + corners + evalops + lattice
@@ -62,24 +76,29 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int) -> dict:
 
 
 def lane_ops_3d(kind: str, size, spc: int, octaves: int) -> dict:
-    w, h, d = size
-    tiles = ((w + 31) // 32) * ((h + 15) // 16) * ((d + 7) // 8)
+    w, h, dd = size
+    tiles = ((w + 31) // 32) * ((h + 15) // 16) * ((dd + 7) // 8)
     threads = tiles * 128
     samples_padded = tiles * 32 * 16 * 8
+    d = DEG[kind]
     st = _staged(spc, octaves)
-    lut = tiles * len(st) * 56 * (COORD_OPS + BASIS_OPS[kind])
+    n8 = sum(1 for _, spci in st if spci >= 8)
+    lut = tiles * n8 * (4 * (d + 1) + 24) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
-    evalops = 0
+    evalops = threads * 4 * (7 - d) * (d + 1)
     for i, spci in st:
         k = spci.bit_length() - 1
         nc = ((31 >> min(k, 31)) + 2) * ((15 >> min(k, 31)) + 2) * ((7 >> min(k, 31)) + 2)
-        corners += tiles * nc * 48
-        cw, rh = min(8, spci), min(4, spci)
-        cells = (8 // cw) * (4 // rh)
-        evalops += threads * (cells * (32 + 4 + rh * 9) + 32 * 4)
+        corners += tiles * nc * 42
+        if spci >= 8:
+            evalops += threads * (32 + 4 + 4 * (9 + 4 * (d + 1)))
+        elif spci == 4:
+            evalops += threads * (2 * (32 + 4 + 1 + 3 * 9) + 24 * 4 + 8)
+        else:
+            evalops += threads * (8 * (32 + 4 + 1 + 9) + 80)
     lattice = samples_padded * (octaves - len(st)) * 23
     tot = lut + corners + evalops + lattice
-    return dict(total=float(tot), per_sample=tot / (w * h * d), lut=lut, corners=corners, eval=evalops,
+    return dict(total=float(tot), per_sample=tot / (w * h * dd), lut=lut, corners=corners, eval=evalops,
                 lattice=lattice)
 
 
