@@ -181,9 +181,21 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
     if (std::ldexp(lim, d->octaves - 1) >= std::ldexp(1.0, 30))
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "OpenSimplex lattice coordinates exceed 2^30");
     double amp = 1.0;
+    int box = 0;
     for (int i = 0; i < d->octaves; ++i) {
         const double scale = std::ldexp(1.0, i);
         const double step = scale / spc;
+        // stage the tile's vertex gradients while the lattice is coarser than
+        // the samples; the box side is bounded by 64 step + 7 vertices
+        P->box_wb[i] = 0;
+        if (step < 1.0) {
+            const int wb = (int)std::floor(64.0 * step * 1.0001) + 8;
+            if ((size_t)(box + wb * wb) * 8 <= (size_t)96 * 1024) {
+                P->box_off[i] = box;
+                P->box_wb[i] = wb;
+                box += wb * wb;
+            }
+        }
         P->base_x[i] = (double)d->origin[0] * scale + (double)d->offset[0] * step;
         P->base_y[i] = (double)d->origin[1] * scale + (double)(d->offset[1] + band_start) * step;
         P->step[i] = (float)step;
@@ -191,6 +203,7 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
         P->key[i] = (d->seed << 8) | (uint32_t)i;
         amp *= (double)d->persistence;
     }
+    P->box_words = box;
     return PTG_OK;
 }
 

@@ -33,6 +33,9 @@ struct SimplexPlan {
     float step[kMaxOctaves];
     float amp[kMaxOctaves];
     uint32_t key[kMaxOctaves];
+    int32_t box_off[kMaxOctaves];  // staged gradient box of octave i: first float2 in shared memory
+    int32_t box_wb[kMaxOctaves];   // its side bound (row stride); 0 = hash vertices directly
+    int32_t box_words;             // float2 words of shared memory for all boxes
 };
 cudaError_t launch_opensimplex2d(const SimplexPlan& P, cudaStream_t stream);
 

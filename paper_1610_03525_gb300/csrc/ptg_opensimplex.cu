@@ -15,6 +15,15 @@
 // vertices per sample and octave; the exclusion of out-of-range ones is
 // branch-free (max(0, 2 - r^2)).
 //
+// Gradient staging: for octaves whose lattice spacing is at least a sample
+// (2^i < spc), the CTA hashes every vertex of the stretched-plane box that its
+// 64 x 64 tile can touch into shared memory once; samples then read their four
+// gradients.  Finer octaves hash the four vertices per sample directly.  The
+// tile spans L = 64 2^i / spc lattice units in real space, i.e.
+// [s0 + r L, s0 + (1 + r) L] in each stretched coordinate (s0 the tile's first
+// sample); two vertices of margin below and three above cover the extra
+// vertices (offsets -1..2) and rounding.
+//
 // Precision: the octave-i position of the CTA tile's first sample is formed in
 // FP64 once per octave and split into an integer vertex and a fraction.  A
 // sample's offset (cs, rs) from it is exact in FP32 (multiples of 2^i / spc);
@@ -39,32 +48,122 @@ constexpr float kStretchLo = (float)(kStretchD - (double)kStretchHi);
 constexpr float kScale = 0.125f;
 
 struct TileOctave {
-    int32_t a0, b0;  // integer stretched vertex of the tile's first sample
-    float fx, fy;    // its fractional stretched coordinates
+    int32_t a0, b0;      // integer stretched vertex of the tile's first sample
+    float fx, fy;        // its fractional stretched coordinates
+    int32_t amin, bmin;  // staged: first vertex of the gradient box
+    int32_t w, h;        // staged: box extent actually filled (<= plan bound)
 };
 
-__device__ __forceinline__ float vertex_term(int32_t a, int32_t b, uint32_t key, float dx, float dy)
+__device__ __forceinline__ float kernel_term(float gx, float gy, float dx, float dy)
 {
-    uint32_t x = (uint32_t)a, y = (uint32_t)b, z = key;
-    pcg3d(x, y, z);
-    const float gx = unit_value(y), gy = unit_value(z);
     const float k = fmaxf(0.0f, 2.0f - fmaf(dx, dx, dy * dy));
     const float k2 = k * k;
     return (k2 * k2) * fmaf(gx, dx, gy * dy);
 }
 
+// Gradient of vertex (a, b): read from the staged box, or hashed.
+template <bool kStaged>
+struct Grad {
+    const float2* box;
+    int32_t amin, bmin, wb, size;
+    uint32_t key;
+    __device__ __forceinline__ float2 at(int32_t a, int32_t b) const
+    {
+        if (kStaged) {
+            int idx = (b - bmin) * wb + (a - amin);
+            idx = min(max(idx, 0), size - 1);  // the box covers every reachable vertex; the clamp only guards
+            return box[idx];
+        }
+        uint32_t x = (uint32_t)a, y = (uint32_t)b, z = key;
+        pcg3d(x, y, z);
+        return make_float2(unit_value(y), unit_value(z));
+    }
+};
+
 // Contribution of vertex (a + da, b + db) at stretched fraction (xi, yi).
-__device__ __forceinline__ float vertex_at(int32_t a, int32_t b, int da, int db, uint32_t key, float xi, float yi)
+template <bool kStaged>
+__device__ __forceinline__ float vertex_at(const Grad<kStaged>& G, int32_t a, int32_t b, int da, int db, float xi,
+                                           float yi)
 {
     const float u = xi - (float)da, v = yi - (float)db;
     const float s = (u + v) * kSquish;
-    return vertex_term(a + da, b + db, key, u + s, v + s);
+    const float2 g = G.at(a + da, b + db);
+    return kernel_term(g.x, g.y, u + s, v + s);
+}
+
+// Branch-free vertex choice (neighbouring samples fall in different
+// triangles, so branches would diverge): both triangles share (1,0) and
+// (0,1); the third vertex is (0,0) or (1,1); the extra one is selected from
+// the barycentric weights.
+template <bool kStaged>
+__device__ __forceinline__ float sample_noise(const Grad<kStaged>& G, int32_t a, int32_t b, float xi, float yi)
+{
+    const bool lower = xi + yi < 1.0f;
+    const int d3 = lower ? 0 : 1;
+    // lower: weights (w00, w10, w01) -> extras (1,1), (-1,1), (1,-1)
+    // upper: weights (w11, w10, w01) -> extras (0,0), (0,2), (2,0)
+    const float wc = lower ? 1.0f - xi - yi : xi + yi - 1.0f;
+    const float wx = lower ? xi : 1.0f - yi;
+    const float wy = lower ? yi : 1.0f - xi;
+    int ex, ey;
+    if (wc <= wx && wc <= wy) { ex = lower ? 1 : 0; ey = lower ? 1 : 0; }
+    else if (wx <= wy) { ex = lower ? -1 : 0; ey = lower ? 1 : 2; }
+    else { ex = lower ? 1 : 2; ey = lower ? -1 : 0; }
+    return vertex_at(G, a, b, 1, 0, xi, yi) + vertex_at(G, a, b, 0, 1, xi, yi) +
+           vertex_at(G, a, b, d3, d3, xi, yi) + vertex_at(G, a, b, ex, ey, xi, yi);
+}
+
+// One octave for the thread's 4 x 8 samples.
+template <bool kStaged>
+__device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const SimplexPlan& P, const TileOctave T,
+                                               const float2* boxes, int i, int tx, int ty)
+{
+    const float step = P.step[i], amp = P.amp[i] * kScale;
+    Grad<kStaged> G;
+    G.key = P.key[i];
+    G.wb = P.box_wb[i];
+    G.box = boxes + P.box_off[i];
+    G.amin = T.amin;
+    G.bmin = T.bmin;
+    G.size = G.wb * G.wb;
+    float cs[kCols], fxc[kCols];
+    int32_t icx[kCols];
+#pragma unroll
+    for (int c = 0; c < kCols; ++c) {
+        cs[c] = (float)(tx * kCols + c) * step;  // exact
+        const float fl = floorf(cs[c]);
+        icx[c] = (int32_t)fl;
+        fxc[c] = T.fx + (cs[c] - fl);
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const float rs = (float)(ty * kRows + r) * step;  // exact
+        const float fl = floorf(rs);
+        const int32_t iry = (int32_t)fl;
+        const float fyr = T.fy + (rs - fl);
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+            const float K = cs[c] + rs;                      // exact
+            const float p = K * kStretchHi;
+            const float e = fmaf(K, kStretchHi, -p);         // exact rounding error of p
+            const float ip = floorf(p);
+            const float t = (p - ip) + (e + K * kStretchLo);
+            const float sx = fxc[c] + t, sy = fyr + t;
+            const float flx = floorf(sx), fly = floorf(sy);
+            const float xi = sx - flx, yi = sy - fly;
+            const int32_t iip = (int32_t)ip;
+            const int32_t a = T.a0 + icx[c] + iip + (int32_t)flx;
+            const int32_t b = T.b0 + iry + iip + (int32_t)fly;
+            acc[r][c] = fmaf(amp, sample_noise(G, a, b, xi, yi), acc[r][c]);
+        }
+    }
 }
 
 template <typename OutT>
 __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_constant__ SimplexPlan P)
 {
     __shared__ TileOctave tile[kMaxOctaves];
+    extern __shared__ float2 boxes[];
     const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
     const int j0x = blockIdx.x * kTW, j0y = blockIdx.y * kTH;
     if (tid < P.N) {
@@ -74,12 +173,39 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
         const double sh = (X + Y) * kStretchD;
         const double xs = X + sh, ys = Y + sh;
         const double fa = floor(xs), fb = floor(ys);
-        tile[i].a0 = (int32_t)(long long)fa;
-        tile[i].b0 = (int32_t)(long long)fb;
-        tile[i].fx = (float)(xs - fa);
-        tile[i].fy = (float)(ys - fb);
+        TileOctave T;
+        T.a0 = (int32_t)(long long)fa;
+        T.b0 = (int32_t)(long long)fb;
+        T.fx = (float)(xs - fa);
+        T.fy = (float)(ys - fb);
+        T.amin = T.bmin = T.w = T.h = 0;
+        if (P.box_wb[i] > 0) {
+            const double L = 64.0 * (double)P.step[i];
+            T.amin = (int32_t)(long long)floor(xs + kStretchD * L) - 2;
+            T.bmin = (int32_t)(long long)floor(ys + kStretchD * L) - 2;
+            T.w = min((int32_t)(long long)floor(xs + (1.0 + kStretchD) * L) + 3 - T.amin + 1, P.box_wb[i]);
+            T.h = min((int32_t)(long long)floor(ys + (1.0 + kStretchD) * L) + 3 - T.bmin + 1, P.box_wb[i]);
+        }
+        tile[i] = T;
     }
     __syncthreads();
+    // hash the gradient boxes of the staged octaves (uniform loop per octave)
+    for (int i = 0; i < P.N; ++i) {
+        if (P.box_wb[i] <= 0) continue;
+        const TileOctave T = tile[i];
+        const int n = T.w * T.h, wb = P.box_wb[i];
+        const float inv = 1.0f / (float)T.w;
+        float2* box = boxes + P.box_off[i];
+        for (int v = tid; v < n; v += kThreads) {
+            const int vy = (int)(((float)v + 0.5f) * inv);  // exact: v < 2^14, w < 2^7
+            const int vx = v - vy * T.w;
+            uint32_t x = (uint32_t)(T.amin + vx), y = (uint32_t)(T.bmin + vy), z = P.key[i];
+            pcg3d(x, y, z);
+            box[vy * wb + vx] = make_float2(unit_value(y), unit_value(z));
+        }
+    }
+    __syncthreads();
+
     float acc[kRows][kCols];
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
@@ -87,60 +213,8 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
         for (int c = 0; c < kCols; ++c) acc[r][c] = 0.0f;
 
     for (int i = 0; i < P.N; ++i) {
-        const TileOctave T = tile[i];
-        const float step = P.step[i], amp = P.amp[i] * kScale;
-        const uint32_t key = P.key[i];
-        float cs[kCols], fxc[kCols];
-        int32_t icx[kCols];
-#pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-            cs[c] = (float)(tx * kCols + c) * step;  // exact
-            const float fl = floorf(cs[c]);
-            icx[c] = (int32_t)fl;
-            fxc[c] = T.fx + (cs[c] - fl);
-        }
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const float rs = (float)(ty * kRows + r) * step;  // exact
-            const float fl = floorf(rs);
-            const int32_t iry = (int32_t)fl;
-            const float fyr = T.fy + (rs - fl);
-#pragma unroll
-            for (int c = 0; c < kCols; ++c) {
-                const float K = cs[c] + rs;                      // exact
-                const float p = K * kStretchHi;
-                const float e = fmaf(K, kStretchHi, -p);         // exact rounding error of p
-                const float ip = floorf(p);
-                const float t = (p - ip) + (e + K * kStretchLo);
-                const float sx = fxc[c] + t, sy = fyr + t;
-                const float flx = floorf(sx), fly = floorf(sy);
-                const float xi = sx - flx, yi = sy - fly;
-                const int32_t iip = (int32_t)ip;
-                const int32_t a = T.a0 + icx[c] + iip + (int32_t)flx;
-                const int32_t b = T.b0 + iry + iip + (int32_t)fly;
-                float h;
-                if (xi + yi < 1.0f) {
-                    h = vertex_at(a, b, 0, 0, key, xi, yi) + vertex_at(a, b, 1, 0, key, xi, yi) +
-                        vertex_at(a, b, 0, 1, key, xi, yi);
-                    const float w00 = 1.0f - xi - yi;
-                    int da, db;
-                    if (w00 <= xi && w00 <= yi) { da = 1; db = 1; }
-                    else if (xi <= yi) { da = -1; db = 1; }
-                    else { da = 1; db = -1; }
-                    h += vertex_at(a, b, da, db, key, xi, yi);
-                } else {
-                    h = vertex_at(a, b, 1, 1, key, xi, yi) + vertex_at(a, b, 1, 0, key, xi, yi) +
-                        vertex_at(a, b, 0, 1, key, xi, yi);
-                    const float w11 = xi + yi - 1.0f, w10 = 1.0f - yi, w01 = 1.0f - xi;
-                    int da, db;
-                    if (w11 <= w10 && w11 <= w01) { da = 0; db = 0; }
-                    else if (w10 <= w01) { da = 0; db = 2; }
-                    else { da = 2; db = 0; }
-                    h += vertex_at(a, b, da, db, key, xi, yi);
-                }
-                acc[r][c] = fmaf(amp, h, acc[r][c]);
-            }
-        }
+        if (P.box_wb[i] > 0) simplex_octave<true>(acc, P, tile[i], boxes, i, tx, ty);
+        else simplex_octave<false>(acc, P, tile[i], boxes, i, tx, ty);
     }
     OutT* out = reinterpret_cast<OutT*>(P.out);
     const int x0 = j0x + tx * kCols, y0 = j0y + ty * kRows;
@@ -173,8 +247,18 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
 cudaError_t launch_opensimplex2d(const SimplexPlan& P, cudaStream_t stream)
 {
     const dim3 grid(P.tiles_x, P.tiles_y, 1);
-    if (P.dtype == 1) opensimplex2d_kernel<__half><<<grid, kThreads, 0, stream>>>(P);
-    else opensimplex2d_kernel<float><<<grid, kThreads, 0, stream>>>(P);
+    const size_t smem = sizeof(float2) * (size_t)P.box_words;
+    if (P.dtype == 1) {
+        cudaError_t e = cudaFuncSetAttribute(opensimplex2d_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        opensimplex2d_kernel<__half><<<grid, kThreads, smem, stream>>>(P);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(opensimplex2d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        opensimplex2d_kernel<float><<<grid, kThreads, smem, stream>>>(P);
+    }
     return cudaGetLastError();
 }
 
