@@ -456,12 +456,18 @@ def main():
         d16 = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, smoothness=P.PTG_C1, seed=0,
                           dtype=P.PTG_F16)
         dP = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, seed=0, variant=P.PTG_PERLIN_S5)
+        dZ = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, smoothness=P.PTG_ZERO_GRADIENT, seed=0)
+        dG = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, smoothness=P.PTG_PAPER_D2M1N3, seed=0)
         extras["c2_f32"] = time_fn(lambda o: P.ptg_field(ctx, dC2, o, stream))
         extras["c1_f16"] = time_fn(lambda o: P.ptg_field(ctx, d16, o, stream), torch.float16)
         extras["perlin_s5_f32"] = time_fn(lambda o: P.ptg_perlin(ctx, dP, o, stream))
+        extras["zero_gradient_f32"] = time_fn(lambda o: P.ptg_field(ctx, dZ, o, stream))
+        extras["paper_d2m1n3_f32"] = time_fn(lambda o: P.ptg_field(ctx, dG, o, stream))
         extras["opensimplex_f32"] = time_fn(lambda o: P.ptg_opensimplex(ctx, dP, o, stream), reps=5)
         for k, v in extras.items():
             v["ops_per_sample"] = R.lane_ops_2d({"c2_f32": "c2", "c1_f16": "c1", "perlin_s5_f32": "perlin_s5",
+                                                 "zero_gradient_f32": "zero_grad",
+                                                 "paper_d2m1n3_f32": "paper_gauge",
                                                  "opensimplex_f32": "opensimplex"}[k], SIZE, SPC,
                                                 OCTAVES)["per_sample"]
         line["baselines"] = extras

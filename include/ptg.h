@@ -63,7 +63,16 @@ typedef enum {
     PTG_ERR_CANCELLED = -7
 } ptg_status;
 
-typedef enum { PTG_C1 = 1, PTG_C2 = 2 } ptg_smoothness;
+/* Cell polynomial (Sec. 3).  PTG_C1 and PTG_C2 are the smooth cells of the
+ * header comment (2D and 3D).  The two 2D-only models of the paper:
+ *   PTG_PAPER_D2M1N3  -- D2M1N3 with the coefficients printed in Sec. 3.1
+ *                        (c22 = c33 = c32 = c23 = 0); continuous across cell
+ *                        faces, its slope is not;
+ *   PTG_ZERO_GRADIENT -- zero-gradient D2M1N3, Eq. (zg), read with the -xy
+ *                        term that the Sec. 3.1 coefficients give (the
+ *                        printed +xy does not interpolate h11); corner
+ *                        values only (words 1.. unused). */
+typedef enum { PTG_C1 = 1, PTG_C2 = 2, PTG_PAPER_D2M1N3 = 3, PTG_ZERO_GRADIENT = 4 } ptg_smoothness;
 
 typedef enum { PTG_F32 = 0, PTG_F16 = 1 } ptg_dtype;
 
@@ -110,7 +119,8 @@ int ptg_heightmap2d(ptg_ctx* ctx, const int64_t size[2], int32_t octaves, int32_
 int ptg_volume3d(ptg_ctx* ctx, const int64_t size[3], int32_t octaves, int32_t smoothness,
                  float persistence, float lacunarity, uint32_t seed, void* out, void* stream);
 
-/* Polynomial-noise field from a full descriptor (C1 or C2, 2D or 3D). */
+/* Polynomial-noise field from a full descriptor (any ptg_smoothness; C1 and C2
+ * in 2D or 3D, the paper's D2M1N3 and zero-gradient models in 2D). */
 int ptg_field(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, void* stream);
 
 /* Perlin's polynomial (Sec. 3.2) with the same lattice, hash words 1..2 as

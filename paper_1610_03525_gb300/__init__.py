@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libptg.so")
 PTG_OK, PTG_PENDING = 0, 1
 PTG_ERR_INVALID, PTG_ERR_UNSUPPORTED, PTG_ERR_NOMEM, PTG_ERR_BUDGET = -1, -2, -3, -4
 PTG_ERR_CUDA, PTG_ERR_TIMEOUT, PTG_ERR_CANCELLED = -5, -6, -7
-PTG_C1, PTG_C2 = 1, 2
+PTG_C1, PTG_C2, PTG_PAPER_D2M1N3, PTG_ZERO_GRADIENT = 1, 2, 3, 4
 PTG_F32, PTG_F16 = 0, 1
 PTG_PERLIN_S5, PTG_PERLIN_S3 = 0, 1
 METHOD_FIELD, METHOD_PERLIN, METHOD_OPENSIMPLEX = 0, 1, 2

@@ -70,8 +70,10 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
     }
     if (d->octaves < 1 || d->octaves > kMaxOctaves)
         return ptg_fail(ctx, PTG_ERR_INVALID, "octaves %d out of [1, 32]", d->octaves);
-    if (kind == kKindField && d->smoothness != PTG_C1 && d->smoothness != PTG_C2)
-        return ptg_fail(ctx, PTG_ERR_INVALID, "smoothness must be PTG_C1 or PTG_C2");
+    if (kind == kKindField && (d->smoothness < PTG_C1 || d->smoothness > PTG_ZERO_GRADIENT))
+        return ptg_fail(ctx, PTG_ERR_INVALID, "smoothness must be a ptg_smoothness value");
+    if (kind == kKindField && d->dims == 3 && d->smoothness != PTG_C1 && d->smoothness != PTG_C2)
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "the paper's D2M1N3 and zero-gradient models are 2D");
     if (kind == kKindPerlin && d->variant != PTG_PERLIN_S5 && d->variant != PTG_PERLIN_S3)
         return ptg_fail(ctx, PTG_ERR_INVALID, "Perlin variant must be PTG_PERLIN_S5 or PTG_PERLIN_S3");
     if (!std::isfinite(d->persistence) || !std::isfinite(d->grad_weight))
@@ -210,7 +212,12 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
 int ptg_kernel_method(int kind, const ptg_field_desc* d)
 {
     if (kind == kKindPerlin) return d->variant == PTG_PERLIN_S3 ? kPerlinS3 : kPerlinS5;
-    return d->smoothness == PTG_C2 ? kC2 : kC1;
+    switch (d->smoothness) {
+    case PTG_C2: return kC2;
+    case PTG_PAPER_D2M1N3: return kPaperGauge;
+    case PTG_ZERO_GRADIENT: return kZeroGrad;
+    default: return kC1;
+    }
 }
 
 int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void* out, int64_t band_start,

@@ -12,10 +12,12 @@ namespace ptg {
 
 // Method codes of the generator kernels.
 enum : int {
-    kC1 = 1,        // D?M1N3, zero twist: tensor cubic Hermite (Sec. 3.1, 3.4)
-    kC2 = 2,        // D?M2N5, zero 2nd derivatives: tensor quintic Hermite (Sec. 3.4)
-    kPerlinS5 = 10, // Perlin's polynomial, smootherstep blend (Sec. 3.2, 5.1)
-    kPerlinS3 = 11  // Perlin's polynomial, smoothstep blend (Sec. 3.2)
+    kC1 = 1,          // D?M1N3, zero twist: tensor cubic Hermite (Sec. 3.1, 3.4)
+    kC2 = 2,          // D?M2N5, zero 2nd derivatives: tensor quintic Hermite (Sec. 3.4)
+    kPaperGauge = 3,  // D2M1N3 with the printed coefficients (Sec. 3.1), C0 across faces
+    kZeroGrad = 4,    // zero-gradient D2M1N3 (Eq. zg with the -xy term), C0 across faces
+    kPerlinS5 = 10,   // Perlin's polynomial, smootherstep blend (Sec. 3.2, 5.1)
+    kPerlinS3 = 11    // Perlin's polynomial, smoothstep blend (Sec. 3.2)
 };
 
 // Octave modes.  A staged octave (cells at least two samples wide) keeps the
@@ -134,12 +136,17 @@ __device__ __forceinline__ float unit_value(uint32_t u)
 //       gradient f_0b multiplies (1-S) x and f_1b multiplies S (x-1):
 //       B0 = (1-S) t, B1 = S (t-1); the corner value is zero.
 // ---------------------------------------------------------------------------
+//   Zero-gradient (Eq. zg): (S3, t); the paper's D2M1N3: t (monomials).
 template <int METHOD>
 __device__ __forceinline__ float4 axis_basis(float t)
 {
     const float t2 = t * t;
     const float u = t - 1.0f;
-    if (METHOD == kC1) {
+    if (METHOD == kZeroGrad) {
+        return make_float4(t2 * fmaf(-2.0f, t, 3.0f), t, 0.0f, 0.0f);
+    } else if (METHOD == kPaperGauge) {
+        return make_float4(t, 0.0f, 0.0f, 0.0f);
+    } else if (METHOD == kC1) {
         const float S = t2 * fmaf(-2.0f, t, 3.0f);
         return make_float4(S, t * u * u, t2 * u, 0.0f);
     } else if (METHOD == kC2) {

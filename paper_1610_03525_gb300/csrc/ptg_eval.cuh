@@ -19,7 +19,8 @@ namespace ptg {
 // Degree along x of one cell row, per method.
 template <int METHOD>
 struct Deg {
-    static constexpr int value = METHOD == kC1 ? 3 : METHOD == kC2 ? 5 : METHOD == kPerlinS3 ? 4 : 6;
+    static constexpr int value = (METHOD == kC1 || METHOD == kPaperGauge || METHOD == kZeroGrad) ? 3
+                               : METHOD == kC2 ? 5 : METHOD == kPerlinS3 ? 4 : 6;
 };
 
 // Node columns of the run8 evaluation for degree D (d + 1 of the 8 columns,
@@ -97,5 +98,101 @@ __device__ __forceinline__ float eval_row(const Row& r, float Sx, float B0x, flo
     return fmaf(B1x, r.F1, fmaf(B0x, r.F0, fmaf(Sx, r.dV, r.V0)));
 }
 
+
+// Per-method cell model: the row collapse at a y-basis entry, the row at
+// t_y = 0, and the evaluation of a collapsed row at an x-basis entry.
+template <int METHOD>
+struct Model {  // tensor-product Hermite cells (C1, C2) and Perlin
+    __device__ static __forceinline__ Row row(const Cell& c, float4 yb) { return row_of(c, yb.x, yb.y, yb.z); }
+    __device__ static __forceinline__ Row row0(const Cell& c) { return row_at_zero(c); }
+    __device__ static __forceinline__ float eval(const Row& r, float4 xb) { return eval_row(r, xb.x, xb.y, xb.z); }
+};
+
+// Zero-gradient D2M1N3 (Eq. zg with -xy): for a row at height y,
+//   h(x) = [h00 + S3(y) dy] + S3(x) [dx + A y] + x [A (S3(y) - y)],
+// dx = h10 - h00, dy = h01 - h00, A = h11 + h00 - h10 - h01.
+// Row fields: V0, dV, F0 = the x coefficient; basis entries (S3, t).
+template <>
+struct Model<kZeroGrad> {
+    __device__ static __forceinline__ Row row(const Cell& c, float4 yb)
+    {
+        const float dx = c.c10.x - c.c00.x, dy = c.c01.x - c.c00.x;
+        const float A = (c.c11.x - c.c01.x) - dx;
+        Row r;
+        r.V0 = fmaf(yb.x, dy, c.c00.x);
+        r.dV = fmaf(A, yb.y, dx);
+        r.F0 = A * (yb.x - yb.y);
+        r.F1 = 0.0f;
+        return r;
+    }
+    __device__ static __forceinline__ Row row0(const Cell& c)
+    {
+        Row r;
+        r.V0 = c.c00.x;
+        r.dV = c.c10.x - c.c00.x;
+        r.F0 = 0.0f;
+        r.F1 = 0.0f;
+        return r;
+    }
+    __device__ static __forceinline__ float eval(const Row& r, float4 xb) { return fmaf(xb.y, r.F0, fmaf(xb.x, r.dV, r.V0)); }
+};
+
+// The D2M1N3 polynomial with the coefficients printed in Sec. 3.1
+// (c22 = c33 = c32 = c23 = 0; c_ji from c_ij by swapping indices and f <-> g).
+// For a row at height y it is the cubic a0 + a1 x + a2 x^2 + a3 x^3 with
+// a_i = sum_j c_ij y^j.  Row fields: V0..F1 = a0..a3; basis entries (t).
+template <>
+struct Model<kPaperGauge> {
+    struct Coef {
+        float c00, c10, c01, c20, c30, c02, c03, c21, c31, c12, c13, c11;
+    };
+    __device__ static __forceinline__ Coef coef(const Cell& c)
+    {
+        const float h00 = c.c00.x, h10 = c.c10.x, h01 = c.c01.x, h11 = c.c11.x;
+        const float f00 = c.c00.y, f10 = c.c10.y, f01 = c.c01.y, f11 = c.c11.y;
+        const float g00 = c.c00.z, g10 = c.c10.z, g01 = c.c01.z, g11 = c.c11.z;
+        Coef k;
+        k.c00 = h00;
+        k.c10 = f00;
+        k.c01 = g00;
+        const float dx0 = h10 - h00, dy0 = h01 - h00, dx1 = h11 - h01, dy1 = h11 - h10;
+        k.c20 = fmaf(3.0f, dx0, -fmaf(2.0f, f00, f10));
+        k.c30 = fmaf(-2.0f, dx0, f10 + f00);
+        k.c02 = fmaf(3.0f, dy0, -fmaf(2.0f, g00, g01));
+        k.c03 = fmaf(-2.0f, dy0, g01 + g00);
+        k.c21 = fmaf(3.0f, dx1, -fmaf(2.0f, f01, f11)) - k.c20;
+        k.c31 = fmaf(-2.0f, dx1, f11 + f01) - k.c30;
+        k.c12 = fmaf(3.0f, dy1, -fmaf(2.0f, g10, g11)) - k.c02;
+        k.c13 = fmaf(-2.0f, dy1, g11 + g10) - k.c03;
+        k.c11 = ((h01 + h10) - (h00 + h11)) + ((f01 - f00) + (g10 - g00));
+        return k;
+    }
+    __device__ static __forceinline__ Row row(const Cell& c, float4 yb)
+    {
+        const Coef k = coef(c);
+        const float y = yb.x;
+        Row r;
+        r.V0 = fmaf(y, fmaf(y, fmaf(y, k.c03, k.c02), k.c01), k.c00);
+        r.dV = fmaf(y, fmaf(y, fmaf(y, k.c13, k.c12), k.c11), k.c10);
+        r.F0 = fmaf(y, k.c21, k.c20);
+        r.F1 = fmaf(y, k.c31, k.c30);
+        return r;
+    }
+    __device__ static __forceinline__ Row row0(const Cell& c)
+    {
+        const Coef k = coef(c);
+        Row r;
+        r.V0 = k.c00;
+        r.dV = k.c10;
+        r.F0 = k.c20;
+        r.F1 = k.c30;
+        return r;
+    }
+    __device__ static __forceinline__ float eval(const Row& r, float4 xb)
+    {
+        const float t = xb.x;
+        return fmaf(t, fmaf(t, fmaf(t, r.F1, r.F0), r.dV), r.V0);
+    }
+};
 
 }  // namespace ptg

@@ -93,7 +93,9 @@ __device__ __forceinline__ void stage_tile(const FieldPlan& P, float4* sm, int j
             uint32_t x = bx + (uint32_t)cx, y = by + (uint32_t)cy, z = op.key;
             pcg3d(x, y, z);
             float4 c;
-            if (METHOD == kC1 || METHOD == kC2)
+            if (METHOD == kZeroGrad)  // corner values only (Eq. zg has zero gradients)
+                c = make_float4(unit_value(x) * op.amp, 0.0f, 0.0f, 0.0f);
+            else if (METHOD == kC1 || METHOD == kC2 || METHOD == kPaperGauge)
                 c = make_float4(unit_value(x) * op.amp, unit_value(y) * op.ampw, unit_value(z) * op.ampw, 0.0f);
             else
                 c = make_float4(0.0f, unit_value(y) * op.amp, unit_value(z) * op.amp, 0.0f);
@@ -132,9 +134,9 @@ __device__ __forceinline__ void run8_octave(float (&nacc)[kRows][Deg<METHOD>::va
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
         const float4 yb = ylut[i * 64 + r * 16 + ty];
-        const Row R = row_of(c, yb.x, yb.y, yb.z);
+        const Row R = Model<METHOD>::row(c, yb);
 #pragma unroll
-        for (int q = 0; q < NN; ++q) nacc[r][q] += eval_row(R, xb[q].x, xb[q].y, xb[q].z);
+        for (int q = 0; q < NN; ++q) nacc[r][q] += Model<METHOD>::eval(R, xb[q]);
     }
 }
 
@@ -156,22 +158,10 @@ __device__ __forceinline__ void small_octave(float (&acc)[kRows][kCols], const f
             const Cell c = load_cell(cg, op.rowlen, lcx, lcy);
 #pragma unroll
             for (int rr = 0; rr < CW; ++rr) {
-                Row R;
-                if (rr == 0) {
-                    R = row_at_zero(c);
-                } else {
-                    const float4 yb = axis_basis<METHOD>(rr * inv);
-                    R = row_of(c, yb.x, yb.y, yb.z);
-                }
+                const Row R = rr == 0 ? Model<METHOD>::row0(c) : Model<METHOD>::row(c, axis_basis<METHOD>(rr * inv));
 #pragma unroll
                 for (int q = 0; q < CW; ++q) {
-                    float h;
-                    if (q == 0) {
-                        h = R.V0;
-                    } else {
-                        const float4 xb = axis_basis<METHOD>(q * inv);
-                        h = eval_row(R, xb.x, xb.y, xb.z);
-                    }
+                    const float h = q == 0 ? R.V0 : Model<METHOD>::eval(R, axis_basis<METHOD>(q * inv));
                     acc[yq * CW + rr][xq * CW + q] += h;
                 }
             }
@@ -261,7 +251,7 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     // cells of 4 and 2 samples, then lattice octaves
     if (s >= 2 && s - 2 < N) small_octave<METHOD, 4>(acc, sm, P, s - 2, tx, ty, n8);
     if (s >= 1 && s - 1 < N) small_octave<METHOD, 2>(acc, sm, P, s - 1, tx, ty, n8);
-    if (METHOD == kC1 || METHOD == kC2)
+    if (METHOD != kPerlinS5 && METHOD != kPerlinS3)
         for (int i = s; i < N; ++i)
             lattice_octave(acc, P.oct[i], (uint32_t)(j0x + tx * kCols), (uint32_t)(j0y + ty * kRows));
     store_tile<OutT>(P, acc, x0 + tx * kCols, y0 + ty * kRows);
@@ -325,6 +315,14 @@ __global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* 
             if (f16) fbm2d_tile<kC2, __half>(plan, sm, bx, by);
             else fbm2d_tile<kC2, float>(plan, sm, bx, by);
             break;
+        case kPaperGauge:
+            if (f16) fbm2d_tile<kPaperGauge, __half>(plan, sm, bx, by);
+            else fbm2d_tile<kPaperGauge, float>(plan, sm, bx, by);
+            break;
+        case kZeroGrad:
+            if (f16) fbm2d_tile<kZeroGrad, __half>(plan, sm, bx, by);
+            else fbm2d_tile<kZeroGrad, float>(plan, sm, bx, by);
+            break;
         case kPerlinS5:
             if (f16) fbm2d_tile<kPerlinS5, __half>(plan, sm, bx, by);
             else fbm2d_tile<kPerlinS5, float>(plan, sm, bx, by);
@@ -363,6 +361,8 @@ size_t fbm2d_smem_bytes(const FieldPlan& P)
     switch (P.method) {
     case kC1: w = smem_words<kC1>(P); break;
     case kC2: w = smem_words<kC2>(P); break;
+    case kPaperGauge: w = smem_words<kPaperGauge>(P); break;
+    case kZeroGrad: w = smem_words<kZeroGrad>(P); break;
     case kPerlinS5: w = smem_words<kPerlinS5>(P); break;
     default: w = smem_words<kPerlinS3>(P); break;
     }
@@ -385,6 +385,8 @@ cudaError_t launch_fbm2d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
     switch (method) {
     case kC1: if (f16) PTG_LAUNCH2D(kC1, __half); else PTG_LAUNCH2D(kC1, float);
     case kC2: if (f16) PTG_LAUNCH2D(kC2, __half); else PTG_LAUNCH2D(kC2, float);
+    case kPaperGauge: if (f16) PTG_LAUNCH2D(kPaperGauge, __half); else PTG_LAUNCH2D(kPaperGauge, float);
+    case kZeroGrad: if (f16) PTG_LAUNCH2D(kZeroGrad, __half); else PTG_LAUNCH2D(kZeroGrad, float);
     case kPerlinS5: if (f16) PTG_LAUNCH2D(kPerlinS5, __half); else PTG_LAUNCH2D(kPerlinS5, float);
     case kPerlinS3: if (f16) PTG_LAUNCH2D(kPerlinS3, __half); else PTG_LAUNCH2D(kPerlinS3, float);
     default: return cudaErrorInvalidValue;

@@ -19,8 +19,11 @@ are at least 8 samples wide:
   cells >= 8 samples, per thread and octave: 4 (y differences) + 4 rows x
                 (9 row reduction + 4 (d+1) at the node columns); once per
                 thread, 4 rows x (7 - d) columns x (d+1) FMA of interpolation;
-  cells of 4 samples, per thread: 2 cells x 32 + 24 samples x 4 + 8 x 1;
-  cells of 2 samples, per thread: 8 cells x (14 + 10);
+  cells of 4 samples, per thread: 2 cells x (prep + 3 rows + 1) + 24 samples
+                x eval + 8 x 1; cells of 2: 8 cells x (prep + row + 1 + 2 eval + 2),
+                with (prep, row, eval) = (4, 9, 4) for the Hermite cells and
+                Perlin, (4, 4, 3) for the zero-gradient model and (25, 8, 4)
+                for the paper's D2M1N3 coefficients;
   lattice octave: per sample 19 (pcg3d word 0: 13, word->float 3, FMA 1,
                 coordinate 2); Perlin's lattice octaves are zero, no work.
 3D tiles of 32 x 16 x 8 (each thread 8 x 4 x 1): the same regimes, with a
@@ -31,7 +34,7 @@ OpenSimplex-style: per sample and octave 150 (4 vertices x 33 + 18).
 """
 from __future__ import annotations
 
-BASIS_OPS = {"c1": 7, "c2": 14, "perlin_s5": 9, "perlin_s3": 8}
+BASIS_OPS = {"c1": 7, "c2": 14, "perlin_s5": 9, "perlin_s3": 8, "zero_grad": 4, "paper_gauge": 0}
 COORD_OPS = 5
 
 
@@ -41,7 +44,10 @@ def _staged(spc: int, octaves: int):
     return [(i, spc >> i) for i in range(min(octaves, s))]
 
 
-DEG = {"c1": 3, "c2": 5, "perlin_s3": 4, "perlin_s5": 6}
+DEG = {"c1": 3, "c2": 5, "perlin_s3": 4, "perlin_s5": 6, "paper_gauge": 3, "zero_grad": 3}
+# (cell preparation, row collapse, per-sample evaluation) operations per model
+MODEL_OPS = {"c1": (4, 9, 4), "c2": (4, 9, 4), "perlin_s3": (4, 9, 4), "perlin_s5": (4, 9, 4),
+             "zero_grad": (4, 4, 3), "paper_gauge": (25, 8, 4)}
 
 
 def lane_ops_2d(kind: str, size, spc: int, octaves: int) -> dict:
@@ -58,16 +64,17 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int) -> dict:
     lut = tiles * n8 * (8 * (d + 1) + 64) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
     evalops = threads * 4 * (7 - d) * (d + 1)
+    prep, row, smp = MODEL_OPS[kind]
     for i, spci in st:
         k = spci.bit_length() - 1
         ncx = (63 >> min(k, 31)) + 2
-        corners += tiles * ncx * ncx * 31
+        corners += tiles * ncx * ncx * (19 if kind == "zero_grad" else 31)
         if spci >= 8:
-            evalops += threads * (4 + 4 * (9 + 4 * (d + 1)))
+            evalops += threads * (prep + 4 * (row + smp * (d + 1)))
         elif spci == 4:
-            evalops += threads * (2 * 32 + 24 * 4 + 8)
+            evalops += threads * (2 * (prep + 3 * row + 1) + 24 * smp + 8)
         else:
-            evalops += threads * 8 * (14 + 10)
+            evalops += threads * 8 * (prep + row + 1 + 2 * smp + 2)
     n_lattice = octaves - len(st)
     lattice = 0 if kind.startswith("perlin") else samples_padded * n_lattice * 19
     tot = lut + corners + evalops + lattice

@@ -54,7 +54,9 @@ def test_desc_layout_matches_header(P):
     (dict(size=(5, 5), spc=3), 0, -2),
     (dict(octaves=0), 0, -1),
     (dict(octaves=33), 0, -1),
-    (dict(smoothness=3), 0, -1),
+    (dict(smoothness=5), 0, -1),
+    (dict(smoothness=3), 0, 0),
+    (dict(smoothness=4, dims=3, size=(32, 32, 32)), 0, -2),
     (dict(lacunarity=3.0), 0, -2),
     (dict(seed=1 << 24), 0, -1),
     (dict(dtype=7), 0, -1),

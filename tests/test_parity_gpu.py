@@ -18,7 +18,8 @@ from paper_1610_03525_gb300 import workloads as W  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 KIND_ORACLE = {"c1": O.C1, "c2": O.C2, "perlin_s5": O.PERLIN_S5, "perlin_s3": O.PERLIN_S3,
-               "opensimplex": O.OPENSIMPLEX}
+               "opensimplex": O.OPENSIMPLEX, "paper_gauge": O.PAPER_GAUGE, "zero_grad": O.ZERO_GRAD}
+SMOOTH = {"c2": P.PTG_C2, "paper_gauge": P.PTG_PAPER_D2M1N3, "zero_grad": P.PTG_ZERO_GRADIENT}
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +35,7 @@ def ctx():
 
 def gpu_field(ctx, kind, dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 0, 0), offset=(0, 0, 0),
               seed=0, persistence=0.5, grad_weight=1.0, dtype=P.PTG_F32):
-    smooth = P.PTG_C2 if kind == "c2" else P.PTG_C1
+    smooth = SMOOTH.get(kind, P.PTG_C1)
     variant = P.PTG_PERLIN_S3 if kind == "perlin_s3" else P.PTG_PERLIN_S5
     d = P.make_desc(dims=dims, size=size, spc=spc, origin=origin, offset=offset, octaves=octaves,
                     smoothness=smooth, persistence=persistence, grad_weight=grad_weight, seed=seed, dtype=dtype,
@@ -42,7 +43,7 @@ def gpu_field(ctx, kind, dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 
     shape = tuple(reversed(size[:dims]))
     out = torch.full(shape, float("nan"), dtype=torch.float16 if dtype == P.PTG_F16 else torch.float32,
                      device="cuda")
-    if kind in ("c1", "c2"):
+    if kind in ("c1", "c2", "paper_gauge", "zero_grad"):
         P.ptg_field(ctx, d, out)
     elif kind.startswith("perlin"):
         P.ptg_perlin(ctx, d, out)
@@ -134,7 +135,7 @@ def test_lattice_octaves_are_exact_corner_values(ctx):
 # ---------------------------------------------------------------------------
 # full-field parity, 256^2 6-octave configuration and every method
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3", "opensimplex"])
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3", "opensimplex", "paper_gauge", "zero_grad"])
 def test_cfg1_full_field(ctx, kind):
     cfg = W.CONFIGS["cfg1_2d_256_c1_n6"]
     out = gpu_field(ctx, kind, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"], seed=0)
@@ -153,7 +154,7 @@ def test_cfg1_fp16_output(ctx, kind):
     assert np.all(err <= tol32(6) + half_ulp16(ref))
 
 
-@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "opensimplex"])
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "opensimplex", "paper_gauge", "zero_grad"])
 @pytest.mark.parametrize("size,spc,octaves", [
     ((1, 1), 1, 1), ((3, 5), 1, 4), ((17, 13), 2, 3), ((200, 136), 8, 7), ((65, 130), 32, 9),
     ((64, 64), 64, 1), ((129, 3), 4, 32),
@@ -198,7 +199,8 @@ def test_3d_ragged(ctx):
 # full-size configurations in the benchmark's launch configuration, sampled
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kind,seed,dtype", [("c1", 0, P.PTG_F32), ("c2", 3, P.PTG_F32), ("c1", 1, P.PTG_F16),
-                                             ("perlin_s5", 2, P.PTG_F32), ("opensimplex", 0, P.PTG_F32)])
+                                             ("perlin_s5", 2, P.PTG_F32), ("opensimplex", 0, P.PTG_F32),
+                                             ("paper_gauge", 1, P.PTG_F32), ("zero_grad", 2, P.PTG_F32)])
 def test_cfg2_sampled(ctx, kind, seed, dtype):
     cfg = W.CONFIGS["cfg2_2d_8192_n12"]
     out = gpu_field(ctx, kind, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"], seed=seed, dtype=dtype)
@@ -225,7 +227,7 @@ def test_cfg3_sampled(ctx):
 # ---------------------------------------------------------------------------
 # locality (Sec. 1): windows tile the world exactly; determinism; host path
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5"])
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "paper_gauge", "zero_grad"])
 def test_chunk_mosaic_bit_exact(ctx, kind):
     big = gpu_field(ctx, kind, size=(512, 384), spc=128, octaves=9, origin=(11, -4, 0), seed=8)
     for oy in (0, 192):
