@@ -190,6 +190,33 @@ def bench_3d(P, R, ctx, stream, torch, reps=10):
                                                                2070.0)}
 
 
+def bench_octave_sweep(P, ctx, stream, torch, octaves=(1, 2, 4, 6, 8, 10, 12), reps=5):
+    """Time per 8192^2 field against the octave count N (spc 1024: octaves
+    10 and 11 sit on lattice points), per method -- the GPU counterpart of the
+    paper's execution time against N at fixed resolution (Sec. 5.2)."""
+    out = torch.empty((SIZE[1], SIZE[0]), dtype=torch.float32, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, fn, kw in [("c1", P.ptg_field, dict(smoothness=P.PTG_C1)),
+                         ("zero_gradient", P.ptg_field, dict(smoothness=P.PTG_ZERO_GRADIENT)),
+                         ("perlin_s5", P.ptg_perlin, dict()),
+                         ("opensimplex", P.ptg_opensimplex, dict())]:
+        row = {}
+        for n in octaves:
+            d = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=n, seed=0, **kw)
+            fn(ctx, d, out, stream)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(reps):
+                fn(ctx, d, out, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            row[str(n)] = round(a.elapsed_time(b) / reps, 4)
+        res[name + "_ms"] = row
+    del out
+    return res
+
+
 def bench_batched(P, ctx, stream, torch, n_chunks=4096, reps=5):
     """4096 2D chunks (side 64..1024, octaves 4..12, C1/C2) in one persistent
     launch replayed from a CUDA graph, against one ptg_field launch per chunk."""
@@ -473,6 +500,7 @@ def main():
         line["baselines"] = extras
         if rank == 0:
             line["config3_3d"] = bench_3d(P, R, ctx, stream, torch)
+            line["octave_sweep"] = bench_octave_sweep(P, ctx, stream, torch)
             line["batched"] = bench_batched(P, ctx, stream, torch)
             line["serving"] = bench_serving(P, torch, duration_s=args.serve_seconds)
 
