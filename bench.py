@@ -499,7 +499,7 @@ def main():
                                                 OCTAVES)["per_sample"]
         line["baselines"] = extras
         if rank == 0:
-            line["config3_3d"] = bench_3d(P, R, ctx, stream, torch)
+            line["volume3d_512_n8"] = bench_3d(P, R, ctx, stream, torch)
             line["octave_sweep"] = bench_octave_sweep(P, ctx, stream, torch)
             line["batched"] = bench_batched(P, ctx, stream, torch)
             line["serving"] = bench_serving(P, torch, duration_s=args.serve_seconds)

@@ -16,12 +16,12 @@ import numpy as np
 # name -> dict(dims, size, spc, octaves, smoothness, origin, dtype(s), seeds)
 CONFIGS = {
     # 2D 256^2, C1, 6 octaves, base lattice 4x4 (spc 64), seed 0, FP32
-    "cfg1_2d_256_c1_n6": dict(dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 0, 0), seeds=(0,)),
+    "2d_256_c1_n6": dict(dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 0, 0), seeds=(0,)),
     # 2D 8192^2, 12 octaves, base lattice 8x8 (spc 1024), C1/C2, seeds 0..3
-    "cfg2_2d_8192_n12": dict(dims=2, size=(8192, 8192), spc=1024, octaves=12, origin=(0, 0, 0),
+    "2d_8192_n12": dict(dims=2, size=(8192, 8192), spc=1024, octaves=12, origin=(0, 0, 0),
                              seeds=(0, 1, 2, 3)),
     # 3D 512^3, 8 octaves, base lattice 4^3 (spc 128), C1, FP16, world offset
-    "cfg3_3d_512_n8": dict(dims=3, size=(512, 512, 512), spc=128, octaves=8, origin=(1 << 20, 1 << 20, 0),
+    "3d_512_n8": dict(dims=3, size=(512, 512, 512), spc=128, octaves=8, origin=(1 << 20, 1 << 20, 0),
                            seeds=(0,)),
 }
 

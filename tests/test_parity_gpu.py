@@ -136,8 +136,8 @@ def test_lattice_octaves_are_exact_corner_values(ctx):
 # full-field parity, 256^2 6-octave configuration and every method
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3", "opensimplex", "paper_gauge", "zero_grad"])
-def test_cfg1_full_field(ctx, kind):
-    cfg = W.CONFIGS["cfg1_2d_256_c1_n6"]
+def test_full_field_256(ctx, kind):
+    cfg = W.CONFIGS["2d_256_c1_n6"]
     out = gpu_field(ctx, kind, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"], seed=0)
     idx = W.grid_indices_2d(*cfg["size"])
     ref = oracle_at(kind, idx, spc=cfg["spc"], octaves=cfg["octaves"], seed=0)
@@ -146,7 +146,7 @@ def test_cfg1_full_field(ctx, kind):
 
 
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "opensimplex"])
-def test_cfg1_fp16_output(ctx, kind):
+def test_fp16_output_256(ctx, kind):
     out = gpu_field(ctx, kind, size=(256, 256), spc=64, octaves=6, seed=0, dtype=P.PTG_F16)
     idx = W.grid_indices_2d(256, 256)
     ref = oracle_at(kind, idx, spc=64, octaves=6, seed=0)
@@ -201,8 +201,8 @@ def test_3d_ragged(ctx):
 @pytest.mark.parametrize("kind,seed,dtype", [("c1", 0, P.PTG_F32), ("c2", 3, P.PTG_F32), ("c1", 1, P.PTG_F16),
                                              ("perlin_s5", 2, P.PTG_F32), ("opensimplex", 0, P.PTG_F32),
                                              ("paper_gauge", 1, P.PTG_F32), ("zero_grad", 2, P.PTG_F32)])
-def test_cfg2_sampled(ctx, kind, seed, dtype):
-    cfg = W.CONFIGS["cfg2_2d_8192_n12"]
+def test_sampled_8192_n12(ctx, kind, seed, dtype):
+    cfg = W.CONFIGS["2d_8192_n12"]
     out = gpu_field(ctx, kind, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"], seed=seed, dtype=dtype)
     idx = W.subsample(cfg["size"], every=1024, n_random=1 << 15, seed=seed)
     ref = oracle_at(kind, idx, spc=cfg["spc"], octaves=cfg["octaves"], seed=seed)
@@ -214,8 +214,8 @@ def test_cfg2_sampled(ctx, kind, seed, dtype):
         assert float(out.float().abs().max()) <= 1.5 * W.total_amplitude(12) + 1e-5
 
 
-def test_cfg3_sampled(ctx):
-    cfg = W.CONFIGS["cfg3_3d_512_n8"]
+def test_sampled_3d_512_n8(ctx):
+    cfg = W.CONFIGS["3d_512_n8"]
     out = gpu_field(ctx, "c1", dims=3, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"],
                     origin=cfg["origin"], seed=0, dtype=P.PTG_F16)
     idx = W.subsample(cfg["size"], every=256, n_random=1 << 15, seed=1)
