@@ -134,7 +134,7 @@ def profile_traffic():
     if not os.path.exists(path):
         return None
     h = hashlib.sha256()
-    for f in ("ptg_fbm2d.cu", "ptg_device.cuh"):
+    for f in ("ptg_fbm2d.cu", "ptg_device.cuh", "ptg_eval.cuh"):
         with open(os.path.join(ROOT, "paper_1610_03525_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     src = h.hexdigest()[:16]
@@ -228,6 +228,11 @@ def bench_batched(P, ctx, stream, torch, n_chunks=4096, reps=5):
                                  smoothness=c["smoothness"], seed=c["seed"]))
         outs.append(torch.empty((c["size"][1], c["size"][0]), dtype=torch.float32, device="cuda"))
     n_samples = sum(c["size"][0] * c["size"][1] for c in chunks)
+    shapes = {}
+    for d in descs:
+        rw = P.ptg_thread_shape(ctx, d)
+        key = "%dx%d" % (rw, 32 // rw)
+        shapes[key] = shapes.get(key, 0) + 1
     plan = P.ptg_batch_prepare(ctx, descs, outs)
     for _ in range(2):
         P.ptg_batch_launch(plan, stream)
@@ -257,7 +262,7 @@ def bench_batched(P, ctx, stream, torch, n_chunks=4096, reps=5):
     del outs
     return {"workload": "%d 2D chunks, side log-uniform 64..1024, octaves 4..12, C1/C2 50/50, spc 1024, "
                         "seeds = chunk id, origins uniform in +-2^20 cells, FP32 out" % n_chunks,
-            "samples": n_samples,
+            "samples": n_samples, "thread_shapes": shapes,
             "batched_graph_ms": ms_batch, "batched_gsamples_s": n_samples / ms_batch / 1e6,
             "per_chunk_launches_ms": ms_single, "per_chunk_gsamples_s": n_samples / ms_single / 1e6,
             "per_chunk_host_wall_ms": wall_single,
@@ -366,6 +371,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=1536, help="oracle rows for the cpu_baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip baselines, e2e and the oracle leg")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="measured seconds of the serving stream")
+    ap.add_argument("--tune-cache", default=None,
+                    help="thread-shape table: loaded if present (and written for this GPU), else timed and written")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -389,6 +396,9 @@ def main():
         torch.cuda.synchronize()
 
     ctx = P.ptg_create(local)
+    t_tune = time.perf_counter()
+    P.ptg_autotune(ctx, 0, args.tune_cache)  # 2D thread shape per octave structure, timed on this GPU
+    t_tune = time.perf_counter() - t_tune
     stream = torch.cuda.current_stream()
     n_samples = SIZE[0] * SIZE[1]
     out = torch.empty((SIZE[1], SIZE[0]), dtype=torch.float32, device="cuda")
@@ -435,7 +445,8 @@ def main():
     props = torch.cuda.get_device_properties(local)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = R.alu_peak(props.multi_processor_count, sm_max)
-    ops = R.lane_ops_2d("c1", SIZE, SPC, OCTAVES)
+    rw = P.ptg_thread_shape(ctx, descs[0])
+    ops = R.lane_ops_2d("c1", SIZE, SPC, OCTAVES, rw)
     achieved = ops["total"] / avg_launch_s
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-ops/s",
             "frac": achieved / peak, "traffic": profile_traffic(),
@@ -453,7 +464,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": world, "samples_per_step": world * n_samples,
                    "parallelism": "replicas (independent fields per rank)" if world > 1 else "single GPU",
-                   "l2": "output 268 MB > 129 MB L2 each step; no flush"},
+                   "l2": "output 268 MB > 129 MB L2 each step; no flush",
+                   "thread_shape": "%dx%d (autotuned in %.2f s)" % (rw, 32 // rw, t_tune)},
         "p50_ms": per[len(per) // 2], "p99_ms": per[min(len(per) - 1, int(0.99 * len(per)))],
         "gpu_launches": args.steps,
         "roofline": roof,
@@ -491,12 +503,19 @@ def main():
         extras["zero_gradient_f32"] = time_fn(lambda o: P.ptg_field(ctx, dZ, o, stream))
         extras["paper_d2m1n3_f32"] = time_fn(lambda o: P.ptg_field(ctx, dG, o, stream))
         extras["opensimplex_f32"] = time_fn(lambda o: P.ptg_opensimplex(ctx, dP, o, stream), reps=5)
+        ex_desc = {"c2_f32": (dC2, P.METHOD_FIELD), "c1_f16": (d16, P.METHOD_FIELD),
+                   "perlin_s5_f32": (dP, P.METHOD_PERLIN), "zero_gradient_f32": (dZ, P.METHOD_FIELD),
+                   "paper_d2m1n3_f32": (dG, P.METHOD_FIELD), "opensimplex_f32": (None, None)}
         for k, v in extras.items():
+            d_k, m_k = ex_desc[k]
+            rw_k = P.ptg_thread_shape(ctx, d_k, m_k) if d_k is not None else 8
+            if d_k is not None:
+                v["thread_shape"] = "%dx%d" % (rw_k, 32 // rw_k)
             v["ops_per_sample"] = R.lane_ops_2d({"c2_f32": "c2", "c1_f16": "c1", "perlin_s5_f32": "perlin_s5",
                                                  "zero_gradient_f32": "zero_grad",
                                                  "paper_d2m1n3_f32": "paper_gauge",
                                                  "opensimplex_f32": "opensimplex"}[k], SIZE, SPC,
-                                                OCTAVES)["per_sample"]
+                                                OCTAVES, rw_k)["per_sample"]
         line["baselines"] = extras
         if rank == 0:
             line["volume3d_512_n8"] = bench_3d(P, R, ctx, stream, torch)

@@ -79,6 +79,19 @@ typedef enum { PTG_F32 = 0, PTG_F16 = 1 } ptg_dtype;
 /* Perlin blend (Sec. 3.2): smootherstep S5 (default) or smoothstep S3. */
 typedef enum { PTG_PERLIN_S5 = 0, PTG_PERLIN_S3 = 1 } ptg_perlin_blend;
 
+/* Thread shape of the 2D polynomial and Perlin generators, or-ed into
+ * desc->variant: how many samples of a 64 x 64 output tile each thread owns,
+ * as consecutive columns x rows.  8 x 4 evaluates octaves whose cells are at
+ * least 8 samples wide at 4 node columns per run; 16 x 2 halves that work per
+ * sample for cells at least 16 samples wide and interpolates more columns.
+ * AUTO takes the context's tuned choice (ptg_autotune), else a fixed rule.
+ * Both shapes compute the same field; results differ only by FP32 rounding
+ * (well inside the stated tolerance).  A shape is a function of the method,
+ * dtype, spc and octave count only, never of the size or offset, so a field
+ * cut into chunks is bit-identical to the whole.  No counterpart in the
+ * paper: a GPU tuning choice. */
+typedef enum { PTG_SHAPE_AUTO = 0, PTG_SHAPE_8X4 = 0x100, PTG_SHAPE_16X2 = 0x200 } ptg_shape;
+
 /* Full description of one field (Sec. 2.1 cell lattice, Sec. 4 octaves). */
 typedef struct {
     uint32_t struct_size; /* sizeof(ptg_field_desc)                            */
@@ -96,7 +109,8 @@ typedef struct {
     float grad_weight;    /* w of Sec. 4; 1.0 default, 0.01 = the paper's      */
     uint32_t seed;        /* < 2^24                                            */
     int32_t dtype;        /* ptg_dtype                                         */
-    int32_t variant;      /* ptg_perlin_blend for ptg_perlin; else 0           */
+    int32_t variant;      /* low byte: ptg_perlin_blend for ptg_perlin, else 0;
+                             bits 8..9: ptg_shape (2D field / Perlin only)     */
 } ptg_field_desc;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
@@ -206,6 +220,23 @@ int ptg_wait(ptg_ctx* ctx, uint64_t req_id, uint64_t timeout_ns);
  * becomes PTG_ERR_CANCELLED.  Returns PTG_OK, or PTG_ERR_INVALID if the
  * request is unknown or already admitted. */
 int ptg_cancel(ptg_ctx* ctx, uint64_t req_id);
+
+/* Autotuner for the 2D thread shape (ptg_shape).  For every 2D method, dtype
+ * and octave structure -- n16 = octaves whose cells are at least 16 samples
+ * wide (min(N, log2(spc) - 3), capped at 8) and whether finer octaves follow
+ * -- time both shapes on a 4096 x 4096 field (effort timed launches each,
+ * 0 = 5) and keep the faster in the context; AUTO fields use the table from
+ * then on.  cache_path (may be NULL): if the file exists and was written for
+ * this device model and SM count, load the table from it instead of timing;
+ * otherwise time and write it (JSON).  Blocks; allocates one 64 MiB scratch
+ * field for the duration.  Returns PTG_OK, PTG_ERR_CUDA, or PTG_ERR_INVALID
+ * (bad arguments, unreadable cache).  No counterpart in the paper. */
+int ptg_autotune(ptg_ctx* ctx, int32_t effort, const char* cache_path);
+
+/* The thread shape (8 for 8 x 4, 16 for 16 x 2) that generator `method`
+ * (0 = ptg_field, 1 = ptg_perlin) would use for desc on this context, in *rw.
+ * Returns PTG_OK or the validation status of desc. */
+int ptg_thread_shape(ptg_ctx* ctx, const ptg_field_desc* desc, int32_t method, int32_t* rw);
 
 /* Check a descriptor for generator `method` (0 = ptg_field, 1 = ptg_perlin,
  * 2 = ptg_opensimplex) without touching any device: returns the status the

@@ -74,8 +74,15 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
         return ptg_fail(ctx, PTG_ERR_INVALID, "smoothness must be a ptg_smoothness value");
     if (kind == kKindField && d->dims == 3 && d->smoothness != PTG_C1 && d->smoothness != PTG_C2)
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "the paper's D2M1N3 and zero-gradient models are 2D");
-    if (kind == kKindPerlin && d->variant != PTG_PERLIN_S5 && d->variant != PTG_PERLIN_S3)
+    const int blend = d->variant & 0xff, shape = d->variant & ~0xff;
+    if (shape != PTG_SHAPE_AUTO && shape != PTG_SHAPE_8X4 && shape != PTG_SHAPE_16X2)
+        return ptg_fail(ctx, PTG_ERR_INVALID, "variant: unknown thread-shape bits 0x%x", (unsigned)shape);
+    if (kind == kKindPerlin && blend != PTG_PERLIN_S5 && blend != PTG_PERLIN_S3)
         return ptg_fail(ctx, PTG_ERR_INVALID, "Perlin variant must be PTG_PERLIN_S5 or PTG_PERLIN_S3");
+    if (kind != kKindPerlin && blend != 0)
+        return ptg_fail(ctx, PTG_ERR_INVALID, "variant: the low byte is the Perlin blend, 0 for other generators");
+    if (shape != PTG_SHAPE_AUTO && (kind == kKindSimplex || d->dims != 2))
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "a thread shape applies to 2D polynomial and Perlin fields");
     if (!std::isfinite(d->persistence) || !std::isfinite(d->grad_weight))
         return ptg_fail(ctx, PTG_ERR_INVALID, "persistence and grad_weight must be finite");
     if (!std::isfinite(d->lacunarity)) return ptg_fail(ctx, PTG_ERR_INVALID, "lacunarity must be finite");
@@ -153,6 +160,7 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
     P->ncount = count;
     P->method = method;
     P->s = s;
+    P->rw = is3d ? 8 : ptg_pick_rw(ctx, d, method, s);
     const size_t smem = is3d ? fbm3d_smem_bytes(*P) : fbm2d_smem_bytes(*P);
     if (smem > (size_t)ctx->max_smem)
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "staging needs %zu bytes of shared memory (max %d)", smem,
@@ -211,7 +219,7 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
 
 int ptg_kernel_method(int kind, const ptg_field_desc* d)
 {
-    if (kind == kKindPerlin) return d->variant == PTG_PERLIN_S3 ? kPerlinS3 : kPerlinS5;
+    if (kind == kKindPerlin) return (d->variant & 0xff) == PTG_PERLIN_S3 ? kPerlinS3 : kPerlinS5;
     switch (d->smoothness) {
     case PTG_C2: return kC2;
     case PTG_PAPER_D2M1N3: return kPaperGauge;

@@ -58,7 +58,7 @@ struct FieldPlan {
     int32_t jx0, jy0, jz0;  // sample index of output element 0 (bands of a larger field)
     int32_t method;         // kC1, kC2, kPerlinS5, kPerlinS3
     int32_t s;              // log2(samples per cell)
-    int32_t pad[1];
+    int32_t rw;             // 2D thread shape: run width 8 (8 x 4 samples a thread) or 16 (16 x 2)
     OctPlan oct[kMaxOctaves];
 };
 static_assert(sizeof(FieldPlan) % 16 == 0, "FieldPlan is copied in 16-byte words");

@@ -23,41 +23,46 @@ struct Deg {
                                : METHOD == kC2 ? 5 : METHOD == kPerlinS3 ? 4 : 6;
 };
 
-// Node columns of the run8 evaluation for degree D (d + 1 of the 8 columns,
-// chosen so that the interpolation weights of the other columns are small:
-// sum |w| <= 1.4, 2.1, 2.3, 2.7 for D = 3, 4, 5, 6).
-template <int D>
+// Node columns of a run of RW columns (8 or 16) for degree D: d + 1 of the
+// run's columns, chosen so that the interpolation weights of the other columns
+// are small (max sum |w| over a column: RW = 8: 1.4, 2.1, 2.3, 2.7 for
+// D = 3, 4, 5, 6; RW = 16: 1.55, 1.66, 1.95, 2.22).
+template <int D, int RW = 8>
 __host__ __device__ constexpr int node_col(int q)
 {
-    return D == 3 ? (q == 0 ? 0 : q == 1 ? 2 : q == 2 ? 5 : 7)
+    return RW == 8
+        ? (D == 3 ? (q == 0 ? 0 : q == 1 ? 2 : q == 2 ? 5 : 7)
          : D == 4 ? (q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 3 : q == 3 ? 6 : 7)
          : D == 5 ? (q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 2 : q == 3 ? 4 : q == 4 ? 6 : 7)
-                  : (q < 4 ? q : q + 1);
+                  : (q < 4 ? q : q + 1))
+        : (D == 3 ? (q == 0 ? 0 : q == 1 ? 4 : q == 2 ? 11 : 15)
+         : D == 4 ? (q == 0 ? 0 : q == 1 ? 3 : q == 2 ? 7 : q == 3 ? 12 : 15)
+         : D == 5 ? (q == 0 ? 0 : q == 1 ? 2 : q == 2 ? 6 : q == 3 ? 9 : q == 4 ? 13 : 15)
+                  : (q == 0 ? 0 : q == 1 ? 1 : q == 2 ? 4 : q == 3 ? 7 : q == 4 ? 11 : q == 5 ? 14 : 15));
 }
 
-template <int D>
+template <int D, int RW = 8>
 __host__ __device__ constexpr int node_of_col(int c)  // node index of column c, or -1
 {
     int r = -1;
     for (int q = 0; q <= D; ++q)
-        if (node_col<D>(q) == c) r = q;
+        if (node_col<D, RW>(q) == c) r = q;
     return r;
 }
 
 // Lagrange weight of node q at column c: prod_{m != q} (c - x_m) / (x_q - x_m),
 // a ratio of small integers (folded to a constant once loops are unrolled).
-template <int D>
+template <int D, int RW = 8>
 __host__ __device__ constexpr float lagrange(int c, int q)
 {
     long long num = 1, den = 1;
     for (int m = 0; m <= D; ++m) {
         if (m == q) continue;
-        num *= (long long)(c - node_col<D>(m));
-        den *= (long long)(node_col<D>(q) - node_col<D>(m));
+        num *= (long long)(c - node_col<D, RW>(m));
+        den *= (long long)(node_col<D, RW>(q) - node_col<D, RW>(m));
     }
     return (float)num / (float)den;
 }
-
 
 // Corner data of one cell: (v, f, g) at (0,0), (1,0), (0,1), (1,1).
 struct Cell {

@@ -1,9 +1,10 @@
 // ptg_fbm2d.cu -- fused all-octave 2D generator for the polynomial noise of
 // Thorimbert & Chopard (arXiv:1610.03525) and for Perlin's polynomial.
 //
-// One CTA makes a 64 x 64 tile of samples with 128 threads; each thread owns
-// 4 rows x 8 consecutive columns and keeps their fractal sums (Sec. 4) in
-// registers across all octaves, then writes each sample once.
+// One CTA makes a 64 x 64 tile of samples with 128 threads; each thread owns a
+// run of RW consecutive columns in RR rows (RW x RR = 8 x 4 or 16 x 2, the
+// "thread shape") and keeps their fractal sums (Sec. 4) in registers across
+// all octaves, then writes each sample once.
 //
 // Inside a cell every method is separable.  For one row y the cell collapses
 // to a 1D function of x,
@@ -14,20 +15,22 @@
 // with the corner constraints of Eq. (mixedderiv) and zero mixed derivatives,
 // or Perlin's polynomial (Sec. 3.2) with v = 0 and its own B0, B1.
 //
-// Octave i has cells of spc_i = spc / 2^i samples.  Four regimes:
-//   spc_i >= 8 ("run8"): a thread's 8-column run lies in one cell, so each of
+// Octave i has cells of spc_i = spc / 2^i samples.  Three regimes:
+//   spc_i >= RW ("run" octaves): a thread's run lies in one cell, so each of
 //     its rows is one polynomial of degree d in the column (d = 3 for C1, 5 for
 //     C2, 4 / 6 for Perlin S3 / S5), and so is the sum over all such octaves.
 //     The kernel evaluates d + 1 node columns per octave and fills the other
-//     columns once, at the end, by exact Lagrange interpolation.
-//   spc_i = 4, 2: in-cell positions are the constants q / spc_i; the basis is
-//     folded into the code and positions t = 0 take the corner data directly.
+//     columns once, at the end, by exact Lagrange interpolation.  The wider
+//     run halves the per-sample cost of these octaves and adds interpolated
+//     columns; which shape is faster depends on the octave mix.
+//   2 <= spc_i < RW: in-cell column positions are the constants q / spc_i and
+//     positions t = 0 take the corner data directly.
 //   spc_i <= 1 ("lattice"): every sample is a lattice point, where the cell
 //     polynomial equals the corner value: one hash per sample (zero for
 //     Perlin, whose value at lattice points is zero).
 // Corners of every staged octave (cells >= 2 samples) are hashed once per CTA
 // into shared memory, pre-scaled by the octave amplitude (Sec. 4.1's C_init),
-// and the per-axis basis of the run8 octaves is tabulated per CTA (the paper's
+// and the per-axis basis of the run octaves is tabulated per CTA (the paper's
 // precomputed space-only terms, Sec. 5.2).
 #include "ptg_device.cuh"
 #include "ptg_eval.cuh"
@@ -36,39 +39,51 @@
 namespace ptg {
 namespace {
 
-constexpr int kTW = 64, kTH = 64, kThreads = 128;
-constexpr int kCols = 8, kRows = 4;  // per thread
+constexpr int kTW = kTile2dX, kTH = kTile2dY, kThreads = 128;
+
+// Thread shape: RW consecutive columns x RR rows per thread.
+template <int RW>
+struct Shape {
+    static_assert(RW == 8 || RW == 16, "run width 8 or 16");
+    static constexpr int RR = 32 / RW;        // rows per thread
+    static constexpr int TXN = kTW / RW;      // threads along x
+    static constexpr int TYN = kTH / RR;      // threads along y
+    static constexpr int LOG = RW == 8 ? 3 : 4;
+};
+static_assert(Shape<8>::TXN * Shape<8>::TYN == kThreads && Shape<16>::TXN * Shape<16>::TYN == kThreads, "");
 
 // Shared-memory layout (float4 units):
-//   x-basis of run8 octaves at node columns [n8][D+1][8 tx],
-//   y-basis of run8 octaves [n8][4 rows][16 ty],
+//   x-basis of run octaves at node columns [nrun][D+1][TXN],
+//   y-basis of run octaves [nrun][RR rows][TYN] (64 per octave),
 //   staged corners of every staged octave (rows swizzled by corner_slot).
-template <int METHOD>
-__host__ __device__ constexpr int xnode_words(int n8) { return n8 * (Deg<METHOD>::value + 1) * 8; }
+template <int METHOD, int RW>
+__host__ __device__ constexpr int xnode_words(int nrun) { return nrun * (Deg<METHOD>::value + 1) * Shape<RW>::TXN; }
 
-__device__ __forceinline__ int n_run8(const FieldPlan& P)
+template <int RW>
+__host__ __device__ __forceinline__ int n_run(const FieldPlan& P)  // octaves with cells >= RW samples
 {
-    const int n = P.s - 2;
+    const int n = P.s - Shape<RW>::LOG + 1;
     return n < 0 ? 0 : (n < P.N ? n : P.N);
 }
 
-template <int METHOD>
+template <int METHOD, int RW>
 __device__ __forceinline__ void stage_tile(const FieldPlan& P, float4* sm, int j0x, int j0y)
 {
-    constexpr int NN = Deg<METHOD>::value + 1;
-    const int tid = threadIdx.x, s = P.s, n8 = n_run8(P);
+    using SH = Shape<RW>;
+    constexpr int D = Deg<METHOD>::value, NN = D + 1;
+    const int tid = threadIdx.x, s = P.s, nrun = n_run<RW>(P);
     float4* xnode = sm;
-    float4* ylut = sm + xnode_words<METHOD>(n8);
-    float4* corners = ylut + n8 * 64;
-    for (int e = tid; e < n8 * NN * 8; e += kThreads) {
-        const int i = e / (NN * 8), rem = e - i * (NN * 8);
-        const int q = rem >> 3, tx = rem & 7;
-        const int col = tx * 8 + node_col<Deg<METHOD>::value>(q);
+    float4* ylut = sm + xnode_words<METHOD, RW>(nrun);
+    float4* corners = ylut + nrun * 64;
+    for (int e = tid; e < nrun * NN * SH::TXN; e += kThreads) {
+        const int i = e / (NN * SH::TXN), rem = e - i * (NN * SH::TXN);
+        const int q = rem / SH::TXN, tx = rem % SH::TXN;
+        const int col = tx * RW + node_col<D, RW>(q);
         xnode[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0x + col), i, s));
     }
-    for (int e = tid; e < n8 * 64; e += kThreads) {  // stored in table order: conflict-free
+    for (int e = tid; e < nrun * 64; e += kThreads) {  // stored in table order: conflict-free
         const int i = e >> 6, slot = e & 63;
-        const int row = (slot & 15) * 4 + (slot >> 4);
+        const int row = (slot % SH::TYN) * SH::RR + slot / SH::TYN;
         ylut[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0y + row), i, s));
     }
     // Corners, octave by octave (uniform loops: every lane of a warp reads the
@@ -117,52 +132,62 @@ __device__ __forceinline__ Cell load_cell(const float4* __restrict__ cg, int row
     return c;
 }
 
-// A run8 octave: node columns only.
-template <int METHOD>
-__device__ __forceinline__ void run8_octave(float (&nacc)[kRows][Deg<METHOD>::value + 1],
-                                            const float4* __restrict__ sm, const FieldPlan& P, int i, int tx,
-                                            int ty, int n8)
+// A run octave: node columns only.
+template <int METHOD, int RW>
+__device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
+                                           const float4* __restrict__ sm, const FieldPlan& P, int i, int tx,
+                                           int ty, int nrun)
 {
+    using SH = Shape<RW>;
     constexpr int NN = Deg<METHOD>::value + 1;
     const OctPlan& op = P.oct[i];
-    const float4* ylut = sm + xnode_words<METHOD>(n8);
-    const float4* cg = ylut + n8 * 64 + op.coff;
-    const Cell c = load_cell(cg, op.rowlen, (tx * kCols) >> op.k, (ty * kRows) >> op.k);
+    const float4* ylut = sm + xnode_words<METHOD, RW>(nrun);
+    const float4* cg = ylut + nrun * 64 + op.coff;
+    const Cell c = load_cell(cg, op.rowlen, (tx * RW) >> op.k, (ty * SH::RR) >> op.k);
     float4 xb[NN];
 #pragma unroll
-    for (int q = 0; q < NN; ++q) xb[q] = sm[(i * NN + q) * 8 + tx];
+    for (int q = 0; q < NN; ++q) xb[q] = sm[(i * NN + q) * SH::TXN + tx];
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-        const float4 yb = ylut[i * 64 + r * 16 + ty];
+    for (int r = 0; r < SH::RR; ++r) {
+        const float4 yb = ylut[i * 64 + r * SH::TYN + ty];
         const Row R = Model<METHOD>::row(c, yb);
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] += Model<METHOD>::eval(R, xb[q]);
     }
 }
 
-// Cells of spc_i = 4 (CW = 4) or 2 (CW = 2) samples: the in-cell position of
-// column c is (c mod CW) / CW, of row r (r mod CW) / CW -- constants.
-template <int METHOD, int CW>
-__device__ __forceinline__ void small_octave(float (&acc)[kRows][kCols], const float4* __restrict__ sm,
-                                             const FieldPlan& P, int i, int tx, int ty, int n8)
+// Cells of CW = 8, 4 or 2 samples (CW < RW): the in-cell position of column c
+// is (c mod CW) / CW, a constant.  Row positions are constants too when a
+// thread's rows cover whole cells (RR >= CW); otherwise (RR < CW) they depend
+// on the thread's row and the row basis is evaluated once per octave.
+template <int METHOD, int RW, int CW>
+__device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], const float4* __restrict__ sm,
+                                             const FieldPlan& P, int i, int tx, int ty, int nrun)
 {
+    using SH = Shape<RW>;
+    constexpr int RR = SH::RR, NXC = RW / CW, RPC = RR < CW ? RR : CW, NYC = RR / RPC;
+    constexpr bool kConstRows = RR >= CW;
     const OctPlan& op = P.oct[i];
-    const float4* cg = sm + xnode_words<METHOD>(n8) + n8 * 64 + op.coff;
+    const float4* cg = sm + xnode_words<METHOD, RW>(nrun) + nrun * 64 + op.coff;
     constexpr float inv = 1.0f / CW;
+    float4 yb[RPC];
 #pragma unroll
-    for (int yq = 0; yq < kRows / CW; ++yq) {
-        const int lcy = (ty * kRows + yq * CW) / CW;
+    for (int rr = 0; rr < RPC; ++rr)
+        yb[rr] = axis_basis<METHOD>(kConstRows ? rr * inv : (float)(((ty * RR) & (CW - 1)) + rr) * inv);
 #pragma unroll
-        for (int xq = 0; xq < kCols / CW; ++xq) {
-            const int lcx = (tx * kCols + xq * CW) / CW;
+    for (int yq = 0; yq < NYC; ++yq) {
+        const int lcy = (ty * RR + yq * RPC) / CW;
+#pragma unroll
+        for (int xq = 0; xq < NXC; ++xq) {
+            const int lcx = (tx * RW + xq * CW) / CW;
             const Cell c = load_cell(cg, op.rowlen, lcx, lcy);
 #pragma unroll
-            for (int rr = 0; rr < CW; ++rr) {
-                const Row R = rr == 0 ? Model<METHOD>::row0(c) : Model<METHOD>::row(c, axis_basis<METHOD>(rr * inv));
+            for (int rr = 0; rr < RPC; ++rr) {
+                const Row R = (kConstRows && rr == 0) ? Model<METHOD>::row0(c) : Model<METHOD>::row(c, yb[rr]);
 #pragma unroll
                 for (int q = 0; q < CW; ++q) {
                     const float h = q == 0 ? R.V0 : Model<METHOD>::eval(R, axis_basis<METHOD>(q * inv));
-                    acc[yq * CW + rr][xq * CW + q] += h;
+                    acc[yq * RPC + rr][xq * CW + q] += h;
                 }
             }
         }
@@ -170,98 +195,123 @@ __device__ __forceinline__ void small_octave(float (&acc)[kRows][kCols], const f
 }
 
 // One lattice octave: every sample sits on a lattice point.
-__device__ __forceinline__ void lattice_octave(float (&acc)[kRows][kCols], const OctPlan& op, uint32_t jx,
+template <int RW>
+__device__ __forceinline__ void lattice_octave(float (&acc)[Shape<RW>::RR][RW], const OctPlan& op, uint32_t jx,
                                                uint32_t jy)
 {
     const int sh = op.k;
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
+    for (int r = 0; r < Shape<RW>::RR; ++r) {
         const uint32_t iy = op.oy + ((jy + r) << sh);
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) {
+        for (int c = 0; c < RW; ++c) {
             const uint32_t ix = op.ox + ((jx + c) << sh);
             acc[r][c] = fmaf(op.amp, unit_value(pcg3d_value(ix, iy, op.key)), acc[r][c]);
         }
     }
 }
 
-template <typename OutT>
-__device__ __forceinline__ void store_tile(const FieldPlan& P, const float (&acc)[kRows][kCols], int x0, int y0)
+template <typename OutT, int RW>
+__device__ __forceinline__ void store_tile_as(const FieldPlan& P, const float (&acc)[Shape<RW>::RR][RW], int x0, int y0)
 {
     OutT* out = reinterpret_cast<OutT*>(P.out);
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
+    for (int r = 0; r < Shape<RW>::RR; ++r) {
         const int y = y0 + r;
         if (y >= P.H) break;
         OutT* row = out + (size_t)y * (size_t)P.W;
-        if (P.vec_ok && x0 + kCols <= P.W) {
+        if (P.vec_ok && x0 + RW <= P.W) {
             if (sizeof(OutT) == 4) {
                 float4* p = reinterpret_cast<float4*>(row + x0);
-                p[0] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-                p[1] = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
-            } else {
-                __half2 h[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) h[q] = __floats2half2_rn(acc[r][2 * q], acc[r][2 * q + 1]);
-                *reinterpret_cast<uint4*>(row + x0) = *reinterpret_cast<const uint4*>(h);
+                for (int v = 0; v < RW / 4; ++v)
+                    p[v] = make_float4(acc[r][4 * v], acc[r][4 * v + 1], acc[r][4 * v + 2], acc[r][4 * v + 3]);
+            } else {
+                uint4* p = reinterpret_cast<uint4*>(row + x0);
+#pragma unroll
+                for (int v = 0; v < RW / 8; ++v) {
+                    __half2 h[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        h[q] = __floats2half2_rn(acc[r][8 * v + 2 * q], acc[r][8 * v + 2 * q + 1]);
+                    p[v] = *reinterpret_cast<const uint4*>(h);
+                }
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < kCols; ++c)
+            for (int c = 0; c < RW; ++c)
                 if (x0 + c < P.W) store1(row + x0 + c, acc[r][c]);
         }
     }
 }
 
+template <int RW>
+__device__ __forceinline__ void store_tile(const FieldPlan& P, const float (&acc)[Shape<RW>::RR][RW], int x0, int y0)
+{
+    if (P.dtype == 1) store_tile_as<__half, RW>(P, acc, x0, y0);
+    else store_tile_as<float, RW>(P, acc, x0, y0);
+}
+
 // Whole tile: stage, evaluate all octaves, store.
-template <int METHOD, typename OutT>
+template <int METHOD, int RW>
 __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int bx, int by)
 {
-    constexpr int D = Deg<METHOD>::value, NN = D + 1;
-    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    using SH = Shape<RW>;
+    constexpr int D = Deg<METHOD>::value, NN = D + 1, RR = SH::RR;
+    const int tid = threadIdx.x, tx = tid % SH::TXN, ty = tid / SH::TXN;
     const int x0 = bx * kTW, y0 = by * kTH;        // output tile origin
     const int j0x = x0 + P.jx0, j0y = y0 + P.jy0;  // sample indices
-    const int s = P.s, N = P.N, n8 = n_run8(P);
-    stage_tile<METHOD>(P, sm, j0x, j0y);
+    const int s = P.s, N = P.N, nrun = n_run<RW>(P);
+    stage_tile<METHOD, RW>(P, sm, j0x, j0y);
     __syncthreads();
 
-    // run8 octaves: node columns, then interpolate the other columns once
-    float nacc[kRows][NN];
+    // run octaves: node columns, then interpolate the other columns once
+    float nacc[RR][NN];
 #pragma unroll
-    for (int r = 0; r < kRows; ++r)
+    for (int r = 0; r < RR; ++r)
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
-    for (int i = 0; i < n8; ++i) run8_octave<METHOD>(nacc, sm, P, i, tx, ty, n8);
-    float acc[kRows][kCols];
+    for (int i = 0; i < nrun; ++i) run_octave<METHOD, RW>(nacc, sm, P, i, tx, ty, nrun);
+    float acc[RR][RW];
 #pragma unroll
-    for (int r = 0; r < kRows; ++r)
+    for (int r = 0; r < RR; ++r)
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-            const int q = node_of_col<D>(c);
+        for (int c = 0; c < RW; ++c) {
+            const int q = node_of_col<D, RW>(c);
             if (q >= 0) {
                 acc[r][c] = nacc[r][q];
             } else {
                 float v = 0.0f;
 #pragma unroll
-                for (int m = 0; m < NN; ++m) v = fmaf(lagrange<D>(c, m), nacc[r][m], v);
+                for (int m = 0; m < NN; ++m) v = fmaf(lagrange<D, RW>(c, m), nacc[r][m], v);
                 acc[r][c] = v;
             }
         }
 
-    // cells of 4 and 2 samples, then lattice octaves
-    if (s >= 2 && s - 2 < N) small_octave<METHOD, 4>(acc, sm, P, s - 2, tx, ty, n8);
-    if (s >= 1 && s - 1 < N) small_octave<METHOD, 2>(acc, sm, P, s - 1, tx, ty, n8);
+    // cells narrower than the run (8, 4 and 2 samples), then lattice octaves
+    if (RW == 16 && s >= 3 && s - 3 < N) small_octave<METHOD, RW, (RW == 16 ? 8 : 4)>(acc, sm, P, s - 3, tx, ty, nrun);
+    if (s >= 2 && s - 2 < N) small_octave<METHOD, RW, 4>(acc, sm, P, s - 2, tx, ty, nrun);
+    if (s >= 1 && s - 1 < N) small_octave<METHOD, RW, 2>(acc, sm, P, s - 1, tx, ty, nrun);
     if (METHOD != kPerlinS5 && METHOD != kPerlinS3)
         for (int i = s; i < N; ++i)
-            lattice_octave(acc, P.oct[i], (uint32_t)(j0x + tx * kCols), (uint32_t)(j0y + ty * kRows));
-    store_tile<OutT>(P, acc, x0 + tx * kCols, y0 + ty * kRows);
+            lattice_octave<RW>(acc, P.oct[i], (uint32_t)(j0x + tx * RW), (uint32_t)(j0y + ty * RR));
+    store_tile<RW>(P, acc, x0 + tx * RW, y0 + ty * RR);
 }
 
-template <int METHOD, typename OutT>
+template <int METHOD, int RW>
 __global__ void __launch_bounds__(kThreads) fbm2d_kernel(const __grid_constant__ FieldPlan P)
 {
     extern __shared__ float4 sm[];
-    fbm2d_tile<METHOD, OutT>(P, sm, blockIdx.x, blockIdx.y);
+    fbm2d_tile<METHOD, RW>(P, sm, blockIdx.x, blockIdx.y);
+}
+
+// One tile of a batch field, as a call (not inlined) so that the batch
+// kernel's registers are those of its largest path, not of all paths at once.
+template <int METHOD>
+__device__ __noinline__ void batch_tile(const FieldPlan& P, float4* sm, int bx, int by)
+{
+    if (P.rw == 16) fbm2d_tile<METHOD, 16>(P, sm, bx, by);
+    else fbm2d_tile<METHOD, 8>(P, sm, bx, by);
 }
 
 // Persistent batched generator: resident CTAs pull tiles of many fields from
@@ -305,32 +355,11 @@ __global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* 
         }
         const long long local = t - tile_start[f];
         const int bx = (int)(local % plan.tiles_x), by = (int)(local / plan.tiles_x);
-        const bool f16 = plan.dtype == 1;
-        switch (plan.method) {
-        case kC1:
-            if (f16) fbm2d_tile<kC1, __half>(plan, sm, bx, by);
-            else fbm2d_tile<kC1, float>(plan, sm, bx, by);
-            break;
-        case kC2:
-            if (f16) fbm2d_tile<kC2, __half>(plan, sm, bx, by);
-            else fbm2d_tile<kC2, float>(plan, sm, bx, by);
-            break;
-        case kPaperGauge:
-            if (f16) fbm2d_tile<kPaperGauge, __half>(plan, sm, bx, by);
-            else fbm2d_tile<kPaperGauge, float>(plan, sm, bx, by);
-            break;
-        case kZeroGrad:
-            if (f16) fbm2d_tile<kZeroGrad, __half>(plan, sm, bx, by);
-            else fbm2d_tile<kZeroGrad, float>(plan, sm, bx, by);
-            break;
-        case kPerlinS5:
-            if (f16) fbm2d_tile<kPerlinS5, __half>(plan, sm, bx, by);
-            else fbm2d_tile<kPerlinS5, float>(plan, sm, bx, by);
-            break;
-        default:
-            if (f16) fbm2d_tile<kPerlinS3, __half>(plan, sm, bx, by);
-            else fbm2d_tile<kPerlinS3, float>(plan, sm, bx, by);
-            break;
+        switch (plan.method) {  // the polynomial models (batches are ptg_field calls)
+        case kC1: batch_tile<kC1>(plan, sm, bx, by); break;
+        case kC2: batch_tile<kC2>(plan, sm, bx, by); break;
+        case kPaperGauge: batch_tile<kPaperGauge>(plan, sm, bx, by); break;
+        default: batch_tile<kZeroGrad>(plan, sm, bx, by); break;
         }
         __syncthreads();
     }
@@ -339,9 +368,12 @@ __global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* 
 template <int METHOD>
 size_t smem_words(const FieldPlan& P)
 {
-    int n8 = P.s - 2;
-    n8 = n8 < 0 ? 0 : (n8 < P.N ? n8 : P.N);
-    return (size_t)xnode_words<METHOD>(n8) + (size_t)n8 * 64 + (size_t)P.ncorner;
+    if (P.rw == 16) {
+        const int nrun = n_run<16>(P);
+        return (size_t)xnode_words<METHOD, 16>(nrun) + (size_t)nrun * 64 + (size_t)P.ncorner;
+    }
+    const int nrun = n_run<8>(P);
+    return (size_t)xnode_words<METHOD, 8>(nrun) + (size_t)nrun * 64 + (size_t)P.ncorner;
 }
 
 template <typename K>
@@ -373,24 +405,29 @@ cudaError_t launch_fbm2d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
 {
     const dim3 grid(P.tiles_x, P.tiles_y, 1);
     const size_t smem = fbm2d_smem_bytes(P);
-    const bool f16 = P.dtype == 1;
-#define PTG_LAUNCH2D(M, T)                                                                           \
+#define PTG_LAUNCH2D_RW(M, RW)                                                                       \
     do {                                                                                             \
-        auto kfn = fbm2d_kernel<M, T>;                                                               \
+        auto kfn = fbm2d_kernel<M, RW>;                                                              \
         cudaError_t e = set_smem(kfn, smem);                                                         \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
         return cudaGetLastError();                                                                   \
     } while (0)
+#define PTG_LAUNCH2D(M)                                                                              \
+    do {                                                                                             \
+        if (P.rw == 16) PTG_LAUNCH2D_RW(M, 16);                                                      \
+        PTG_LAUNCH2D_RW(M, 8);                                                                       \
+    } while (0)
     switch (method) {
-    case kC1: if (f16) PTG_LAUNCH2D(kC1, __half); else PTG_LAUNCH2D(kC1, float);
-    case kC2: if (f16) PTG_LAUNCH2D(kC2, __half); else PTG_LAUNCH2D(kC2, float);
-    case kPaperGauge: if (f16) PTG_LAUNCH2D(kPaperGauge, __half); else PTG_LAUNCH2D(kPaperGauge, float);
-    case kZeroGrad: if (f16) PTG_LAUNCH2D(kZeroGrad, __half); else PTG_LAUNCH2D(kZeroGrad, float);
-    case kPerlinS5: if (f16) PTG_LAUNCH2D(kPerlinS5, __half); else PTG_LAUNCH2D(kPerlinS5, float);
-    case kPerlinS3: if (f16) PTG_LAUNCH2D(kPerlinS3, __half); else PTG_LAUNCH2D(kPerlinS3, float);
+    case kC1: PTG_LAUNCH2D(kC1);
+    case kC2: PTG_LAUNCH2D(kC2);
+    case kPaperGauge: PTG_LAUNCH2D(kPaperGauge);
+    case kZeroGrad: PTG_LAUNCH2D(kZeroGrad);
+    case kPerlinS5: PTG_LAUNCH2D(kPerlinS5);
+    case kPerlinS3: PTG_LAUNCH2D(kPerlinS3);
     default: return cudaErrorInvalidValue;
     }
+#undef PTG_LAUNCH2D_RW
 #undef PTG_LAUNCH2D
 }
 

@@ -55,7 +55,14 @@ struct ptg_ctx {
     cudaEvent_t batch_uploaded = nullptr;
     // request loop
     PtgServer* server = nullptr;
+    // 2D thread-shape table filled by ptg_autotune: run width (8 / 16) per
+    // [method index][dtype][n16 0..8][finer octaves follow], 0 = untuned
+    uint8_t tune_rw[6][2][9][2] = {};
 };
+
+// Run width (8 or 16) of a 2D polynomial / Perlin field: the shape bits of
+// desc->variant, else the context's tuned table, else the fixed rule.
+int ptg_pick_rw(const ptg_ctx* ctx, const ptg_field_desc* d, int method, int s);
 
 int ptg_fail(ptg_ctx* ctx, int code, const char* fmt, ...);
 int ptg_cuda_fail(ptg_ctx* ctx, cudaError_t e, const char* where);

@@ -9,21 +9,26 @@ loop control and barriers are overhead and are NOT counted, so the achieved
 fraction of the issue peak measures how little overhead and stall the kernels
 add on top of the arithmetic they must do.
 
-Per 2D tile of 64 x 64 samples (128 threads x 4 rows x 8 columns), with
-d = 3 (C1), 5 (C2), 4 (Perlin-S3), 6 (Perlin-S5) and n8 = octaves whose cells
-are at least 8 samples wide:
-  basis tables: n8 x (8 (d+1) + 64) entries x (5 coordinate + basis ops:
-                C1 7, C2 14, Perlin-S5 9, Perlin-S3 8);
+Per 2D tile of 64 x 64 samples, 128 threads, each thread a run of RW columns
+in RR rows (RW x RR = 8 x 4 or 16 x 2, the thread shape), with d = 3 (C1), 5
+(C2), 4 (Perlin-S3), 6 (Perlin-S5) and nrun = octaves whose cells are at least
+RW samples wide ("run" octaves):
+  basis tables: nrun x ((64/RW)(d+1) + 64) entries x (5 coordinate + basis
+                ops: C1 7, C2 14, Perlin-S5 9, Perlin-S3 8);
   corners:      per staged corner 31 (pcg3d 15, three word->float maps 9,
                 three amplitude scalings 3, grid index 4);
-  cells >= 8 samples, per thread and octave: 4 (y differences) + 4 rows x
-                (9 row reduction + 4 (d+1) at the node columns); once per
-                thread, 4 rows x (7 - d) columns x (d+1) FMA of interpolation;
-  cells of 4 samples, per thread: 2 cells x (prep + 3 rows + 1) + 24 samples
-                x eval + 8 x 1; cells of 2: 8 cells x (prep + row + 1 + 2 eval + 2),
-                with (prep, row, eval) = (4, 9, 4) for the Hermite cells and
-                Perlin, (4, 4, 3) for the zero-gradient model and (25, 8, 4)
-                for the paper's D2M1N3 coefficients;
+  run octaves, per thread and octave: prep + RR rows x (row reduction + eval
+                at each of the d+1 node columns); once per thread, RR rows x
+                (RW - d - 1) columns x (d+1) FMA of interpolation;
+  cells of CW < RW samples (CW = 8 for RW 16; 4, 2), per thread: RW/CW cells
+                along the run, each with prep + one row reduction per row
+                (row 0 of a cell, where the row is the corner data, costs 1),
+                (CW - 1) evaluations per row and 1 accumulate of column 0; a
+                thread whose RR rows are fewer than CW evaluates its two row
+                bases at run time (2 + basis ops each).  (prep, row, eval) =
+                (4, 9, 4) for the Hermite cells and Perlin, (4, 4, 3) for the
+                zero-gradient model and (25, 8, 4) for the paper's D2M1N3
+                coefficients;
   lattice octave: per sample 19 (pcg3d word 0: 13, word->float 3, FMA 1,
                 coordinate 2); Perlin's lattice octaves are zero, no work.
 3D tiles of 32 x 16 x 8 (each thread 8 x 4 x 1): the same regimes, with a
@@ -50,7 +55,22 @@ MODEL_OPS = {"c1": (4, 9, 4), "c2": (4, 9, 4), "perlin_s3": (4, 9, 4), "perlin_s
              "zero_grad": (4, 4, 3), "paper_gauge": (25, 8, 4)}
 
 
-def lane_ops_2d(kind: str, size, spc: int, octaves: int) -> dict:
+def small_cell_ops(kind: str, rw: int, cw: int) -> int:
+    """Lane operations of one thread for one octave of cw-sample cells."""
+    rr = 32 // rw
+    prep, row, smp = MODEL_OPS[kind]
+    ncx = rw // cw
+    rpc = min(rr, cw)
+    ncy = rr // rpc
+    const_rows = rr >= cw
+    per_cell = prep + (1 + (rpc - 1) * row if const_rows else rpc * row) + rpc * ((cw - 1) * smp + 1)
+    ops = ncx * ncy * per_cell
+    if not const_rows:
+        ops += rpc * (2 + BASIS_OPS[kind])
+    return ops
+
+
+def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8) -> dict:
     w, h = size
     tiles = ((w + 63) // 64) * ((h + 63) // 64)
     threads = tiles * 128
@@ -58,23 +78,22 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int) -> dict:
     if kind == "opensimplex":
         tot = 150 * samples_padded * octaves
         return dict(total=float(tot), per_sample=tot / (w * h))
+    rr = 32 // rw
     d = DEG[kind]
     st = _staged(spc, octaves)
-    n8 = sum(1 for _, spci in st if spci >= 8)
-    lut = tiles * n8 * (8 * (d + 1) + 64) * (COORD_OPS + BASIS_OPS[kind])
+    nrun = sum(1 for _, spci in st if spci >= rw)
+    lut = tiles * nrun * ((64 // rw) * (d + 1) + 64) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
-    evalops = threads * 4 * (7 - d) * (d + 1)
+    evalops = threads * rr * (rw - d - 1) * (d + 1)
     prep, row, smp = MODEL_OPS[kind]
     for i, spci in st:
         k = spci.bit_length() - 1
         ncx = (63 >> min(k, 31)) + 2
         corners += tiles * ncx * ncx * (19 if kind == "zero_grad" else 31)
-        if spci >= 8:
-            evalops += threads * (prep + 4 * (row + smp * (d + 1)))
-        elif spci == 4:
-            evalops += threads * (2 * (prep + 3 * row + 1) + 24 * smp + 8)
+        if spci >= rw:
+            evalops += threads * (prep + rr * (row + smp * (d + 1)))
         else:
-            evalops += threads * 8 * (prep + row + 1 + 2 * smp + 2)
+            evalops += threads * small_cell_ops(kind, rw, spci)
     n_lattice = octaves - len(st)
     lattice = 0 if kind.startswith("perlin") else samples_padded * n_lattice * 19
     tot = lut + corners + evalops + lattice

@@ -69,6 +69,13 @@ def test_desc_layout_matches_header(P):
     (dict(persistence=float("nan")), 0, -1),
     (dict(origin=(1 << 40, 0, 0), octaves=12, spc=1024), 2, -2),
     (dict(size=(1, 1), spc=1, octaves=32), 0, 0),
+    (dict(variant=0x100), 0, 0),                      # thread shape 8 x 4
+    (dict(variant=0x201), 1, 0),                      # Perlin S3, shape 16 x 2
+    (dict(variant=0x300), 0, -1),                     # unknown shape bits
+    (dict(variant=0x1000), 0, -1),
+    (dict(variant=1), 0, -1),                         # blend byte on a polynomial field
+    (dict(variant=0x100), 2, -2),                     # no shape for OpenSimplex
+    (dict(variant=0x200, dims=3, size=(32, 32, 32)), 0, -2),
 ])
 def test_validation_codes(P, kw, method, code):
     d = P.make_desc(**kw)

@@ -57,6 +57,19 @@ def test_batch_equals_single_launches(ctx):
         assert torch.equal(o, r), k
 
 
+def test_batch_mixed_thread_shapes(ctx):
+    """Fields pinned to either 2D thread shape in one batch: each equals its
+    own single launch with the same shape."""
+    descs, outs = _chunks(48, seed=11)
+    for k, d in enumerate(descs):
+        d.variant = P.PTG_SHAPE_8X4 if k % 2 else P.PTG_SHAPE_16X2
+    ref = _singles(ctx, descs, outs)
+    P.ptg_batch(ctx, descs, outs)
+    torch.cuda.synchronize()
+    for k, (o, r) in enumerate(zip(outs, ref)):
+        assert torch.equal(o, r), k
+
+
 def test_prepared_batch_graph_replays(ctx):
     descs, outs = _chunks(40, seed=7)
     ref = _singles(ctx, descs, outs)

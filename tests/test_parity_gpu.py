@@ -34,9 +34,9 @@ def ctx():
 
 
 def gpu_field(ctx, kind, dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 0, 0), offset=(0, 0, 0),
-              seed=0, persistence=0.5, grad_weight=1.0, dtype=P.PTG_F32):
+              seed=0, persistence=0.5, grad_weight=1.0, dtype=P.PTG_F32, shape=P.PTG_SHAPE_AUTO):
     smooth = SMOOTH.get(kind, P.PTG_C1)
-    variant = P.PTG_PERLIN_S3 if kind == "perlin_s3" else P.PTG_PERLIN_S5
+    variant = (P.PTG_PERLIN_S3 if kind == "perlin_s3" else P.PTG_PERLIN_S5) | shape
     d = P.make_desc(dims=dims, size=size, spc=spc, origin=origin, offset=offset, octaves=octaves,
                     smoothness=smooth, persistence=persistence, grad_weight=grad_weight, seed=seed, dtype=dtype,
                     variant=variant)
@@ -193,6 +193,52 @@ def test_3d_ragged(ctx):
         idx = W.grid_indices_3d(*size)
         ref = oracle_at(kind, idx, dims=3, spc=spc, octaves=N, origin=(-7, 3, -(1 << 30)), seed=2)
         assert np.abs(gather(out, idx) - ref).max() <= tol32(N)
+
+
+# ---------------------------------------------------------------------------
+# both 2D thread shapes (8 x 4 and 16 x 2 samples a thread) against the oracle
+# ---------------------------------------------------------------------------
+SHAPES = [P.PTG_SHAPE_8X4, P.PTG_SHAPE_16X2]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3", "paper_gauge", "zero_grad"])
+@pytest.mark.parametrize("size,spc,octaves", [
+    ((256, 256), 64, 6),      # run octaves of 64/32/16-sample cells, then 8, 4, 2
+    ((200, 136), 16, 7),      # ragged; one 16-wide run octave, 8/4/2, lattice
+    ((130, 70), 2048, 13),    # eight run octaves, 8/4/2, lattice
+    ((96, 80), 8, 5),         # no 16-wide run octave
+])
+def test_thread_shapes_vs_oracle(ctx, kind, shape, size, spc, octaves):
+    origin = (-(1 << 20) + 3, 12345, 0)
+    out = gpu_field(ctx, kind, size=size, spc=spc, octaves=octaves, origin=origin, seed=21, persistence=0.6,
+                    grad_weight=0.75, shape=shape)
+    assert P.ptg_thread_shape(ctx, P.make_desc(dims=2, size=size, spc=spc, octaves=octaves, variant=shape)) == \
+        (8 if shape == P.PTG_SHAPE_8X4 else 16)
+    idx = W.grid_indices_2d(*size)
+    ref = oracle_at(kind, idx, spc=spc, octaves=octaves, origin=origin, seed=21, persistence=0.6, grad_weight=0.75)
+    err = np.abs(gather(out, idx) - ref).max()
+    assert err <= tol32(octaves, 0.6), err
+
+
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "zero_grad"])
+def test_thread_shapes_agree(ctx, kind):
+    """Same field, both shapes: equal up to FP32 rounding (twice the bar)."""
+    a = gpu_field(ctx, kind, size=(1024, 512), spc=256, octaves=10, seed=3, shape=P.PTG_SHAPE_8X4)
+    b = gpu_field(ctx, kind, size=(1024, 512), spc=256, octaves=10, seed=3, shape=P.PTG_SHAPE_16X2)
+    assert float((a - b).abs().max()) <= 2 * tol32(10)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_thread_shape_fp16_and_mosaic(ctx, shape):
+    big = gpu_field(ctx, "c2", size=(512, 384), spc=128, octaves=9, origin=(11, -4, 0), seed=8,
+                    dtype=P.PTG_F16, shape=shape)
+    idx = W.subsample((512, 384), every=64, n_random=4096, seed=2)
+    ref = oracle_at("c2", idx, spc=128, octaves=9, origin=(11, -4, 0), seed=8)
+    assert np.all(np.abs(gather(big, idx) - ref) <= tol32(9) + half_ulp16(ref))
+    part = gpu_field(ctx, "c2", size=(256, 192), spc=128, octaves=9, origin=(11, -4, 0), offset=(256, 192, 0),
+                     seed=8, dtype=P.PTG_F16, shape=shape)
+    assert torch.equal(part, big[192:384, 256:512])
 
 
 # ---------------------------------------------------------------------------
