@@ -230,8 +230,8 @@ def bench_batched(P, ctx, stream, torch, n_chunks=4096, reps=5):
     n_samples = sum(c["size"][0] * c["size"][1] for c in chunks)
     shapes = {}
     for d in descs:
-        rw = P.ptg_thread_shape(ctx, d)
-        key = "%dx%d" % (rw, 32 // rw)
+        rw, nt = P.ptg_launch_config(ctx, d)
+        key = "%dx%d%s" % (rw, 32 // rw, " tile" if nt else "")
         shapes[key] = shapes.get(key, 0) + 1
     plan = P.ptg_batch_prepare(ctx, descs, outs)
     for _ in range(2):
@@ -262,7 +262,7 @@ def bench_batched(P, ctx, stream, torch, n_chunks=4096, reps=5):
     del outs
     return {"workload": "%d 2D chunks, side log-uniform 64..1024, octaves 4..12, C1/C2 50/50, spc 1024, "
                         "seeds = chunk id, origins uniform in +-2^20 cells, FP32 out" % n_chunks,
-            "samples": n_samples, "thread_shapes": shapes,
+            "samples": n_samples, "launch_configs": shapes,
             "batched_graph_ms": ms_batch, "batched_gsamples_s": n_samples / ms_batch / 1e6,
             "per_chunk_launches_ms": ms_single, "per_chunk_gsamples_s": n_samples / ms_single / 1e6,
             "per_chunk_host_wall_ms": wall_single,
@@ -445,8 +445,8 @@ def main():
     props = torch.cuda.get_device_properties(local)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = R.alu_peak(props.multi_processor_count, sm_max)
-    rw = P.ptg_thread_shape(ctx, descs[0])
-    ops = R.lane_ops_2d("c1", SIZE, SPC, OCTAVES, rw)
+    rw, nt = P.ptg_launch_config(ctx, descs[0])
+    ops = R.lane_ops_2d("c1", SIZE, SPC, OCTAVES, rw, nt)
     achieved = ops["total"] / avg_launch_s
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tlane-ops/s",
             "frac": achieved / peak, "traffic": profile_traffic(),
@@ -465,7 +465,8 @@ def main():
         "config": {"workload": WORKLOAD, "global_batch": world, "samples_per_step": world * n_samples,
                    "parallelism": "replicas (independent fields per rank)" if world > 1 else "single GPU",
                    "l2": "output 268 MB > 129 MB L2 each step; no flush",
-                   "thread_shape": "%dx%d (autotuned in %.2f s)" % (rw, 32 // rw, t_tune)},
+                   "launch_config": "thread shape %dx%d, %d octaves at the tile nodes (autotuned in %.2f s)" % (
+                       rw, 32 // rw, nt, t_tune)},
         "p50_ms": per[len(per) // 2], "p99_ms": per[min(len(per) - 1, int(0.99 * len(per)))],
         "gpu_launches": args.steps,
         "roofline": roof,
@@ -508,14 +509,14 @@ def main():
                    "paper_d2m1n3_f32": (dG, P.METHOD_FIELD), "opensimplex_f32": (None, None)}
         for k, v in extras.items():
             d_k, m_k = ex_desc[k]
-            rw_k = P.ptg_thread_shape(ctx, d_k, m_k) if d_k is not None else 8
+            rw_k, nt_k = P.ptg_launch_config(ctx, d_k, m_k) if d_k is not None else (8, 0)
             if d_k is not None:
-                v["thread_shape"] = "%dx%d" % (rw_k, 32 // rw_k)
+                v["launch_config"] = "%dx%d, %d tile octaves" % (rw_k, 32 // rw_k, nt_k)
             v["ops_per_sample"] = R.lane_ops_2d({"c2_f32": "c2", "c1_f16": "c1", "perlin_s5_f32": "perlin_s5",
                                                  "zero_gradient_f32": "zero_grad",
                                                  "paper_d2m1n3_f32": "paper_gauge",
                                                  "opensimplex_f32": "opensimplex"}[k], SIZE, SPC,
-                                                OCTAVES, rw_k)["per_sample"]
+                                                OCTAVES, rw_k, nt_k)["per_sample"]
         line["baselines"] = extras
         if rank == 0:
             line["volume3d_512_n8"] = bench_3d(P, R, ctx, stream, torch)

@@ -92,6 +92,19 @@ typedef enum { PTG_PERLIN_S5 = 0, PTG_PERLIN_S3 = 1 } ptg_perlin_blend;
  * paper: a GPU tuning choice. */
 typedef enum { PTG_SHAPE_AUTO = 0, PTG_SHAPE_8X4 = 0x100, PTG_SHAPE_16X2 = 0x200 } ptg_shape;
 
+/* How the 2D generators evaluate the octaves whose cells cover a whole
+ * 64 x 64 tile (cells of at least 64 samples), or-ed into desc->variant.
+ * Each such octave is one polynomial of degree d per axis over the tile, and
+ * so is their sum (Sec. 2.2: the cell polynomial; Sec. 4: the octave sum).
+ * RUNS evaluates each octave at every thread's node columns, as the finer
+ * octaves are; TILE evaluates their sum once per tile at (d + 1)^2 nodes and
+ * interpolates it (degree <= 4 models: C1, the paper's D2M1N3 and
+ * zero-gradient models, Perlin S3).  AUTO: the context's tuned choice, else a
+ * fixed rule.  Both compute the same field up to FP32 rounding; like the
+ * thread shape, the choice depends on the method, dtype, spc and octave count
+ * only.  No counterpart in the paper: a GPU tuning choice. */
+typedef enum { PTG_COARSE_AUTO = 0, PTG_COARSE_RUNS = 0x400, PTG_COARSE_TILE = 0x800 } ptg_coarse;
+
 /* Full description of one field (Sec. 2.1 cell lattice, Sec. 4 octaves). */
 typedef struct {
     uint32_t struct_size; /* sizeof(ptg_field_desc)                            */
@@ -110,7 +123,8 @@ typedef struct {
     uint32_t seed;        /* < 2^24                                            */
     int32_t dtype;        /* ptg_dtype                                         */
     int32_t variant;      /* low byte: ptg_perlin_blend for ptg_perlin, else 0;
-                             bits 8..9: ptg_shape (2D field / Perlin only)     */
+                             bits 8..9: ptg_shape, bits 10..11: ptg_coarse
+                             (2D field / Perlin only)                          */
 } ptg_field_desc;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
@@ -221,22 +235,28 @@ int ptg_wait(ptg_ctx* ctx, uint64_t req_id, uint64_t timeout_ns);
  * request is unknown or already admitted. */
 int ptg_cancel(ptg_ctx* ctx, uint64_t req_id);
 
-/* Autotuner for the 2D thread shape (ptg_shape).  For every 2D method, dtype
- * and octave structure -- n16 = octaves whose cells are at least 16 samples
- * wide (min(N, log2(spc) - 3), capped at 8) and whether finer octaves follow
- * -- time both shapes on a 4096 x 4096 field (effort timed launches each,
- * 0 = 5) and keep the faster in the context; AUTO fields use the table from
- * then on.  cache_path (may be NULL): if the file exists and was written for
- * this device model and SM count, load the table from it instead of timing;
- * otherwise time and write it (JSON).  Blocks; allocates one 64 MiB scratch
- * field for the duration.  Returns PTG_OK, PTG_ERR_CUDA, or PTG_ERR_INVALID
- * (bad arguments, unreadable cache).  No counterpart in the paper. */
+/* Autotuner for the 2D launch configuration: the thread shape (ptg_shape)
+ * and the coarse-octave mode (ptg_coarse).  For every 2D method, dtype and
+ * octave structure -- the number of octaves with cells of at least 64
+ * samples (capped at 8), of 16 to 32 samples (0..2), and whether finer
+ * octaves follow -- time every configuration on an 8192 x 8192 field (effort
+ * timed launches each, 0 = 5) and keep the fastest in the context; AUTO
+ * fields use the table from then on.  cache_path (may be NULL): if the file
+ * exists and was written for this device model and SM count, load the table
+ * from it instead of timing; otherwise time and write it (JSON).  Call it
+ * before other work on the context.  Blocks (about a second); allocates one
+ * 256 MiB scratch field for the duration.  Returns PTG_OK, PTG_ERR_CUDA, or PTG_ERR_INVALID
+ * (bad arguments, a cache file that is not a table, a cache that cannot be
+ * written).  No counterpart in the paper. */
 int ptg_autotune(ptg_ctx* ctx, int32_t effort, const char* cache_path);
 
-/* The thread shape (8 for 8 x 4, 16 for 16 x 2) that generator `method`
- * (0 = ptg_field, 1 = ptg_perlin) would use for desc on this context, in *rw.
- * Returns PTG_OK or the validation status of desc. */
-int ptg_thread_shape(ptg_ctx* ctx, const ptg_field_desc* desc, int32_t method, int32_t* rw);
+/* The launch configuration that generator `method` (0 = ptg_field,
+ * 1 = ptg_perlin) would use for desc on this context: *rw = 8 (8 x 4) or
+ * 16 (16 x 2); *tile_octaves = how many octaves are summed at the tile nodes
+ * (0 = none).  Either pointer may be NULL.  Returns PTG_OK or the validation
+ * status of desc. */
+int ptg_launch_config(ptg_ctx* ctx, const ptg_field_desc* desc, int32_t method, int32_t* rw,
+                      int32_t* tile_octaves);
 
 /* Check a descriptor for generator `method` (0 = ptg_field, 1 = ptg_perlin,
  * 2 = ptg_opensimplex) without touching any device: returns the status the

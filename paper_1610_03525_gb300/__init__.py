@@ -22,6 +22,7 @@ PTG_C1, PTG_C2, PTG_PAPER_D2M1N3, PTG_ZERO_GRADIENT = 1, 2, 3, 4
 PTG_F32, PTG_F16 = 0, 1
 PTG_PERLIN_S5, PTG_PERLIN_S3 = 0, 1
 PTG_SHAPE_AUTO, PTG_SHAPE_8X4, PTG_SHAPE_16X2 = 0, 0x100, 0x200
+PTG_COARSE_AUTO, PTG_COARSE_RUNS, PTG_COARSE_TILE = 0, 0x400, 0x800
 METHOD_FIELD, METHOD_PERLIN, METHOD_OPENSIMPLEX = 0, 1, 2
 
 STATUS_NAMES = {
@@ -87,7 +88,7 @@ def lib():
             "ptg_cancel": ([P, U64], ctypes.c_int),
             "ptg_debug_hold": ([P, I32], ctypes.c_int),
             "ptg_autotune": ([P, I32, ctypes.c_char_p], ctypes.c_int),
-            "ptg_thread_shape": ([P, P, I32, ctypes.POINTER(I32)], ctypes.c_int),
+            "ptg_launch_config": ([P, P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
             "ptg_last_error": ([P], ctypes.c_char_p),
             "ptg_validate": ([P, I32, ctypes.c_char_p, I32], ctypes.c_int),
             "ptg_debug_hash": ([P, I32, P, I64, P, P], ctypes.c_int),
@@ -302,17 +303,18 @@ def ptg_cancel(ctx: Context, req_id: int) -> int:
 
 
 def ptg_autotune(ctx: Context, effort: int = 0, cache_path: str | None = None) -> int:
-    """Time both 2D thread shapes per octave structure and keep the faster
-    (or load the table from cache_path, writing it after timing)."""
+    """Time the 2D launch configurations per octave structure and keep the
+    fastest (or load the table from cache_path, writing it after timing)."""
     path = cache_path.encode() if cache_path else None
     return _check(ctx, lib().ptg_autotune(ctx.handle, effort, path))
 
 
-def ptg_thread_shape(ctx: Context, desc: ptg_field_desc, method: int = METHOD_FIELD) -> int:
-    """Run width (8 or 16) that generator `method` would use for desc."""
-    rw = ctypes.c_int32(0)
-    _check(ctx, lib().ptg_thread_shape(ctx.handle, ctypes.byref(desc), method, ctypes.byref(rw)))
-    return rw.value
+def ptg_launch_config(ctx: Context, desc: ptg_field_desc, method: int = METHOD_FIELD):
+    """(run width 8 or 16, octaves summed at the tile nodes) that generator
+    `method` would use for desc on this context."""
+    rw, nt = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(ctx, lib().ptg_launch_config(ctx.handle, ctypes.byref(desc), method, ctypes.byref(rw), ctypes.byref(nt)))
+    return rw.value, nt.value
 
 
 def ptg_debug_hold(ctx: Context, hold: int) -> int:

@@ -74,15 +74,20 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
         return ptg_fail(ctx, PTG_ERR_INVALID, "smoothness must be a ptg_smoothness value");
     if (kind == kKindField && d->dims == 3 && d->smoothness != PTG_C1 && d->smoothness != PTG_C2)
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "the paper's D2M1N3 and zero-gradient models are 2D");
-    const int blend = d->variant & 0xff, shape = d->variant & ~0xff;
-    if (shape != PTG_SHAPE_AUTO && shape != PTG_SHAPE_8X4 && shape != PTG_SHAPE_16X2)
-        return ptg_fail(ctx, PTG_ERR_INVALID, "variant: unknown thread-shape bits 0x%x", (unsigned)shape);
+    const int blend = d->variant & 0xff, shape = d->variant & 0x300, coarse = d->variant & 0xc00;
+    if (d->variant & ~0xfff) return ptg_fail(ctx, PTG_ERR_INVALID, "variant: unknown bits 0x%x", (unsigned)d->variant);
+    if (shape == 0x300) return ptg_fail(ctx, PTG_ERR_INVALID, "variant: unknown thread-shape bits");
+    if (coarse == 0xc00) return ptg_fail(ctx, PTG_ERR_INVALID, "variant: unknown coarse-octave bits");
     if (kind == kKindPerlin && blend != PTG_PERLIN_S5 && blend != PTG_PERLIN_S3)
         return ptg_fail(ctx, PTG_ERR_INVALID, "Perlin variant must be PTG_PERLIN_S5 or PTG_PERLIN_S3");
     if (kind != kKindPerlin && blend != 0)
         return ptg_fail(ctx, PTG_ERR_INVALID, "variant: the low byte is the Perlin blend, 0 for other generators");
-    if (shape != PTG_SHAPE_AUTO && (kind == kKindSimplex || d->dims != 2))
-        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "a thread shape applies to 2D polynomial and Perlin fields");
+    if ((shape | coarse) != 0 && (kind == kKindSimplex || d->dims != 2))
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "thread shape and coarse-octave mode apply to 2D polynomial and "
+                                                  "Perlin fields");
+    if (coarse == PTG_COARSE_TILE && ((kind == kKindField && d->smoothness == PTG_C2) ||
+                                      (kind == kKindPerlin && blend == PTG_PERLIN_S5)))
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "tile nodes apply to models of degree <= 4 (not C2, not Perlin S5)");
     if (!std::isfinite(d->persistence) || !std::isfinite(d->grad_weight))
         return ptg_fail(ctx, PTG_ERR_INVALID, "persistence and grad_weight must be finite");
     if (!std::isfinite(d->lacunarity)) return ptg_fail(ctx, PTG_ERR_INVALID, "lacunarity must be finite");
@@ -160,7 +165,9 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
     P->ncount = count;
     P->method = method;
     P->s = s;
-    P->rw = is3d ? 8 : ptg_pick_rw(ctx, d, method, s);
+    P->rw = 8;
+    P->nt = 0;
+    if (!is3d) ptg_pick_config(ctx, d, method, s, &P->rw, &P->nt);
     const size_t smem = is3d ? fbm3d_smem_bytes(*P) : fbm2d_smem_bytes(*P);
     if (smem > (size_t)ctx->max_smem)
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "staging needs %zu bytes of shared memory (max %d)", smem,

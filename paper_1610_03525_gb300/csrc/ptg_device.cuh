@@ -59,6 +59,8 @@ struct FieldPlan {
     int32_t method;         // kC1, kC2, kPerlinS5, kPerlinS3
     int32_t s;              // log2(samples per cell)
     int32_t rw;             // 2D thread shape: run width 8 (8 x 4 samples a thread) or 16 (16 x 2)
+    int32_t nt;             // 2D: octaves summed at the tile nodes (cells >= 64 samples), 0 = none
+    int32_t pad[3];
     OctPlan oct[kMaxOctaves];
 };
 static_assert(sizeof(FieldPlan) % 16 == 0, "FieldPlan is copied in 16-byte words");

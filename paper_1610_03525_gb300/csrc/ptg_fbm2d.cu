@@ -15,8 +15,12 @@
 // with the corner constraints of Eq. (mixedderiv) and zero mixed derivatives,
 // or Perlin's polynomial (Sec. 3.2) with v = 0 and its own B0, B1.
 //
-// Octave i has cells of spc_i = spc / 2^i samples.  Three regimes:
-//   spc_i >= RW ("run" octaves): a thread's run lies in one cell, so each of
+// Octave i has cells of spc_i = spc / 2^i samples.  Four regimes:
+//   spc_i >= 64 ("tile" octaves): the cell covers the whole tile, so each
+//     octave -- and their sum -- is one polynomial of degree d per axis over
+//     the tile.  The CTA evaluates that sum at (d + 1)^2 tile nodes once and
+//     every thread interpolates it to its own node columns.
+//   RW <= spc_i < 64 ("run" octaves): a thread's run lies in one cell, so each of
 //     its rows is one polynomial of degree d in the column (d = 3 for C1, 5 for
 //     C2, 4 / 6 for Perlin S3 / S5), and so is the sum over all such octaves.
 //     The kernel evaluates d + 1 node columns per octave and fills the other
@@ -52,12 +56,22 @@ struct Shape {
 };
 static_assert(Shape<8>::TXN * Shape<8>::TYN == kThreads && Shape<16>::TXN * Shape<16>::TYN == kThreads, "");
 
-// Shared-memory layout (float4 units):
-//   x-basis of run octaves at node columns [nrun][D+1][TXN],
-//   y-basis of run octaves [nrun][RR rows][TYN] (64 per octave),
-//   staged corners of every staged octave (rows swizzled by corner_slot).
+// Shared-memory layout (float4 units), with nr = run octaves that are not
+// tile octaves:
+//   x-basis of those run octaves at node columns [nr][D+1][TXN],
+//   y-basis of those run octaves [nr][RR rows][TYN] (64 per octave),
+//   staged corners of every staged octave (rows swizzled by corner_slot),
+//   with tile octaves: the tile nodes' values [D+1][LW], then a copy of the
+//   interpolation weights (TileWeights) made while the corners are hashed.
 template <int METHOD, int RW>
-__host__ __device__ constexpr int xnode_words(int nrun) { return nrun * (Deg<METHOD>::value + 1) * Shape<RW>::TXN; }
+__host__ __device__ constexpr int xnode_words(int nr) { return nr * (Deg<METHOD>::value + 1) * Shape<RW>::TXN; }
+
+template <int METHOD, int RW>
+__host__ __device__ constexpr int grid_words()  // float4 words: tile nodes' values, then their weights
+{
+    return ((Deg<METHOD>::value + 1) * TileWeights<Deg<METHOD>::value, RW>::LW +
+            (int)sizeof(TileWeights<Deg<METHOD>::value, RW>) / 4) / 4;
+}
 
 template <int RW>
 __host__ __device__ __forceinline__ int n_run(const FieldPlan& P)  // octaves with cells >= RW samples
@@ -66,25 +80,44 @@ __host__ __device__ __forceinline__ int n_run(const FieldPlan& P)  // octaves wi
     return n < 0 ? 0 : (n < P.N ? n : P.N);
 }
 
+// Tile octaves: octaves with cells >= 64 samples that the host chose to sum
+// at the tile nodes (P.nt; never for degree > 4, where the (d+1)^2 nodes cost
+// about what they save).
+template <int METHOD>
+__host__ __device__ __forceinline__ int n_tile(const FieldPlan& P)
+{
+    return Deg<METHOD>::value <= 4 ? P.nt : 0;
+}
+
+// Interpolation weights of the tile nodes (compile-time tables).
+template <int D, int RW>
+__device__ const TileWeights<D, RW> kTileWeights = make_tile_weights<D, RW>();
+
 template <int METHOD, int RW>
 __device__ __forceinline__ void stage_tile(const FieldPlan& P, float4* sm, int j0x, int j0y)
 {
     using SH = Shape<RW>;
     constexpr int D = Deg<METHOD>::value, NN = D + 1;
-    const int tid = threadIdx.x, s = P.s, nrun = n_run<RW>(P);
+    const int tid = threadIdx.x, s = P.s, nt = n_tile<METHOD>(P), nr = n_run<RW>(P) - nt;
     float4* xnode = sm;
-    float4* ylut = sm + xnode_words<METHOD, RW>(nrun);
-    float4* corners = ylut + nrun * 64;
-    for (int e = tid; e < nrun * NN * SH::TXN; e += kThreads) {
+    float4* ylut = sm + xnode_words<METHOD, RW>(nr);
+    float4* corners = ylut + nr * 64;
+    for (int e = tid; e < nr * NN * SH::TXN; e += kThreads) {
         const int i = e / (NN * SH::TXN), rem = e - i * (NN * SH::TXN);
         const int q = rem / SH::TXN, tx = rem % SH::TXN;
         const int col = tx * RW + node_col<D, RW>(q);
-        xnode[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0x + col), i, s));
+        xnode[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0x + col), nt + i, s));
     }
-    for (int e = tid; e < nrun * 64; e += kThreads) {  // stored in table order: conflict-free
+    for (int e = tid; e < nr * 64; e += kThreads) {  // stored in table order: conflict-free
         const int i = e >> 6, slot = e & 63;
         const int row = (slot % SH::TYN) * SH::RR + slot / SH::TYN;
-        ylut[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0y + row), i, s));
+        ylut[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0y + row), nt + i, s));
+    }
+    if (D <= 4 && nt > 0) {  // weights of the tile nodes, global -> shared (latency hidden by the hashing below)
+        constexpr int NW = (int)sizeof(TileWeights<D, RW>) / 16;
+        const float4* src = reinterpret_cast<const float4*>(&kTileWeights<D, RW>);
+        float4* dst = corners + P.ncorner + NN * TileWeights<D, RW>::LW / 4;
+        for (int e = tid; e < NW; e += kThreads) dst[e] = __ldg(src + e);
     }
     // Corners, octave by octave (uniform loops: every lane of a warp reads the
     // same octave parameters).  Octaves with at most 32 corners go to one warp
@@ -133,23 +166,24 @@ __device__ __forceinline__ Cell load_cell(const float4* __restrict__ cg, int row
 }
 
 // A run octave: node columns only.
+// i = octave, ti = its slot in the basis tables (i minus the tile octaves).
 template <int METHOD, int RW>
 __device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
-                                           const float4* __restrict__ sm, const FieldPlan& P, int i, int tx,
-                                           int ty, int nrun)
+                                           const float4* __restrict__ sm, const FieldPlan& P, int i, int ti,
+                                           int tx, int ty, int nr)
 {
     using SH = Shape<RW>;
     constexpr int NN = Deg<METHOD>::value + 1;
     const OctPlan& op = P.oct[i];
-    const float4* ylut = sm + xnode_words<METHOD, RW>(nrun);
-    const float4* cg = ylut + nrun * 64 + op.coff;
+    const float4* ylut = sm + xnode_words<METHOD, RW>(nr);
+    const float4* cg = ylut + nr * 64 + op.coff;
     const Cell c = load_cell(cg, op.rowlen, (tx * RW) >> op.k, (ty * SH::RR) >> op.k);
     float4 xb[NN];
 #pragma unroll
-    for (int q = 0; q < NN; ++q) xb[q] = sm[(i * NN + q) * SH::TXN + tx];
+    for (int q = 0; q < NN; ++q) xb[q] = sm[(ti * NN + q) * SH::TXN + tx];
 #pragma unroll
     for (int r = 0; r < SH::RR; ++r) {
-        const float4 yb = ylut[i * 64 + r * SH::TYN + ty];
+        const float4 yb = ylut[ti * 64 + r * SH::TYN + ty];
         const Row R = Model<METHOD>::row(c, yb);
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] += Model<METHOD>::eval(R, xb[q]);
@@ -162,13 +196,13 @@ __device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METH
 // on the thread's row and the row basis is evaluated once per octave.
 template <int METHOD, int RW, int CW>
 __device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], const float4* __restrict__ sm,
-                                             const FieldPlan& P, int i, int tx, int ty, int nrun)
+                                             const FieldPlan& P, int i, int tx, int ty, int nr)
 {
     using SH = Shape<RW>;
     constexpr int RR = SH::RR, NXC = RW / CW, RPC = RR < CW ? RR : CW, NYC = RR / RPC;
     constexpr bool kConstRows = RR >= CW;
     const OctPlan& op = P.oct[i];
-    const float4* cg = sm + xnode_words<METHOD, RW>(nrun) + nrun * 64 + op.coff;
+    const float4* cg = sm + xnode_words<METHOD, RW>(nr) + nr * 64 + op.coff;
     constexpr float inv = 1.0f / CW;
     float4 yb[RPC];
 #pragma unroll
@@ -190,6 +224,74 @@ __device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], co
                     acc[yq * RPC + rr][xq * CW + q] += h;
                 }
             }
+        }
+    }
+}
+
+// Tile octaves, CTA part: the sum of octaves 0 .. nt-1 at the (d+1)^2 tile
+// nodes, into G[q][r] (row stride LW).  Each node is summed by PARTS
+// consecutive lanes, octaves dealt round-robin, then added across the lanes
+// with a fixed butterfly (the same bits in every lane and on every run).
+template <int METHOD>
+__device__ __forceinline__ void tile_grid(const FieldPlan& P, const float4* __restrict__ corners, float* G,
+                                          int j0x, int j0y, int nt)
+{
+    constexpr int D = Deg<METHOD>::value, NN = D + 1, NG = NN * NN, LW = TileWeights<D, 8>::LW;
+    constexpr int PARTS = NG <= 16 ? 8 : (NG <= 32 ? 4 : 2);
+    static_assert(NG <= kThreads / PARTS, "one lane group per node");
+    const int tid = threadIdx.x, node = tid / PARTS, part = tid % PARTS;
+    const int q = node / NN, r = node - q * NN;
+    float v = 0.0f;
+    if (node < NG) {
+        const uint32_t jx = (uint32_t)(j0x + tile_node<D>(q)), jy = (uint32_t)(j0y + tile_node<D>(r));
+        for (int i = part; i < nt; i += PARTS) {
+            const OctPlan& op = P.oct[i];
+            const Cell c = load_cell(corners + op.coff, op.rowlen, 0, 0);
+            const Row R = Model<METHOD>::row(c, axis_basis<METHOD>(axis_t(jy, i, P.s)));
+            v += Model<METHOD>::eval(R, axis_basis<METHOD>(axis_t(jx, i, P.s)));
+        }
+    }
+#pragma unroll
+    for (int o = PARTS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (node < NG && part == 0) G[q * LW + r] = v;
+}
+
+// Tile octaves, thread part: the tile polynomial at the thread's rows and
+// node columns, added to the node accumulators.
+template <int METHOD, int RW>
+__device__ __forceinline__ void add_tile_grid(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
+                                              const float* __restrict__ G, int tx, int ty)
+{
+    using SH = Shape<RW>;
+    constexpr int D = Deg<METHOD>::value, NN = D + 1, LW = TileWeights<D, RW>::LW;
+    const TileWeights<D, RW>& W = *reinterpret_cast<const TileWeights<D, RW>*>(G + NN * LW);
+    float Rq[SH::RR][NN];  // tile polynomial at the thread's rows, tile columns q
+#pragma unroll
+    for (int r = 0; r < SH::RR; ++r) {
+        const float* ly = W.ly[ty * SH::RR + r];
+        float w[NN];
+#pragma unroll
+        for (int m = 0; m < NN; ++m) w[m] = ly[m];
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            float a = 0.0f;
+#pragma unroll
+            for (int m = 0; m < NN; ++m) a = fmaf(w[m], G[q * LW + m], a);
+            Rq[r][q] = a;
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NN; ++n) {
+        const float* lx = W.lx[tx][n];
+        float w[NN];
+#pragma unroll
+        for (int q = 0; q < NN; ++q) w[q] = lx[q];
+#pragma unroll
+        for (int r = 0; r < SH::RR; ++r) {
+            float a = 0.0f;
+#pragma unroll
+            for (int q = 0; q < NN; ++q) a = fmaf(w[q], Rq[r][q], a);
+            nacc[r][n] += a;
         }
     }
 }
@@ -261,9 +363,14 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     const int tid = threadIdx.x, tx = tid % SH::TXN, ty = tid / SH::TXN;
     const int x0 = bx * kTW, y0 = by * kTH;        // output tile origin
     const int j0x = x0 + P.jx0, j0y = y0 + P.jy0;  // sample indices
-    const int s = P.s, N = P.N, nrun = n_run<RW>(P);
+    const int s = P.s, N = P.N, nt = n_tile<METHOD>(P), nrun = n_run<RW>(P), nr = nrun - nt;
     stage_tile<METHOD, RW>(P, sm, j0x, j0y);
     __syncthreads();
+
+    // tile octaves: their sum at the tile nodes (read back after the barrier below)
+    const float4* corners = sm + xnode_words<METHOD, RW>(nr) + nr * 64;
+    float* G = reinterpret_cast<float*>(sm + xnode_words<METHOD, RW>(nr) + nr * 64 + P.ncorner);
+    if (Deg<METHOD>::value <= 4 && nt > 0) tile_grid<METHOD>(P, corners, G, j0x, j0y, nt);
 
     // run octaves: node columns, then interpolate the other columns once
     float nacc[RR][NN];
@@ -271,7 +378,11 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     for (int r = 0; r < RR; ++r)
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
-    for (int i = 0; i < nrun; ++i) run_octave<METHOD, RW>(nacc, sm, P, i, tx, ty, nrun);
+    for (int i = nt; i < nrun; ++i) run_octave<METHOD, RW>(nacc, sm, P, i, i - nt, tx, ty, nr);
+    if (Deg<METHOD>::value <= 4 && nt > 0) {  // uniform over the CTA
+        __syncthreads();
+        add_tile_grid<METHOD, RW>(nacc, G, tx, ty);
+    }
     float acc[RR][RW];
 #pragma unroll
     for (int r = 0; r < RR; ++r)
@@ -289,9 +400,9 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
         }
 
     // cells narrower than the run (8, 4 and 2 samples), then lattice octaves
-    if (RW == 16 && s >= 3 && s - 3 < N) small_octave<METHOD, RW, (RW == 16 ? 8 : 4)>(acc, sm, P, s - 3, tx, ty, nrun);
-    if (s >= 2 && s - 2 < N) small_octave<METHOD, RW, 4>(acc, sm, P, s - 2, tx, ty, nrun);
-    if (s >= 1 && s - 1 < N) small_octave<METHOD, RW, 2>(acc, sm, P, s - 1, tx, ty, nrun);
+    if (RW == 16 && s >= 3 && s - 3 < N) small_octave<METHOD, RW, (RW == 16 ? 8 : 4)>(acc, sm, P, s - 3, tx, ty, nr);
+    if (s >= 2 && s - 2 < N) small_octave<METHOD, RW, 4>(acc, sm, P, s - 2, tx, ty, nr);
+    if (s >= 1 && s - 1 < N) small_octave<METHOD, RW, 2>(acc, sm, P, s - 1, tx, ty, nr);
     if (METHOD != kPerlinS5 && METHOD != kPerlinS3)
         for (int i = s; i < N; ++i)
             lattice_octave<RW>(acc, P.oct[i], (uint32_t)(j0x + tx * RW), (uint32_t)(j0y + ty * RR));
@@ -368,12 +479,10 @@ __global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* 
 template <int METHOD>
 size_t smem_words(const FieldPlan& P)
 {
-    if (P.rw == 16) {
-        const int nrun = n_run<16>(P);
-        return (size_t)xnode_words<METHOD, 16>(nrun) + (size_t)nrun * 64 + (size_t)P.ncorner;
-    }
-    const int nrun = n_run<8>(P);
-    return (size_t)xnode_words<METHOD, 8>(nrun) + (size_t)nrun * 64 + (size_t)P.ncorner;
+    const int nt = n_tile<METHOD>(P), nr = (P.rw == 16 ? n_run<16>(P) : n_run<8>(P)) - nt;
+    const size_t grid = nt > 0 ? (size_t)(P.rw == 16 ? grid_words<METHOD, 16>() : grid_words<METHOD, 8>()) : 0;
+    const size_t xw = P.rw == 16 ? (size_t)xnode_words<METHOD, 16>(nr) : (size_t)xnode_words<METHOD, 8>(nr);
+    return xw + (size_t)nr * 64 + (size_t)P.ncorner + grid;
 }
 
 template <typename K>

@@ -55,14 +55,17 @@ struct ptg_ctx {
     cudaEvent_t batch_uploaded = nullptr;
     // request loop
     PtgServer* server = nullptr;
-    // 2D thread-shape table filled by ptg_autotune: run width (8 / 16) per
-    // [method index][dtype][n16 0..8][finer octaves follow], 0 = untuned
-    uint8_t tune_rw[6][2][9][2] = {};
+    // 2D launch-configuration table filled by ptg_autotune, per [method
+    // index][dtype][tile octaves 0..8][16..32-sample-cell octaves 0..2][finer
+    // octaves follow]: run width (8 / 16) | 0x80 when the tile octaves are
+    // summed at the tile nodes; 0 = untuned
+    uint8_t tune[6][2][9][3][2] = {};
 };
 
-// Run width (8 or 16) of a 2D polynomial / Perlin field: the shape bits of
-// desc->variant, else the context's tuned table, else the fixed rule.
-int ptg_pick_rw(const ptg_ctx* ctx, const ptg_field_desc* d, int method, int s);
+// Launch configuration of a 2D polynomial / Perlin field: run width (8 or 16)
+// and the number of octaves summed at the tile nodes.  The variant bits of
+// desc win, then the context's tuned table, then the fixed rule.
+void ptg_pick_config(const ptg_ctx* ctx, const ptg_field_desc* d, int method, int s, int32_t* rw, int32_t* nt);
 
 int ptg_fail(ptg_ctx* ctx, int code, const char* fmt, ...);
 int ptg_cuda_fail(ptg_ctx* ctx, cudaError_t e, const char* where);

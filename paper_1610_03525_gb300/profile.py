@@ -20,6 +20,8 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--shape", default="auto", choices=["auto", "8x4", "16x2"], help="2D thread shape")
+    ap.add_argument("--coarse", default="auto", choices=["auto", "runs", "tile"], help="2D coarse-octave mode")
+    ap.add_argument("--tune-cache", default=None, help="launch-config table to load (as bench.py --tune-cache)")
     args = ap.parse_args()
 
     import torch
@@ -31,17 +33,20 @@ def main():
     d = P.make_desc(dims=dims, size=tuple(args.size), spc=args.spc, origin=tuple(args.origin) + (0,) * 3,
                     octaves=args.octaves, smoothness=P.PTG_C2 if args.kind == "c2" else P.PTG_C1,
                     variant=(P.PTG_PERLIN_S3 if args.kind == "perlin_s3" else P.PTG_PERLIN_S5) |
-                    {"auto": P.PTG_SHAPE_AUTO, "8x4": P.PTG_SHAPE_8X4, "16x2": P.PTG_SHAPE_16X2}[args.shape],
+                    {"auto": P.PTG_SHAPE_AUTO, "8x4": P.PTG_SHAPE_8X4, "16x2": P.PTG_SHAPE_16X2}[args.shape] |
+                    {"auto": P.PTG_COARSE_AUTO, "runs": P.PTG_COARSE_RUNS, "tile": P.PTG_COARSE_TILE}[args.coarse],
                     dtype=dtype)
     out = torch.empty(tuple(reversed(args.size)), dtype=torch.float16 if dtype == P.PTG_F16 else torch.float32,
                       device="cuda")
     ctx = P.ptg_create(0)
+    if args.tune_cache:
+        P.ptg_autotune(ctx, 0, args.tune_cache)
     fn = {"c1": P.ptg_field, "c2": P.ptg_field, "perlin_s5": P.ptg_perlin, "perlin_s3": P.ptg_perlin,
           "opensimplex": P.ptg_opensimplex}[args.kind]
     shape = ""
     if dims == 2 and args.kind != "opensimplex":
-        rw = P.ptg_thread_shape(ctx, d, P.METHOD_PERLIN if args.kind.startswith("perlin") else P.METHOD_FIELD)
-        shape = " (thread shape %dx%d)" % (rw, 32 // rw)
+        rw, nt = P.ptg_launch_config(ctx, d, P.METHOD_PERLIN if args.kind.startswith("perlin") else P.METHOD_FIELD)
+        shape = " (thread shape %dx%d, %d octaves at the tile nodes)" % (rw, 32 // rw, nt)
     for _ in range(args.reps):
         fn(ctx, d, out)
     torch.cuda.synchronize()

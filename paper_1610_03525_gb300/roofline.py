@@ -20,6 +20,11 @@ RW samples wide ("run" octaves):
   run octaves, per thread and octave: prep + RR rows x (row reduction + eval
                 at each of the d+1 node columns); once per thread, RR rows x
                 (RW - d - 1) columns x (d+1) FMA of interpolation;
+  tile octaves (cells >= 64 samples, when summed at the tile nodes): per tile
+                (d+1)^2 nodes x nt x (2 (coordinate + basis) + prep + row + eval)
+                and (lanes a node - 1) adds a node; per thread
+                RR x (d+1)^2 FMA to the thread's rows and RR x (d+1)^2 to its
+                node columns; no basis tables for these octaves;
   cells of CW < RW samples (CW = 8 for RW 16; 4, 2), per thread: RW/CW cells
                 along the run, each with prep + one row reduction per row
                 (row 0 of a cell, where the row is the corner data, costs 1),
@@ -29,12 +34,18 @@ RW samples wide ("run" octaves):
                 (4, 9, 4) for the Hermite cells and Perlin, (4, 4, 3) for the
                 zero-gradient model and (25, 8, 4) for the paper's D2M1N3
                 coefficients;
-  lattice octave: per sample 19 (pcg3d word 0: 13, word->float 3, FMA 1,
-                coordinate 2); Perlin's lattice octaves are zero, no work.
+  lattice octave: per sample 14 -- pcg3d word 0 of (x, y, key) with the
+                row-invariant words' LCG steps and the x-word addend y*z
+                hoisted out of the row: x's LCG step 1 (it advances by a
+                per-octave constant along the run), y and z multiply-adds 2,
+                three xorshifts 6, the final multiply-add 1; word->float 3;
+                FMA 1.  Perlin's lattice octaves are zero, no work.
 3D tiles of 32 x 16 x 8 (each thread 8 x 4 x 1): the same regimes, with a
 reduction along z of the cell's four corner columns (32 ops) before each cell
 is used, basis tables of n8 x (4 (d+1) + 24) entries, corners 42 (pcg4d 20,
-four word->float maps 12, four scalings 4, index 6) and lattice samples 23.
+four word->float maps 12, four scalings 4, index 6) and lattice samples 15
+(pcg4d word 0 with the row-invariant terms hoisted: 1 + 3 multiply-adds + 3
+xorshifts (6) + 1, word->float 3, FMA 1).
 OpenSimplex-style: per sample and octave 150 (4 vertices x 33 + 18).
 """
 from __future__ import annotations
@@ -70,7 +81,7 @@ def small_cell_ops(kind: str, rw: int, cw: int) -> int:
     return ops
 
 
-def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8) -> dict:
+def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8, nt: int = 0) -> dict:
     w, h = size
     tiles = ((w + 63) // 64) * ((h + 63) // 64)
     threads = tiles * 128
@@ -81,21 +92,29 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8) -> dict:
     rr = 32 // rw
     d = DEG[kind]
     st = _staged(spc, octaves)
-    nrun = sum(1 for _, spci in st if spci >= rw)
+    nrun = sum(1 for _, spci in st if spci >= rw) - nt
     lut = tiles * nrun * ((64 // rw) * (d + 1) + 64) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
     evalops = threads * rr * (rw - d - 1) * (d + 1)
     prep, row, smp = MODEL_OPS[kind]
+    if nt:
+        nodes = (d + 1) ** 2
+        parts = 8 if nodes <= 16 else (4 if nodes <= 32 else 2)
+        evalops += tiles * nodes * nt * (2 * (COORD_OPS + BASIS_OPS[kind]) + prep + row + smp)
+        evalops += tiles * nodes * (parts - 1)  # adds across the lanes of a node
+        evalops += threads * 2 * rr * (d + 1) ** 2
     for i, spci in st:
         k = spci.bit_length() - 1
         ncx = (63 >> min(k, 31)) + 2
         corners += tiles * ncx * ncx * (19 if kind == "zero_grad" else 31)
+        if i < nt:
+            continue
         if spci >= rw:
             evalops += threads * (prep + rr * (row + smp * (d + 1)))
         else:
             evalops += threads * small_cell_ops(kind, rw, spci)
     n_lattice = octaves - len(st)
-    lattice = 0 if kind.startswith("perlin") else samples_padded * n_lattice * 19
+    lattice = 0 if kind.startswith("perlin") else samples_padded * n_lattice * 14
     tot = lut + corners + evalops + lattice
     return dict(total=float(tot), per_sample=tot / (w * h), lut=lut, corners=corners, eval=evalops,
                 lattice=lattice)
@@ -122,7 +141,7 @@ def lane_ops_3d(kind: str, size, spc: int, octaves: int) -> dict:
             evalops += threads * (2 * (32 + 4 + 1 + 3 * 9) + 24 * 4 + 8)
         else:
             evalops += threads * (8 * (32 + 4 + 1 + 9) + 80)
-    lattice = samples_padded * (octaves - len(st)) * 23
+    lattice = samples_padded * (octaves - len(st)) * 15
     tot = lut + corners + evalops + lattice
     return dict(total=float(tot), per_sample=tot / (w * h * dd), lut=lut, corners=corners, eval=evalops,
                 lattice=lattice)

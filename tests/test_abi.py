@@ -73,6 +73,12 @@ def test_desc_layout_matches_header(P):
     (dict(variant=0x201), 1, 0),                      # Perlin S3, shape 16 x 2
     (dict(variant=0x300), 0, -1),                     # unknown shape bits
     (dict(variant=0x1000), 0, -1),
+    (dict(variant=0x800), 0, 0),                      # C1 at the tile nodes
+    (dict(variant=0x801), 1, 0),                      # Perlin S3 at the tile nodes
+    (dict(variant=0x800), 1, -2),                     # not Perlin S5 (degree 6)
+    (dict(variant=0x800, smoothness=2), 0, -2),       # not C2 (degree 5)
+    (dict(variant=0x400, smoothness=2), 0, 0),
+    (dict(variant=0xc00), 0, -1),                     # unknown coarse bits
     (dict(variant=1), 0, -1),                         # blend byte on a polynomial field
     (dict(variant=0x100), 2, -2),                     # no shape for OpenSimplex
     (dict(variant=0x200, dims=3, size=(32, 32, 32)), 0, -2),

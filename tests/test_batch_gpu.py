@@ -57,12 +57,13 @@ def test_batch_equals_single_launches(ctx):
         assert torch.equal(o, r), k
 
 
-def test_batch_mixed_thread_shapes(ctx):
-    """Fields pinned to either 2D thread shape in one batch: each equals its
-    own single launch with the same shape."""
+def test_batch_mixed_launch_configs(ctx):
+    """Fields pinned to every 2D launch configuration in one batch: each
+    equals its own single launch with the same configuration."""
     descs, outs = _chunks(48, seed=11)
     for k, d in enumerate(descs):
-        d.variant = P.PTG_SHAPE_8X4 if k % 2 else P.PTG_SHAPE_16X2
+        d.variant = (P.PTG_SHAPE_8X4 if k % 2 else P.PTG_SHAPE_16X2) | \
+            (P.PTG_COARSE_TILE if (k // 2) % 2 and d.smoothness == P.PTG_C1 else P.PTG_COARSE_RUNS)
     ref = _singles(ctx, descs, outs)
     P.ptg_batch(ctx, descs, outs)
     torch.cuda.synchronize()

@@ -34,9 +34,9 @@ def ctx():
 
 
 def gpu_field(ctx, kind, dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 0, 0), offset=(0, 0, 0),
-              seed=0, persistence=0.5, grad_weight=1.0, dtype=P.PTG_F32, shape=P.PTG_SHAPE_AUTO):
+              seed=0, persistence=0.5, grad_weight=1.0, dtype=P.PTG_F32, shape=P.PTG_SHAPE_AUTO, coarse=0):
     smooth = SMOOTH.get(kind, P.PTG_C1)
-    variant = (P.PTG_PERLIN_S3 if kind == "perlin_s3" else P.PTG_PERLIN_S5) | shape
+    variant = (P.PTG_PERLIN_S3 if kind == "perlin_s3" else P.PTG_PERLIN_S5) | shape | coarse
     d = P.make_desc(dims=dims, size=size, spc=spc, origin=origin, offset=offset, octaves=octaves,
                     smoothness=smooth, persistence=persistence, grad_weight=grad_weight, seed=seed, dtype=dtype,
                     variant=variant)
@@ -196,25 +196,34 @@ def test_3d_ragged(ctx):
 
 
 # ---------------------------------------------------------------------------
-# both 2D thread shapes (8 x 4 and 16 x 2 samples a thread) against the oracle
+# every 2D launch configuration (thread shape 8 x 4 or 16 x 2; coarse octaves
+# per run or at the tile nodes) against the oracle
 # ---------------------------------------------------------------------------
 SHAPES = [P.PTG_SHAPE_8X4, P.PTG_SHAPE_16X2]
+TILE_KINDS = ("c1", "perlin_s3", "paper_gauge", "zero_grad")  # degree <= 4
 
 
+@pytest.mark.parametrize("coarse", [P.PTG_COARSE_RUNS, P.PTG_COARSE_TILE])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3", "paper_gauge", "zero_grad"])
 @pytest.mark.parametrize("size,spc,octaves", [
-    ((256, 256), 64, 6),      # run octaves of 64/32/16-sample cells, then 8, 4, 2
+    ((256, 256), 64, 6),      # one tile octave, run octaves of 32/16-sample cells, then 8, 4, 2
     ((200, 136), 16, 7),      # ragged; one 16-wide run octave, 8/4/2, lattice
-    ((130, 70), 2048, 13),    # eight run octaves, 8/4/2, lattice
+    ((130, 70), 2048, 13),    # six tile octaves, two run octaves, 8/4/2, lattice
     ((96, 80), 8, 5),         # no 16-wide run octave
+    ((100, 70), 1 << 20, 20),  # fifteen tile octaves
 ])
-def test_thread_shapes_vs_oracle(ctx, kind, shape, size, spc, octaves):
+def test_launch_configs_vs_oracle(ctx, kind, shape, coarse, size, spc, octaves):
+    if coarse == P.PTG_COARSE_TILE and kind not in TILE_KINDS:
+        pytest.skip("tile nodes are for models of degree <= 4")
     origin = (-(1 << 20) + 3, 12345, 0)
     out = gpu_field(ctx, kind, size=size, spc=spc, octaves=octaves, origin=origin, seed=21, persistence=0.6,
-                    grad_weight=0.75, shape=shape)
-    assert P.ptg_thread_shape(ctx, P.make_desc(dims=2, size=size, spc=spc, octaves=octaves, variant=shape)) == \
-        (8 if shape == P.PTG_SHAPE_8X4 else 16)
+                    grad_weight=0.75, shape=shape, coarse=coarse)
+    rw, nt = P.ptg_launch_config(ctx, P.make_desc(dims=2, size=size, spc=spc, octaves=octaves,
+                                                  variant=shape | coarse))
+    assert rw == (8 if shape == P.PTG_SHAPE_8X4 else 16)
+    n64 = max(0, min(octaves, spc.bit_length() - 6))
+    assert nt == (n64 if coarse == P.PTG_COARSE_TILE else 0)
     idx = W.grid_indices_2d(*size)
     ref = oracle_at(kind, idx, spc=spc, octaves=octaves, origin=origin, seed=21, persistence=0.6, grad_weight=0.75)
     err = np.abs(gather(out, idx) - ref).max()
@@ -222,22 +231,25 @@ def test_thread_shapes_vs_oracle(ctx, kind, shape, size, spc, octaves):
 
 
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "zero_grad"])
-def test_thread_shapes_agree(ctx, kind):
-    """Same field, both shapes: equal up to FP32 rounding (twice the bar)."""
-    a = gpu_field(ctx, kind, size=(1024, 512), spc=256, octaves=10, seed=3, shape=P.PTG_SHAPE_8X4)
-    b = gpu_field(ctx, kind, size=(1024, 512), spc=256, octaves=10, seed=3, shape=P.PTG_SHAPE_16X2)
-    assert float((a - b).abs().max()) <= 2 * tol32(10)
+def test_launch_configs_agree(ctx, kind):
+    """Same field, every configuration: equal up to FP32 rounding (twice the bar)."""
+    coarse = [P.PTG_COARSE_RUNS] + ([P.PTG_COARSE_TILE] if kind in TILE_KINDS else [])
+    outs = [gpu_field(ctx, kind, size=(1024, 512), spc=1024, octaves=10, seed=3, shape=sh, coarse=co)
+            for sh in SHAPES for co in coarse]
+    for b in outs[1:]:
+        assert float((outs[0] - b).abs().max()) <= 2 * tol32(10)
 
 
+@pytest.mark.parametrize("coarse", [P.PTG_COARSE_RUNS, P.PTG_COARSE_TILE])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_thread_shape_fp16_and_mosaic(ctx, shape):
-    big = gpu_field(ctx, "c2", size=(512, 384), spc=128, octaves=9, origin=(11, -4, 0), seed=8,
-                    dtype=P.PTG_F16, shape=shape)
+def test_launch_config_fp16_and_mosaic(ctx, shape, coarse):
+    big = gpu_field(ctx, "c1", size=(512, 384), spc=1024, octaves=9, origin=(11, -4, 0), seed=8,
+                    dtype=P.PTG_F16, shape=shape, coarse=coarse)
     idx = W.subsample((512, 384), every=64, n_random=4096, seed=2)
-    ref = oracle_at("c2", idx, spc=128, octaves=9, origin=(11, -4, 0), seed=8)
+    ref = oracle_at("c1", idx, spc=1024, octaves=9, origin=(11, -4, 0), seed=8)
     assert np.all(np.abs(gather(big, idx) - ref) <= tol32(9) + half_ulp16(ref))
-    part = gpu_field(ctx, "c2", size=(256, 192), spc=128, octaves=9, origin=(11, -4, 0), offset=(256, 192, 0),
-                     seed=8, dtype=P.PTG_F16, shape=shape)
+    part = gpu_field(ctx, "c1", size=(256, 192), spc=1024, octaves=9, origin=(11, -4, 0), offset=(256, 192, 0),
+                     seed=8, dtype=P.PTG_F16, shape=shape, coarse=coarse)
     assert torch.equal(part, big[192:384, 256:512])
 
 
