@@ -93,6 +93,43 @@ __device__ __forceinline__ uint32_t pcg3d_value(uint32_t x, uint32_t y, uint32_t
     return x;
 }
 
+// Word 0 of pcg3d along a run of lattice points (x0 + c d, y, z), c = 0, 1, ...
+// The LCG steps of y and z and the addend y1 z1 of x's first cross step are
+// the same for the whole run, and x's LCG step advances by d * 1664525 per
+// point, so a point costs its own cross steps and xorshifts only.
+__device__ __forceinline__ uint32_t pcg_lcg(uint32_t u) { return u * 1664525u + 1013904223u; }
+
+// x's state after its first cross step at c = 0: lcg(x0) + y1 z1.
+__device__ __forceinline__ uint32_t pcg3d_run_base(uint32_t x0, uint32_t y1, uint32_t z1)
+{
+    return pcg_lcg(x0) + y1 * z1;
+}
+
+// The rest of pcg3d word 0 from that state (x2 = base + c d 1664525).
+__device__ __forceinline__ uint32_t pcg3d_run_value(uint32_t x2, uint32_t y1, uint32_t z1)
+{
+    const uint32_t y2 = y1 + z1 * x2;
+    const uint32_t z2 = z1 + x2 * y2;
+    const uint32_t x3 = x2 ^ (x2 >> 16), y3 = y2 ^ (y2 >> 16), z3 = z2 ^ (z2 >> 16);
+    return x3 + y3 * z3;
+}
+
+// pcg4d word 0 likewise, with y1, z1, w1 fixed along the run: lcg(x0) + y1 w1,
+// then y, z, w cross steps, xorshifts of x, y, w and x + y w.
+__device__ __forceinline__ uint32_t pcg4d_run_base(uint32_t x0, uint32_t y1, uint32_t w1)
+{
+    return pcg_lcg(x0) + y1 * w1;
+}
+
+__device__ __forceinline__ uint32_t pcg4d_run_value(uint32_t x2, uint32_t y1, uint32_t z1, uint32_t w1)
+{
+    const uint32_t y2 = y1 + z1 * x2;
+    const uint32_t z2 = z1 + x2 * y2;
+    const uint32_t w2 = w1 + y2 * z2;
+    const uint32_t x3 = x2 ^ (x2 >> 16), y3 = y2 ^ (y2 >> 16), w3 = w2 ^ (w2 >> 16);
+    return x3 + y3 * w3;
+}
+
 __device__ __forceinline__ void pcg4d(uint32_t& x, uint32_t& y, uint32_t& z, uint32_t& w)
 {
     x = x * 1664525u + 1013904223u;

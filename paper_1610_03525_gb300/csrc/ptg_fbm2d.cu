@@ -302,13 +302,16 @@ __device__ __forceinline__ void lattice_octave(float (&acc)[Shape<RW>::RR][RW], 
                                                uint32_t jy)
 {
     const int sh = op.k;
+    const uint32_t z1 = pcg_lcg(op.key), dx = 1664525u << sh;  // x's LCG step advances by dx a column
+    const uint32_t x0 = op.ox + (jx << sh);
 #pragma unroll
     for (int r = 0; r < Shape<RW>::RR; ++r) {
-        const uint32_t iy = op.oy + ((jy + r) << sh);
+        const uint32_t y1 = pcg_lcg(op.oy + ((jy + r) << sh));
+        const uint32_t base = pcg3d_run_base(x0, y1, z1);
 #pragma unroll
         for (int c = 0; c < RW; ++c) {
-            const uint32_t ix = op.ox + ((jx + c) << sh);
-            acc[r][c] = fmaf(op.amp, unit_value(pcg3d_value(ix, iy, op.key)), acc[r][c]);
+            const uint32_t h = pcg3d_run_value(base + (uint32_t)c * dx, y1, z1);
+            acc[r][c] = fmaf(op.amp, unit_value(h), acc[r][c]);
         }
     }
 }

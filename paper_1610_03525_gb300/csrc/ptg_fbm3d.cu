@@ -182,14 +182,16 @@ __device__ __forceinline__ void lattice_octave3(float (&acc)[kRows][kCols], cons
                                                 uint32_t jy, uint32_t jz)
 {
     const int sh = op.k;
-    const uint32_t iz = op.oz + (jz << sh);
+    const uint32_t z1 = pcg_lcg(op.oz + (jz << sh)), w1 = pcg_lcg(op.key);
+    const uint32_t dx = 1664525u << sh, x0 = op.ox + (jx << sh);  // x's LCG step advances by dx a column
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
-        const uint32_t iy = op.oy + ((jy + r) << sh);
+        const uint32_t y1 = pcg_lcg(op.oy + ((jy + r) << sh));
+        const uint32_t base = pcg4d_run_base(x0, y1, w1);
 #pragma unroll
         for (int c = 0; c < kCols; ++c) {
-            const uint32_t ix = op.ox + ((jx + c) << sh);
-            acc[r][c] = fmaf(op.amp, unit_value(pcg4d_value(ix, iy, iz, op.key)), acc[r][c]);
+            const uint32_t h = pcg4d_run_value(base + (uint32_t)c * dx, y1, z1, w1);
+            acc[r][c] = fmaf(op.amp, unit_value(h), acc[r][c]);
         }
     }
 }
