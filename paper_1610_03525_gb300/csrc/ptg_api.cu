@@ -131,7 +131,10 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
     const int esz = d->dtype == PTG_F16 ? 2 : 4;
     P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
     P->nst = d->octaves < s ? d->octaves : s;
-    int coff = 0, count = 0;
+    // 2D: coarse octaves (cells >= 128 samples) first, then fine ones at fixed offsets
+    int ncoarse = s - 6;
+    ncoarse = ncoarse < 0 ? 0 : (ncoarse < d->octaves ? ncoarse : d->octaves);
+    int coff = 0, count = 0, cend = 0;
     double amp = 1.0;
     const double p = (double)d->persistence, w = (double)d->grad_weight;
     for (int i = 0; i < d->octaves; ++i) {
@@ -147,7 +150,14 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
             o.magic = (uint32_t)(((uint64_t{1} << 32) + (uint64_t)o.ncx - 1) / (uint64_t)o.ncx);
             o.magic2 = (uint32_t)(((uint64_t{1} << 32) + (uint64_t)(o.ncx * o.ncy) - 1) / (uint64_t)(o.ncx * o.ncy));
             o.rowlen = corner_slot(o.ncx - 1) + 1;
-            coff += o.rowlen * o.ncy * o.ncz;
+            if (is3d) {
+                coff += o.rowlen * o.ncy * o.ncz;
+                cend = coff;
+            } else {
+                o.coff = k >= 7 ? 4 * i : 4 * ncoarse + fine_off2(k);
+                const int e = o.coff + o.rowlen * o.ncy;
+                cend = e > cend ? e : cend;
+            }
             count += o.ncx * o.ncy * o.ncz;
         } else {
             o.mode = kModeLattice;
@@ -161,7 +171,7 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
         o.ampw = (float)(amp * w);
         amp *= p;
     }
-    P->ncorner = coff;
+    P->ncorner = cend;
     P->ncount = count;
     P->method = method;
     P->s = s;

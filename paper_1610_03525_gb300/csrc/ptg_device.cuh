@@ -220,7 +220,22 @@ __device__ __forceinline__ float axis_t(uint32_t j, int i, int s)
 // every 8 corners, so that the 8 lanes of a quarter warp that read corners 1,
 // 2 or 4 apart (cells of 8, 4 or 2 samples) hit 8 different 16-byte bank
 // groups.
-__host__ __device__ __forceinline__ int corner_slot(int cx) { return cx + (cx >> 3); }
+__host__ __device__ constexpr int corner_slot(int cx) { return cx + (cx >> 3); }
+
+// 2D staged corner layout of a 64 x 64 tile.  Octaves whose cells have 2^K
+// samples with K >= 7 come first, 4 slots each, in octave order; then the
+// fine octaves K = 6 .. 1 at fixed offsets from the end of that coarse part,
+// so that kernels specialised on K address them with constants.  Absent fine
+// octaves leave their slots at the end (K small) unused and unreserved.
+__host__ __device__ constexpr int corner_ncx2(int K) { return (63 >> K) + 2; }
+__host__ __device__ constexpr int corner_rowlen2(int K) { return corner_slot(corner_ncx2(K) - 1) + 1; }
+__host__ __device__ constexpr int corner_size2(int K) { return corner_rowlen2(K) * corner_ncx2(K); }
+__host__ __device__ constexpr int fine_off2(int K)
+{
+    int o = 0;
+    for (int k = 6; k > K; --k) o += corner_size2(k);
+    return o;
+}
 
 // Output stores.
 __device__ __forceinline__ void store1(float* p, float v) { *p = v; }

@@ -113,6 +113,58 @@ constexpr TileWeights<D, RW> make_tile_weights()
     return w;
 }
 
+// Per-axis basis of an in-cell position t as compile-time values, computed in
+// double and rounded once: the functions of axis_basis.
+struct alignas(16) Basis4 {
+    float x, y, z, w;
+};
+
+template <int METHOD>
+constexpr Basis4 basis_const(double t)
+{
+    const double t2 = t * t, u = t - 1.0;
+    const double S3 = t2 * (3.0 - 2.0 * t), S5 = t2 * t * (10.0 + t * (-15.0 + 6.0 * t));
+    if (METHOD == kZeroGrad) return Basis4{(float)S3, (float)t, 0.0f, 0.0f};
+    if (METHOD == kPaperGauge) return Basis4{(float)t, 0.0f, 0.0f, 0.0f};
+    if (METHOD == kC1) return Basis4{(float)S3, (float)(t * u * u), (float)(t2 * u), 0.0f};
+    if (METHOD == kC2)
+        return Basis4{(float)S5, (float)(t * u * u * (-u) * (1.0 + 3.0 * t)), (float)(t2 * t * u * (4.0 - 3.0 * t)),
+                      0.0f};
+    const double S = METHOD == kPerlinS5 ? S5 : S3;
+    return Basis4{(float)S, (float)((1.0 - S) * t), (float)(S * u), 0.0f};
+}
+
+// Run octaves with cells of 2^K samples, RW <= 2^K <= 64.  Tiles start at
+// multiples of min(64, spc) samples, so tile column c lies at (c mod 2^K) / 2^K
+// of its cell in every tile: the basis at a thread's node columns and rows
+// is one table for all tiles, with 2^K / RW distinct thread columns and 2^K
+// distinct rows per K.  Flat: x at xoff(K) + q (2^K / RW) + (tx mod 2^K / RW),
+// y at yoff(K) + (row mod 2^K).
+template <int METHOD, int RW>
+struct RunBasis {
+    static constexpr int NN = Deg<METHOD>::value + 1, LOG = RW == 8 ? 3 : 4;
+    static constexpr int NX = NN * ((64 / RW) * 2 - 1), NY = 64 * 2 - (1 << LOG);  // sums over K = LOG .. 6
+    __host__ __device__ static constexpr int xoff(int K) { return NN * ((1 << (K - LOG)) - 1); }
+    __host__ __device__ static constexpr int yoff(int K) { return (1 << K) - (1 << LOG); }
+    Basis4 x[NX];
+    Basis4 y[NY];
+};
+
+template <int METHOD, int RW>
+constexpr RunBasis<METHOD, RW> make_run_basis()
+{
+    using B = RunBasis<METHOD, RW>;
+    B b{};
+    for (int K = B::LOG; K <= 6; ++K) {
+        const int m = (1 << K) - 1, nx = (1 << K) / RW;
+        for (int q = 0; q < B::NN; ++q)
+            for (int tx = 0; tx < nx; ++tx)
+                b.x[B::xoff(K) + q * nx + tx] = basis_const<METHOD>((double)(tx * RW + node_col<B::NN - 1, RW>(q)) / (m + 1));
+        for (int row = 0; row <= m; ++row) b.y[B::yoff(K) + row] = basis_const<METHOD>((double)row / (m + 1));
+    }
+    return b;
+}
+
 // Corner data of one cell: (v, f, g) at (0,0), (1,0), (0,1), (1,1).
 struct Cell {
     float4 c00, c10, c01, c11;

@@ -56,28 +56,23 @@ struct Shape {
 };
 static_assert(Shape<8>::TXN * Shape<8>::TYN == kThreads && Shape<16>::TXN * Shape<16>::TYN == kThreads, "");
 
-// Shared-memory layout (float4 units), with nr = run octaves that are not
-// tile octaves:
-//   x-basis of those run octaves at node columns [nr][D+1][TXN],
-//   y-basis of those run octaves [nr][RR rows][TYN] (64 per octave),
+// Shared-memory layout (float4 units), with ng = run octaves with cells of
+// 128 samples or more that are not tile octaves (their basis depends on the
+// tile's place in the cell; finer run octaves read constant tables):
+//   x-basis of those octaves at node columns [ng][D+1][TXN],
+//   y-basis of those octaves [ng][RR rows][TYN] (64 per octave),
+//   a copy of the constant basis tables of the finer run octaves (Perlin, if any),
 //   staged corners of every staged octave (rows swizzled by corner_slot),
 //   with tile octaves: the tile nodes' values [D+1][LW], then a copy of the
 //   interpolation weights (TileWeights) made while the corners are hashed.
 template <int METHOD, int RW>
-__host__ __device__ constexpr int xnode_words(int nr) { return nr * (Deg<METHOD>::value + 1) * Shape<RW>::TXN; }
+__host__ __device__ constexpr int xnode_words(int ng) { return ng * (Deg<METHOD>::value + 1) * Shape<RW>::TXN; }
 
 template <int METHOD, int RW>
 __host__ __device__ constexpr int grid_words()  // float4 words: tile nodes' values, then their weights
 {
     return ((Deg<METHOD>::value + 1) * TileWeights<Deg<METHOD>::value, RW>::LW +
             (int)sizeof(TileWeights<Deg<METHOD>::value, RW>) / 4) / 4;
-}
-
-template <int RW>
-__host__ __device__ __forceinline__ int n_run(const FieldPlan& P)  // octaves with cells >= RW samples
-{
-    const int n = P.s - Shape<RW>::LOG + 1;
-    return n < 0 ? 0 : (n < P.N ? n : P.N);
 }
 
 // Tile octaves: octaves with cells >= 64 samples that the host chose to sum
@@ -89,6 +84,49 @@ __host__ __device__ __forceinline__ int n_tile(const FieldPlan& P)
     return Deg<METHOD>::value <= 4 ? P.nt : 0;
 }
 
+// Octaves with cells of 128 samples or more (the first ones in the corner
+// layout), and those of them that are run octaves (not tile octaves).
+__host__ __device__ __forceinline__ int n_coarse(const FieldPlan& P)
+{
+    const int n = P.s - 6;
+    return n < 0 ? 0 : (n < P.N ? n : P.N);
+}
+
+template <int METHOD>
+__host__ __device__ __forceinline__ int n_generic(const FieldPlan& P)
+{
+    const int n = n_coarse(P) - n_tile<METHOD>(P);
+    return n > 0 ? n : 0;
+}
+
+// Whether the field has run octaves with cells of 2^LOG .. 64 samples (the
+// octaves that read the constant basis tables).
+template <int METHOD, int RW>
+__host__ __device__ __forceinline__ bool has_fine_runs(const FieldPlan& P)
+{
+    int kmax = P.s - n_tile<METHOD>(P), kmin = P.s - P.N + 1;
+    kmax = kmax < 6 ? kmax : 6;
+    kmin = kmin > Shape<RW>::LOG ? kmin : Shape<RW>::LOG;
+    return kmax >= kmin;
+}
+
+// Where run_octave_k reads the constant basis tables: a shared-memory copy
+// made while the corners are hashed (Perlin) or the global tables through the
+// read-only cache (the polynomial models).  Each is the faster of the two for
+// its kernels, by measurement on GB300 (2-9%).
+template <int METHOD>
+__host__ __device__ constexpr bool shared_run_basis() { return METHOD == kPerlinS5 || METHOD == kPerlinS3; }
+
+template <int METHOD, int RW>
+__host__ __device__ __forceinline__ int run_basis_words(const FieldPlan& P)  // shared-memory copy, float4 words
+{
+    return shared_run_basis<METHOD>() && has_fine_runs<METHOD, RW>(P) ? (int)sizeof(RunBasis<METHOD, RW>) / 16 : 0;
+}
+
+// Basis tables of the run octaves with cells of 8 .. 64 samples.
+template <int METHOD, int RW>
+__device__ const RunBasis<METHOD, RW> kRunBasis = make_run_basis<METHOD, RW>();
+
 // Interpolation weights of the tile nodes (compile-time tables).
 template <int D, int RW>
 __device__ const TileWeights<D, RW> kTileWeights = make_tile_weights<D, RW>();
@@ -98,17 +136,23 @@ __device__ __forceinline__ void stage_tile(const FieldPlan& P, float4* sm, int j
 {
     using SH = Shape<RW>;
     constexpr int D = Deg<METHOD>::value, NN = D + 1;
-    const int tid = threadIdx.x, s = P.s, nt = n_tile<METHOD>(P), nr = n_run<RW>(P) - nt;
+    const int tid = threadIdx.x, s = P.s, nt = n_tile<METHOD>(P), ng = n_generic<METHOD>(P);
     float4* xnode = sm;
-    float4* ylut = sm + xnode_words<METHOD, RW>(nr);
-    float4* corners = ylut + nr * 64;
-    for (int e = tid; e < nr * NN * SH::TXN; e += kThreads) {
+    float4* ylut = sm + xnode_words<METHOD, RW>(ng);
+    float4* rbase = ylut + ng * 64;
+    const int nrb = run_basis_words<METHOD, RW>(P);
+    float4* corners = rbase + nrb;
+    {  // constant tables, global -> shared (latency hidden by the hashing below)
+        const float4* src = reinterpret_cast<const float4*>(&kRunBasis<METHOD, RW>);
+        for (int e = tid; e < nrb; e += kThreads) rbase[e] = __ldg(src + e);
+    }
+    for (int e = tid; e < ng * NN * SH::TXN; e += kThreads) {
         const int i = e / (NN * SH::TXN), rem = e - i * (NN * SH::TXN);
         const int q = rem / SH::TXN, tx = rem % SH::TXN;
         const int col = tx * RW + node_col<D, RW>(q);
         xnode[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0x + col), nt + i, s));
     }
-    for (int e = tid; e < nr * 64; e += kThreads) {  // stored in table order: conflict-free
+    for (int e = tid; e < ng * 64; e += kThreads) {  // stored in table order: conflict-free
         const int i = e >> 6, slot = e & 63;
         const int row = (slot % SH::TYN) * SH::RR + slot / SH::TYN;
         ylut[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0y + row), nt + i, s));
@@ -169,14 +213,14 @@ __device__ __forceinline__ Cell load_cell(const float4* __restrict__ cg, int row
 // i = octave, ti = its slot in the basis tables (i minus the tile octaves).
 template <int METHOD, int RW>
 __device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
-                                           const float4* __restrict__ sm, const FieldPlan& P, int i, int ti,
-                                           int tx, int ty, int nr)
+                                           const float4* __restrict__ sm, const float4* __restrict__ corners,
+                                           const FieldPlan& P, int i, int ti, int tx, int ty, int ng)
 {
     using SH = Shape<RW>;
     constexpr int NN = Deg<METHOD>::value + 1;
     const OctPlan& op = P.oct[i];
-    const float4* ylut = sm + xnode_words<METHOD, RW>(nr);
-    const float4* cg = ylut + nr * 64 + op.coff;
+    const float4* ylut = sm + xnode_words<METHOD, RW>(ng);
+    const float4* cg = corners + op.coff;
     const Cell c = load_cell(cg, op.rowlen, (tx * RW) >> op.k, (ty * SH::RR) >> op.k);
     float4 xb[NN];
 #pragma unroll
@@ -190,19 +234,58 @@ __device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METH
     }
 }
 
+// A run octave with cells of 2^K samples, RW <= 2^K <= 64: the same work as
+// run_octave, with the corner block, its row length and the cell index
+// shifts known at compile time and the bases read from the constant tables.
+template <int METHOD, int RW, int K>
+__device__ __forceinline__ void run_octave_k(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
+                                             const float4* __restrict__ fine, const float4* __restrict__ rb,
+                                             int tx, int ty)
+{
+    using SH = Shape<RW>;
+    using RB = RunBasis<METHOD, RW>;
+    constexpr int NN = Deg<METHOD>::value + 1, NXK = (1 << K) / RW;
+    const Cell c = load_cell(fine + fine_off2(K), corner_rowlen2(K), (tx * RW) >> K, (ty * SH::RR) >> K);
+    const float4* tb = shared_run_basis<METHOD>() ? rb : reinterpret_cast<const float4*>(&kRunBasis<METHOD, RW>);
+    const float4* xt = tb + RB::xoff(K) + (tx & (NXK - 1));
+    const float4* yt = tb + RB::NX + RB::yoff(K);
+    float4 xb[NN];
+#pragma unroll
+    for (int q = 0; q < NN; ++q) xb[q] = shared_run_basis<METHOD>() ? xt[q * NXK] : __ldg(xt + q * NXK);
+#pragma unroll
+    for (int r = 0; r < SH::RR; ++r) {
+        const float4* yp = yt + ((ty * SH::RR + r) & ((1 << K) - 1));
+        const float4 yb = shared_run_basis<METHOD>() ? *yp : __ldg(yp);
+        const Row R = Model<METHOD>::row(c, yb);
+#pragma unroll
+        for (int q = 0; q < NN; ++q) nacc[r][q] += Model<METHOD>::eval(R, xb[q]);
+    }
+}
+
+template <int METHOD, int RW, int K>
+__device__ __forceinline__ void run_fine(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
+                                         const float4* __restrict__ fine, const float4* __restrict__ rb, int s,
+                                         int N, int nt, int tx, int ty)
+{
+    if constexpr (K >= Shape<RW>::LOG) {
+        const int i = s - K;  // the octave with cells of 2^K samples, if it is a run octave of this field
+        if (i >= nt && i >= 0 && i < N) run_octave_k<METHOD, RW, K>(nacc, fine, rb, tx, ty);
+    }
+}
+
 // Cells of CW = 8, 4 or 2 samples (CW < RW): the in-cell position of column c
 // is (c mod CW) / CW, a constant.  Row positions are constants too when a
 // thread's rows cover whole cells (RR >= CW); otherwise (RR < CW) they depend
 // on the thread's row and the row basis is evaluated once per octave.
 template <int METHOD, int RW, int CW>
-__device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], const float4* __restrict__ sm,
-                                             const FieldPlan& P, int i, int tx, int ty, int nr)
+__device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], const float4* __restrict__ fine,
+                                             int tx, int ty)
 {
     using SH = Shape<RW>;
     constexpr int RR = SH::RR, NXC = RW / CW, RPC = RR < CW ? RR : CW, NYC = RR / RPC;
+    constexpr int K = CW == 8 ? 3 : (CW == 4 ? 2 : 1);
     constexpr bool kConstRows = RR >= CW;
-    const OctPlan& op = P.oct[i];
-    const float4* cg = sm + xnode_words<METHOD, RW>(nr) + nr * 64 + op.coff;
+    const float4* cg = fine + fine_off2(K);
     constexpr float inv = 1.0f / CW;
     float4 yb[RPC];
 #pragma unroll
@@ -214,7 +297,7 @@ __device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], co
 #pragma unroll
         for (int xq = 0; xq < NXC; ++xq) {
             const int lcx = (tx * RW + xq * CW) / CW;
-            const Cell c = load_cell(cg, op.rowlen, lcx, lcy);
+            const Cell c = load_cell(cg, corner_rowlen2(K), lcx, lcy);
 #pragma unroll
             for (int rr = 0; rr < RPC; ++rr) {
                 const Row R = (kConstRows && rr == 0) ? Model<METHOD>::row0(c) : Model<METHOD>::row(c, yb[rr]);
@@ -366,13 +449,15 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     const int tid = threadIdx.x, tx = tid % SH::TXN, ty = tid / SH::TXN;
     const int x0 = bx * kTW, y0 = by * kTH;        // output tile origin
     const int j0x = x0 + P.jx0, j0y = y0 + P.jy0;  // sample indices
-    const int s = P.s, N = P.N, nt = n_tile<METHOD>(P), nrun = n_run<RW>(P), nr = nrun - nt;
+    const int s = P.s, N = P.N, nt = n_tile<METHOD>(P), ng = n_generic<METHOD>(P);
     stage_tile<METHOD, RW>(P, sm, j0x, j0y);
     __syncthreads();
 
     // tile octaves: their sum at the tile nodes (read back after the barrier below)
-    const float4* corners = sm + xnode_words<METHOD, RW>(nr) + nr * 64;
-    float* G = reinterpret_cast<float*>(sm + xnode_words<METHOD, RW>(nr) + nr * 64 + P.ncorner);
+    const float4* rb = sm + xnode_words<METHOD, RW>(ng) + ng * 64;
+    const float4* corners = rb + run_basis_words<METHOD, RW>(P);
+    const float4* fine = corners + 4 * n_coarse(P);  // corner blocks of the octaves with cells <= 64 samples
+    float* G = reinterpret_cast<float*>(const_cast<float4*>(corners) + P.ncorner);
     if (Deg<METHOD>::value <= 4 && nt > 0) tile_grid<METHOD>(P, corners, G, j0x, j0y, nt);
 
     // run octaves: node columns, then interpolate the other columns once
@@ -381,7 +466,11 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     for (int r = 0; r < RR; ++r)
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
-    for (int i = nt; i < nrun; ++i) run_octave<METHOD, RW>(nacc, sm, P, i, i - nt, tx, ty, nr);
+    for (int i = 0; i < ng; ++i) run_octave<METHOD, RW>(nacc, sm, corners, P, nt + i, i, tx, ty, ng);
+    run_fine<METHOD, RW, 6>(nacc, fine, rb, s, N, nt, tx, ty);
+    run_fine<METHOD, RW, 5>(nacc, fine, rb, s, N, nt, tx, ty);
+    run_fine<METHOD, RW, 4>(nacc, fine, rb, s, N, nt, tx, ty);
+    run_fine<METHOD, RW, 3>(nacc, fine, rb, s, N, nt, tx, ty);
     if (Deg<METHOD>::value <= 4 && nt > 0) {  // uniform over the CTA
         __syncthreads();
         add_tile_grid<METHOD, RW>(nacc, G, tx, ty);
@@ -403,17 +492,23 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
         }
 
     // cells narrower than the run (8, 4 and 2 samples), then lattice octaves
-    if (RW == 16 && s >= 3 && s - 3 < N) small_octave<METHOD, RW, (RW == 16 ? 8 : 4)>(acc, sm, P, s - 3, tx, ty, nr);
-    if (s >= 2 && s - 2 < N) small_octave<METHOD, RW, 4>(acc, sm, P, s - 2, tx, ty, nr);
-    if (s >= 1 && s - 1 < N) small_octave<METHOD, RW, 2>(acc, sm, P, s - 1, tx, ty, nr);
+    if (RW == 16 && s >= 3 && s - 3 < N) small_octave<METHOD, RW, (RW == 16 ? 8 : 4)>(acc, fine, tx, ty);
+    if (s >= 2 && s - 2 < N) small_octave<METHOD, RW, 4>(acc, fine, tx, ty);
+    if (s >= 1 && s - 1 < N) small_octave<METHOD, RW, 2>(acc, fine, tx, ty);
     if (METHOD != kPerlinS5 && METHOD != kPerlinS3)
         for (int i = s; i < N; ++i)
             lattice_octave<RW>(acc, P.oct[i], (uint32_t)(j0x + tx * RW), (uint32_t)(j0y + ty * RR));
     store_tile<RW>(P, acc, x0 + tx * RW, y0 + ty * RR);
 }
 
+// At least five CTAs a SM for C2 and Perlin S5 (up to 102 registers), so that
+// their degree-5/6 node accumulators are not squeezed into spills; the other
+// models are left to the compiler's own choice (78-80 registers, six CTAs).
+template <int METHOD>
+constexpr int min_ctas() { return Deg<METHOD>::value > 4 ? 5 : 0; }
+
 template <int METHOD, int RW>
-__global__ void __launch_bounds__(kThreads) fbm2d_kernel(const __grid_constant__ FieldPlan P)
+__global__ void __launch_bounds__(kThreads, min_ctas<METHOD>()) fbm2d_kernel(const __grid_constant__ FieldPlan P)
 {
     extern __shared__ float4 sm[];
     fbm2d_tile<METHOD, RW>(P, sm, blockIdx.x, blockIdx.y);
@@ -482,10 +577,11 @@ __global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* 
 template <int METHOD>
 size_t smem_words(const FieldPlan& P)
 {
-    const int nt = n_tile<METHOD>(P), nr = (P.rw == 16 ? n_run<16>(P) : n_run<8>(P)) - nt;
+    const int nt = n_tile<METHOD>(P), ng = n_generic<METHOD>(P);
     const size_t grid = nt > 0 ? (size_t)(P.rw == 16 ? grid_words<METHOD, 16>() : grid_words<METHOD, 8>()) : 0;
-    const size_t xw = P.rw == 16 ? (size_t)xnode_words<METHOD, 16>(nr) : (size_t)xnode_words<METHOD, 8>(nr);
-    return xw + (size_t)nr * 64 + (size_t)P.ncorner + grid;
+    const size_t xw = P.rw == 16 ? (size_t)xnode_words<METHOD, 16>(ng) : (size_t)xnode_words<METHOD, 8>(ng);
+    const size_t rbw = P.rw == 16 ? run_basis_words<METHOD, 16>(P) : run_basis_words<METHOD, 8>(P);
+    return xw + (size_t)ng * 64 + rbw + (size_t)P.ncorner + grid;
 }
 
 template <typename K>
