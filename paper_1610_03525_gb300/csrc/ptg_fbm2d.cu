@@ -370,12 +370,9 @@ __device__ __forceinline__ void add_tile_grid(float (&nacc)[Shape<RW>::RR][Deg<M
 #pragma unroll
         for (int q = 0; q < NN; ++q) w[q] = lx[q];
 #pragma unroll
-        for (int r = 0; r < SH::RR; ++r) {
-            float a = 0.0f;
+        for (int r = 0; r < SH::RR; ++r)
 #pragma unroll
-            for (int q = 0; q < NN; ++q) a = fmaf(w[q], Rq[r][q], a);
-            nacc[r][n] += a;
-        }
+            for (int q = 0; q < NN; ++q) nacc[r][n] = fmaf(w[q], Rq[r][q], nacc[r][n]);
     }
 }
 
@@ -403,6 +400,29 @@ template <typename OutT, int RW>
 __device__ __forceinline__ void store_tile_as(const FieldPlan& P, const float (&acc)[Shape<RW>::RR][RW], int x0, int y0)
 {
     OutT* out = reinterpret_cast<OutT*>(P.out);
+    if (P.vec_ok && x0 + RW <= P.W && y0 + Shape<RW>::RR <= P.H) {  // whole run inside: vector stores only
+        OutT* row = out + (size_t)y0 * (size_t)P.W + x0;
+#pragma unroll
+        for (int r = 0; r < Shape<RW>::RR; ++r, row += P.W) {
+            if (sizeof(OutT) == 4) {
+                float4* p = reinterpret_cast<float4*>(row);
+#pragma unroll
+                for (int v = 0; v < RW / 4; ++v)
+                    p[v] = make_float4(acc[r][4 * v], acc[r][4 * v + 1], acc[r][4 * v + 2], acc[r][4 * v + 3]);
+            } else {
+                uint4* p = reinterpret_cast<uint4*>(row);
+#pragma unroll
+                for (int v = 0; v < RW / 8; ++v) {
+                    __half2 h[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        h[q] = __floats2half2_rn(acc[r][8 * v + 2 * q], acc[r][8 * v + 2 * q + 1]);
+                    p[v] = *reinterpret_cast<const uint4*>(h);
+                }
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int r = 0; r < Shape<RW>::RR; ++r) {
         const int y = y0 + r;
@@ -501,11 +521,11 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     store_tile<RW>(P, acc, x0 + tx * RW, y0 + ty * RR);
 }
 
-// At least five CTAs a SM for C2 and Perlin S5 (up to 102 registers), so that
-// their degree-5/6 node accumulators are not squeezed into spills; the other
-// models are left to the compiler's own choice (78-80 registers, six CTAs).
+// At least five CTAs a SM for Perlin S5 (up to 102 registers), so that its
+// degree-6 node accumulators are not squeezed into spills; the other models
+// are left to the compiler's own choice (70-96 registers).
 template <int METHOD>
-constexpr int min_ctas() { return Deg<METHOD>::value > 4 ? 5 : 0; }
+constexpr int min_ctas() { return METHOD == kPerlinS5 ? 5 : 0; }
 
 template <int METHOD, int RW>
 __global__ void __launch_bounds__(kThreads, min_ctas<METHOD>()) fbm2d_kernel(const __grid_constant__ FieldPlan P)
