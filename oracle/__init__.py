@@ -49,6 +49,7 @@ class Desc(ctypes.Structure):
         ("grad_weight", ctypes.c_double),
         ("seed", ctypes.c_uint32),
         ("pad2", ctypes.c_uint32),
+        ("frequency", ctypes.c_double),
     ]
 
 
@@ -81,6 +82,8 @@ def lib():
         L.ptgo_opensimplex_points.restype = ctypes.c_int
         L.ptgo_hash_batch.argtypes = [ctypes.c_int, P, ctypes.c_int64, P]
         L.ptgo_axis_batch.argtypes = [ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, P, P]
+        L.ptgo_axis_freq_batch.argtypes = [ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_double,
+                                           ctypes.c_int, P, P]
         L.ptgo_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -91,7 +94,7 @@ def _ptr(a: np.ndarray):
 
 
 def make_desc(dims, size, cells, origin=(0, 0, 0), octaves=1, method=C1, persistence=0.5,
-              grad_weight=1.0, seed=0) -> Desc:
+              grad_weight=1.0, seed=0, frequency=2.0) -> Desc:
     d = Desc()
     d.dims = dims
     d.method = method
@@ -104,6 +107,8 @@ def make_desc(dims, size, cells, origin=(0, 0, 0), octaves=1, method=C1, persist
     d.persistence = float(np.float32(persistence))
     d.grad_weight = float(np.float32(grad_weight))
     d.seed = seed
+    # the frequency ratio enters as the float32 value the GPU path receives
+    d.frequency = float(np.float32(frequency))
     return d
 
 
@@ -147,6 +152,15 @@ def axis(origin: int, spc: int, j, octave: int):
     cell = np.empty(j.shape[0], np.uint32)
     t = np.empty(j.shape[0], np.float64)
     lib().ptgo_axis_batch(origin, spc, _ptr(j), j.shape[0], octave, _ptr(cell), _ptr(t))
+    return cell, t
+
+
+def axis_freq(origin: int, spc: int, j, f: float, octave: int):
+    """Cell and in-cell position at octave i for frequency ratio f (any f)."""
+    j = np.ascontiguousarray(np.atleast_1d(j), dtype=np.int64)
+    cell = np.empty(j.shape[0], np.uint32)
+    t = np.empty(j.shape[0], np.float64)
+    lib().ptgo_axis_freq_batch(origin, spc, _ptr(j), j.shape[0], float(f), octave, _ptr(cell), _ptr(t))
     return cell, t
 
 

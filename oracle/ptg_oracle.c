@@ -76,6 +76,8 @@ typedef struct {
     double grad_weight;   /* w of Sec. 4                                    */
     uint32_t seed;        /* < 2^24                                         */
     uint32_t pad2;
+    double frequency;     /* f of Sec. 4, frequency ratio between octaves;
+                             0 or 2 = the exact dyadic map of ptgo_axis      */
 } ptgo_desc;
 
 /* ------------------------------------------------------------------------ */
@@ -168,6 +170,25 @@ void ptgo_axis(int64_t origin, int64_t spc, int64_t j, int octave, uint32_t* cel
     *cell = (uint32_t)((uint64_t)origin << octave) + (uint32_t)whole;
     *t = (double)rem / (double)spc;
 }
+
+/* Any frequency ratio f (Sec. 4: f_i proportional to f^i): the lattice      */
+/* coordinate of sample j at octave i is (origin + j/spc) f^i, in double.     */
+/* The cell is its floor (mod 2^32), t the rest.                             */
+void ptgo_axis_freq(int64_t origin, int64_t spc, int64_t j, double f, int octave, uint32_t* cell, double* t)
+{
+    const double u = ((double)origin + (double)j / (double)spc) * pow(f, (double)octave);
+    const double fl = floor(u);
+    *cell = (uint32_t)(uint64_t)(int64_t)fl;
+    *t = u - fl;
+}
+
+void ptgo_axis_freq_batch(int64_t origin, int64_t spc, const int64_t* j, int64_t n, double f, int octave,
+                          uint32_t* cell, double* t)
+{
+    for (int64_t m = 0; m < n; ++m) ptgo_axis_freq(origin, spc, j[m], f, octave, &cell[m], &t[m]);
+}
+
+static int dyadic(const ptgo_desc* d) { return d->frequency == 0.0 || d->frequency == 2.0; }
 
 /* ------------------------------------------------------------------------ */
 /* Constraint system (Sec. 2.1 Eq. mixedderiv, Sec. 2.2 Eq. polynomial).     */
@@ -514,6 +535,7 @@ double ptgo_opensimplex_at(double x, double y, uint32_t seed, int octave)
 static int desc_ok(const ptgo_desc* d)
 {
     if (!d || (d->dims != 2 && d->dims != 3) || d->octaves < 1 || d->octaves > 32) return 0;
+    if (!(d->frequency == 0.0 || (d->frequency >= 1.0 && d->frequency <= 16.0))) return 0;
     for (int k = 0; k < d->dims; ++k)
         if (d->size[k] <= 0 || d->cells[k] <= 0 || d->size[k] % d->cells[k]) return 0;
     if (d->method == PTGO_C1 || d->method == PTGO_C2) return 1;
@@ -556,10 +578,15 @@ int ptgo_field_samples(const ptgo_desc* d, const int64_t* idx, int64_t n, double
                 uint32_t cell[3];
                 double t[3];
                 double h;
-                for (int k = 0; k < dims; ++k) ptgo_axis(d->origin[k], spc[k], idx[m * dims + k], i, &cell[k], &t[k]);
+                for (int k = 0; k < dims; ++k) {
+                    if (dyadic(d))
+                        ptgo_axis(d->origin[k], spc[k], idx[m * dims + k], i, &cell[k], &t[k]);
+                    else
+                        ptgo_axis_freq(d->origin[k], spc[k], idx[m * dims + k], d->frequency, i, &cell[k], &t[k]);
+                }
                 if (d->method == PTGO_OPENSIMPLEX) {
-                    /* real position in octave-i lattice units: (origin + j/spc) 2^i */
-                    double scale = ldexp(1.0, i);
+                    /* real position in octave-i lattice units: (origin + j/spc) f^i */
+                    double scale = dyadic(d) ? ldexp(1.0, i) : pow(d->frequency, (double)i);
                     double x = ((double)d->origin[0] + (double)idx[m * dims] / (double)spc[0]) * scale;
                     double y = ((double)d->origin[1] + (double)idx[m * dims + 1] / (double)spc[1]) * scale;
                     h = ptgo_opensimplex_at(x, y, d->seed, i);

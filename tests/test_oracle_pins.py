@@ -381,6 +381,48 @@ def test_octave_sum_matches_independent_composition():
         assert np.abs(got - ref).max() < 1e-12
 
 
+@pytest.mark.parametrize("f", [1.0, 1.5, 2.0, 3.0, 4.0])
+def test_axis_any_frequency_matches_exact_rationals(f):
+    """Sec. 4, f_i proportional to f^i: sample j of an axis sits at
+    (origin + j/spc) f^i lattice units; cell = floor, t = the rest."""
+    for spc in (1, 64, 1024):
+        for origin in (0, -7, 2**10):
+            j = RNG.integers(0, 5000, size=32)
+            for octave in (0, 1, 5, 9):
+                cell, t = O.axis_freq(origin, spc, j, f, octave)
+                for jj, cc, tt in zip(j, cell, t):
+                    pos = (Fraction(origin) + Fraction(int(jj), spc)) * Fraction(f) ** octave
+                    fl = math.floor(pos)
+                    assert int(cc) == fl % 2**32
+                    assert tt == float(pos - fl)
+
+
+def test_octave_sum_any_frequency_matches_independent_composition():
+    """The same fBm rebuilt from single octaves for frequency ratios 1.5 and
+    3: amplitude p^i, lattice coordinate (origin + j/spc) f^i."""
+    size, cells, N, p = (48, 40), (3, 5), 6, 0.6
+    origin = (-17, 2**10 + 3)
+    idx = np.stack(np.meshgrid(np.arange(size[0]), np.arange(size[1]), indexing="xy"), -1).reshape(-1, 2)
+    idx = idx[RNG.choice(idx.shape[0], 200, replace=False)]
+    for f in (1.5, 3.0):
+        for meth in (O.C1, O.PERLIN_S5, O.ZERO_GRAD):
+            got = O.field_samples(2, size, cells, idx, octaves=N, method=meth, persistence=p, grad_weight=0.5,
+                                  seed=9, origin=origin, frequency=f)
+            pf = float(np.float32(p))
+            ref = np.zeros(idx.shape[0])
+            for i in range(N):
+                cl = np.zeros((idx.shape[0], 2), np.uint32)
+                tl = np.zeros((idx.shape[0], 2))
+                for m, (jx, jy) in enumerate(idx):
+                    for k, jj in enumerate((jx, jy)):
+                        pos = (Fraction(origin[k]) + Fraction(int(jj) * cells[k], size[k])) * Fraction(f) ** i
+                        fl = math.floor(pos)
+                        cl[m, k] = fl % 2**32
+                        tl[m, k] = float(pos - fl)
+                ref += pf**i * O.octave_at(2, meth, 9, i, float(np.float32(0.5)), cl, tl)
+            assert np.abs(got - ref).max() < 1e-12
+
+
 # --------------------------------------------------------------------------
 # Perlin (Sec. 3.2) and OpenSimplex-style pins
 # --------------------------------------------------------------------------
