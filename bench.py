@@ -518,6 +518,15 @@ def main():
                                                  "opensimplex_f32": "opensimplex"}[k], SIZE, SPC,
                                                 OCTAVES, rw_k, nt_k)["per_sample"]
         line["baselines"] = extras
+        # any frequency ratio between octaves (per-sample generator), same size and octave count
+        general = {}
+        for name, fn, kw in [("c1", P.ptg_field, dict(smoothness=P.PTG_C1)),
+                             ("zero_gradient", P.ptg_field, dict(smoothness=P.PTG_ZERO_GRADIENT)),
+                             ("perlin_s5", P.ptg_perlin, dict(variant=P.PTG_PERLIN_S5)),
+                             ("opensimplex", P.ptg_opensimplex, dict())]:
+            dL = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, seed=0, lacunarity=1.9, **kw)
+            general[name + "_f32"] = time_fn(lambda o, fn=fn, dL=dL: fn(ctx, dL, o, stream), reps=3)
+        line["lacunarity_1.9"] = general
         if rank == 0:
             line["volume3d_512_n8"] = bench_3d(P, R, ctx, stream, torch)
             line["octave_sweep"] = bench_octave_sweep(P, ctx, stream, torch)

@@ -55,7 +55,7 @@ typedef enum {
     PTG_OK = 0,
     PTG_PENDING = 1,
     PTG_ERR_INVALID = -1,     /* bad argument                                  */
-    PTG_ERR_UNSUPPORTED = -2, /* valid but not supported (e.g. lacunarity != 2)*/
+    PTG_ERR_UNSUPPORTED = -2, /* valid but not supported (e.g. 3D lacunarity != 2)*/
     PTG_ERR_NOMEM = -3,       /* an allocation failed                          */
     PTG_ERR_BUDGET = -4,      /* request can never fit the HBM budget          */
     PTG_ERR_CUDA = -5,        /* a CUDA call failed                            */
@@ -118,7 +118,15 @@ typedef struct {
     int32_t octaves;      /* N in [1, 32]                                      */
     int32_t smoothness;   /* ptg_smoothness (ptg_field, ptg_submit)            */
     float persistence;    /* amplitude ratio between octaves (0.5 typical)     */
-    float lacunarity;     /* frequency ratio between octaves; must be 2        */
+    float lacunarity;     /* frequency ratio f between octaves, in [1, 16]
+                             (Sec. 4: frequency f^i at octave i).  f = 2 runs
+                             the fused generators; any other f (2D only) runs
+                             a per-sample generator in which the lattice
+                             coordinate (origin + (offset + j)/spc) f^i is
+                             formed per tile in FP64 and must stay below 2^30
+                             (else PTG_ERR_UNSUPPORTED); thread-shape and
+                             coarse-octave bits are ignored there, and
+                             batches (ptg_batch*) need f = 2               */
     float grad_weight;    /* w of Sec. 4; 1.0 default, 0.01 = the paper's      */
     uint32_t seed;        /* < 2^24                                            */
     int32_t dtype;        /* ptg_dtype                                         */

@@ -90,8 +90,18 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "tile nodes apply to models of degree <= 4 (not C2, not Perlin S5)");
     if (!std::isfinite(d->persistence) || !std::isfinite(d->grad_weight))
         return ptg_fail(ctx, PTG_ERR_INVALID, "persistence and grad_weight must be finite");
-    if (!std::isfinite(d->lacunarity)) return ptg_fail(ctx, PTG_ERR_INVALID, "lacunarity must be finite");
-    if (d->lacunarity != 2.0f) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "lacunarity must be 2");
+    if (!std::isfinite(d->lacunarity) || d->lacunarity < 1.0f || d->lacunarity > 16.0f)
+        return ptg_fail(ctx, PTG_ERR_INVALID, "lacunarity (frequency ratio) must be in [1, 16]");
+    if (d->lacunarity != 2.0f) {
+        if (d->dims != 2) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "a lacunarity other than 2 is supported in 2D");
+        // every octave's lattice coordinates must stay below 2^30 in magnitude
+        const double fN = std::pow((double)d->lacunarity, (double)(d->octaves - 1));
+        for (int k = 0; k < 2; ++k) {
+            const double e = std::fabs((double)d->origin[k]) + (double)(d->offset[k] + d->size[k]) / (double)d->spc;
+            if (e * fN >= std::ldexp(1.0, 30))
+                return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "lattice coordinates (origin + extent) * f^(N-1) exceed 2^30");
+        }
+    }
     if (d->seed >= (1u << 24)) return ptg_fail(ctx, PTG_ERR_INVALID, "seed must be < 2^24");
     if (d->dtype != PTG_F32 && d->dtype != PTG_F16) return ptg_fail(ctx, PTG_ERR_INVALID, "bad dtype");
     *spc_log2 = s;
@@ -199,18 +209,18 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
     if (P->tiles_y > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall for one launch");
     const int esz = d->dtype == PTG_F16 ? 2 : 4;
     P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
-    const double spc = std::ldexp(1.0, s);
+    const double spc = std::ldexp(1.0, s), f = (double)d->lacunarity;
     double lim = 0.0;
     for (int k = 0; k < 2; ++k) {
         const double e = std::fabs((double)d->origin[k]) + (double)(d->offset[k] + d->size[k]) / spc;
         if (e > lim) lim = e;
     }
-    if (std::ldexp(lim, d->octaves - 1) >= std::ldexp(1.0, 30))
+    if (lim * std::pow(f, (double)(d->octaves - 1)) >= std::ldexp(1.0, 30))
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "OpenSimplex lattice coordinates exceed 2^30");
     double amp = 1.0;
     int box = 0;
     for (int i = 0; i < d->octaves; ++i) {
-        const double scale = std::ldexp(1.0, i);
+        const double scale = f == 2.0 ? std::ldexp(1.0, i) : std::pow(f, (double)i);
         const double step = scale / spc;
         // stage the tile's vertex gradients while the lattice is coarser than
         // the samples; the box side is bounded by 64 step + 7 vertices
@@ -229,6 +239,56 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
         P->amp[i] = (float)amp;
         P->key[i] = (d->seed << 8) | (uint32_t)i;
         amp *= (double)d->persistence;
+    }
+    P->box_words = box;
+    return PTG_OK;
+}
+
+// Launch plan of a 2D polynomial / Perlin field with a frequency ratio other
+// than 2 (or of a band of one), for the per-sample generator.
+int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int s, int64_t band_start,
+                          int64_t band_len, GeneralPlan* P)
+{
+    memset(P, 0, sizeof *P);
+    P->out = out;
+    P->W = (int32_t)d->size[0];
+    P->H = (int32_t)band_len;
+    P->dtype = d->dtype;
+    P->N = d->octaves;
+    P->method = method;
+    P->tiles_x = (P->W + kTile2dX - 1) / kTile2dX;
+    P->tiles_y = (P->H + kTile2dY - 1) / kTile2dY;
+    if (P->tiles_y > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall for one launch");
+    const int esz = d->dtype == PTG_F16 ? 2 : 4;
+    P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
+    const double spc = std::ldexp(1.0, s), f = (double)d->lacunarity;
+    const double p = (double)d->persistence, w = (double)d->grad_weight;
+    double amp = 1.0;
+    int box = 0;
+    for (int i = 0; i < d->octaves; ++i) {
+        const double fi = std::pow(f, (double)i), scale = fi / spc;
+        P->base_x[i] = (double)d->origin[0] * fi + (double)d->offset[0] * scale;
+        P->base_y[i] = (double)d->origin[1] * fi + (double)(d->offset[1] + band_start) * scale;
+        P->scale[i] = scale;
+        P->scale_hi[i] = (float)scale;
+        P->scale_lo[i] = (float)(scale - (double)P->scale_hi[i]);
+        P->amp[i] = (float)amp;
+        P->ampw[i] = (float)(amp * w);
+        P->key[i] = (d->seed << 8) | (uint32_t)i;
+        // stage the corners of the cells a tile spans while cells cover two or
+        // more samples: one cell before the base cell, floor(63 scale) + 1
+        // after it, one more for rounding, and the corner past the last cell
+        P->box_w[i] = 0;
+        if (scale <= 0.5) {
+            const int bw = (int)std::floor(63.0 * scale) + 5;
+            if ((size_t)(box + bw * bw) * sizeof(float4) <= (size_t)96 * 1024) {
+                P->box_off[i] = box;
+                P->box_w[i] = bw;
+                P->box_magic[i] = (uint32_t)(((uint64_t{1} << 32) + (uint64_t)bw - 1) / (uint64_t)bw);
+                box += bw * bw;
+            }
+        }
+        amp *= p;
     }
     P->box_words = box;
     return PTG_OK;
@@ -254,6 +314,11 @@ int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void
         int rc = ptg_make_simplex_plan(ctx, d, out, s, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
         e = launch_opensimplex2d(P, st);
+    } else if (d->lacunarity != 2.0f) {
+        GeneralPlan P;
+        int rc = ptg_make_general_plan(ctx, d, ptg_kernel_method(kind, d), out, s, band_start, band_len, &P);
+        if (rc != PTG_OK) return rc;
+        e = launch_general2d(P, st);
     } else {
         const int method = ptg_kernel_method(kind, d);
         FieldPlan P;
@@ -392,6 +457,9 @@ int ptg_validate(const ptg_field_desc* d, int32_t method, char* msg, int32_t msg
         if (kind == kKindSimplex) {
             SimplexPlan P;
             rc = ptg_make_simplex_plan(&scratch, d, nullptr, s, 0, slow, &P);
+        } else if (d->lacunarity != 2.0f) {
+            GeneralPlan P;
+            rc = ptg_make_general_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, s, 0, slow, &P);
         } else {
             FieldPlan P;
             rc = ptg_make_field_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, s, 0, slow, &P);

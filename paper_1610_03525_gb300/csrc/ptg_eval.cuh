@@ -113,6 +113,19 @@ constexpr TileWeights<D, RW> make_tile_weights()
     return w;
 }
 
+// Corner data of one staged corner from its hash words, pre-scaled by the
+// octave amplitude (and the gradient weight w of Sec. 4): (v, f, g, 0) for
+// the Hermite cells and the paper's D2M1N3, (v, 0, 0, 0) for the
+// zero-gradient model, (0, f, g, 0) for Perlin.
+template <int METHOD>
+__device__ __forceinline__ float4 corner_data(uint32_t hx, uint32_t hy, uint32_t hz, float amp, float ampw)
+{
+    if (METHOD == kZeroGrad) return make_float4(unit_value(hx) * amp, 0.0f, 0.0f, 0.0f);
+    if (METHOD == kC1 || METHOD == kC2 || METHOD == kPaperGauge)
+        return make_float4(unit_value(hx) * amp, unit_value(hy) * ampw, unit_value(hz) * ampw, 0.0f);
+    return make_float4(0.0f, unit_value(hy) * amp, unit_value(hz) * amp, 0.0f);
+}
+
 // Per-axis basis of an in-cell position t as compile-time values, computed in
 // double and rounded once: the functions of axis_basis.
 struct alignas(16) Basis4 {

@@ -184,14 +184,7 @@ __device__ __forceinline__ void stage_tile(const FieldPlan& P, float4* sm, int j
             const int cx = e - cy * op.ncx;
             uint32_t x = bx + (uint32_t)cx, y = by + (uint32_t)cy, z = op.key;
             pcg3d(x, y, z);
-            float4 c;
-            if (METHOD == kZeroGrad)  // corner values only (Eq. zg has zero gradients)
-                c = make_float4(unit_value(x) * op.amp, 0.0f, 0.0f, 0.0f);
-            else if (METHOD == kC1 || METHOD == kC2 || METHOD == kPaperGauge)
-                c = make_float4(unit_value(x) * op.amp, unit_value(y) * op.ampw, unit_value(z) * op.ampw, 0.0f);
-            else
-                c = make_float4(0.0f, unit_value(y) * op.amp, unit_value(z) * op.amp, 0.0f);
-            cg[cy * op.rowlen + corner_slot(cx)] = c;
+            cg[cy * op.rowlen + corner_slot(cx)] = corner_data<METHOD>(x, y, z, op.amp, op.ampw);
         }
     }
 }

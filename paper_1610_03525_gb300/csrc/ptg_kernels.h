@@ -39,6 +39,26 @@ struct SimplexPlan {
 };
 cudaError_t launch_opensimplex2d(const SimplexPlan& P, cudaStream_t stream);
 
+// Polynomial and Perlin fields with any frequency ratio f between octaves
+// (2D).  base[i] = lattice coordinate of output sample (0, 0) at octave i
+// (FP64, host); scale[i] = f^i / spc lattice units per sample, also split
+// into two floats (hi + lo) for the per-sample offsets inside a tile.
+struct GeneralPlan {
+    void* out;
+    int32_t W, H, dtype, N, vec_ok, tiles_x, tiles_y, method;
+    int32_t box_words;  // float4 words of shared memory for all staged corner boxes
+    int32_t pad[3];
+    double base_x[kMaxOctaves], base_y[kMaxOctaves];
+    double scale[kMaxOctaves];
+    float scale_hi[kMaxOctaves], scale_lo[kMaxOctaves];
+    float amp[kMaxOctaves], ampw[kMaxOctaves];
+    uint32_t key[kMaxOctaves];
+    int32_t box_off[kMaxOctaves];  // staged corner box of octave i: first float4 in shared memory
+    int32_t box_w[kMaxOctaves];    // its side (cells + 1); 0 = hash the corners of each sample
+    uint32_t box_magic[kMaxOctaves];  // ceil(2^32 / box_w)
+};
+cudaError_t launch_general2d(const GeneralPlan& P, cudaStream_t stream);
+
 // Test hooks.
 cudaError_t launch_debug_hash(int dims, const uint32_t* keys, long long n, uint32_t* out, cudaStream_t stream);
 cudaError_t launch_debug_axis(long long origin, int s, int octave, const long long* j, long long n,

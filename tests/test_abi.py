@@ -57,7 +57,12 @@ def test_desc_layout_matches_header(P):
     (dict(smoothness=5), 0, -1),
     (dict(smoothness=3), 0, 0),
     (dict(smoothness=4, dims=3, size=(32, 32, 32)), 0, -2),
-    (dict(lacunarity=3.0), 0, -2),
+    (dict(lacunarity=3.0), 0, 0),                     # any frequency ratio in 2D
+    (dict(lacunarity=1.5), 2, 0),
+    (dict(lacunarity=3.0, dims=3, size=(32, 32, 32)), 0, -2),
+    (dict(lacunarity=0.5), 0, -1),
+    (dict(lacunarity=17.0), 0, -1),
+    (dict(lacunarity=3.0, octaves=20, spc=64, size=(64, 64)), 0, -2),  # 3^19 lattice units
     (dict(seed=1 << 24), 0, -1),
     (dict(dtype=7), 0, -1),
     (dict(dims=4), 0, -1),

@@ -34,12 +34,13 @@ def ctx():
 
 
 def gpu_field(ctx, kind, dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 0, 0), offset=(0, 0, 0),
-              seed=0, persistence=0.5, grad_weight=1.0, dtype=P.PTG_F32, shape=P.PTG_SHAPE_AUTO, coarse=0):
+              seed=0, persistence=0.5, grad_weight=1.0, dtype=P.PTG_F32, shape=P.PTG_SHAPE_AUTO, coarse=0,
+              lacunarity=2.0):
     smooth = SMOOTH.get(kind, P.PTG_C1)
     variant = (P.PTG_PERLIN_S3 if kind == "perlin_s3" else P.PTG_PERLIN_S5) | shape | coarse
     d = P.make_desc(dims=dims, size=size, spc=spc, origin=origin, offset=offset, octaves=octaves,
                     smoothness=smooth, persistence=persistence, grad_weight=grad_weight, seed=seed, dtype=dtype,
-                    variant=variant)
+                    variant=variant, lacunarity=lacunarity)
     shape = tuple(reversed(size[:dims]))
     out = torch.full(shape, float("nan"), dtype=torch.float16 if dtype == P.PTG_F16 else torch.float32,
                      device="cuda")
@@ -54,13 +55,14 @@ def gpu_field(ctx, kind, dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 
 
 
 def oracle_at(kind, idx, dims=2, spc=64, octaves=6, origin=(0, 0, 0), offset=(0, 0, 0), seed=0,
-              persistence=0.5, grad_weight=1.0):
+              persistence=0.5, grad_weight=1.0, lacunarity=2.0):
     """Oracle values at sample indices idx (n, dims) of the window."""
     idx = np.asarray(idx, np.int64) + np.asarray(offset[:dims], np.int64)[None, :]
     size = (spc,) * dims
     cells = (1,) * dims
     return O.field_samples(dims, size, cells, idx, octaves=octaves, method=KIND_ORACLE[kind],
-                           persistence=persistence, grad_weight=grad_weight, seed=seed, origin=origin)
+                           persistence=persistence, grad_weight=grad_weight, seed=seed, origin=origin,
+                           frequency=lacunarity)
 
 
 def tol32(octaves, persistence=0.5):
@@ -254,6 +256,45 @@ def test_launch_config_fp16_and_mosaic(ctx, shape, coarse):
 
 
 # ---------------------------------------------------------------------------
+# any frequency ratio f between octaves (Sec. 4), per-sample generator
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3", "paper_gauge", "zero_grad", "opensimplex"])
+@pytest.mark.parametrize("f", [1.5, 1.93, 3.0])
+@pytest.mark.parametrize("size,spc,octaves,origin", [
+    ((256, 192), 64, 6, (0, 0, 0)),
+    ((130, 70), 16, 9, (-(1 << 10) + 3, 345, 0)),    # ragged, cells down to a fraction of a sample
+    ((96, 64), 1024, 8, (1 << 16, -(1 << 16), 0)),   # world offset, coarse cells
+])
+def test_any_lacunarity_vs_oracle(ctx, kind, f, size, spc, octaves, origin):
+    out = gpu_field(ctx, kind, size=size, spc=spc, octaves=octaves, origin=origin, seed=13, persistence=0.6,
+                    grad_weight=0.75, lacunarity=f)
+    idx = W.grid_indices_2d(*size)
+    ref = oracle_at(kind, idx, spc=spc, octaves=octaves, origin=origin, seed=13, persistence=0.6, grad_weight=0.75,
+                    lacunarity=f)
+    err = np.abs(gather(out, idx) - ref).max()
+    assert err <= tol32(octaves, 0.6), err
+
+
+@pytest.mark.parametrize("kind", ["c1", "perlin_s5"])
+def test_any_lacunarity_fp16_host_and_chunks(ctx, kind):
+    f, size, spc, N = 1.75, (1000, 777), 128, 10
+    out = gpu_field(ctx, kind, size=size, spc=spc, octaves=N, seed=4, lacunarity=f, dtype=P.PTG_F16)
+    idx = W.subsample(size, every=97, n_random=8192, seed=3)
+    ref = oracle_at(kind, idx, spc=spc, octaves=N, seed=4, lacunarity=f)
+    assert np.all(np.abs(gather(out, idx) - ref) <= tol32(N) + half_ulp16(ref))
+    # banded host output equals the device field
+    d = P.make_desc(dims=2, size=size, spc=spc, octaves=N, seed=4, lacunarity=f, dtype=P.PTG_F16,
+                    variant=P.PTG_PERLIN_S5 if kind == "perlin_s5" else 0)
+    host = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    P.ptg_generate_host(ctx, d, 1 if kind == "perlin_s5" else 0, host)
+    assert torch.equal(host, out.cpu()) or float((host.float() - out.float().cpu()).abs().max()) <= 2 * tol32(N) + 1e-3
+    # a window of the field: the same values to rounding (tile bases are formed per tile in FP64)
+    big = gpu_field(ctx, kind, size=(512, 384), spc=spc, octaves=N, seed=4, lacunarity=f)
+    part = gpu_field(ctx, kind, size=(256, 192), spc=spc, octaves=N, seed=4, lacunarity=f, offset=(256, 128, 0))
+    assert float((part - big[128:320, 256:512]).abs().max()) <= 2 * tol32(N)
+
+
+# ---------------------------------------------------------------------------
 # full-size configurations in the benchmark's launch configuration, sampled
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kind,seed,dtype", [("c1", 0, P.PTG_F32), ("c2", 3, P.PTG_F32), ("c1", 1, P.PTG_F16),
@@ -337,7 +378,7 @@ def test_short_forms(ctx):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kw,code", [
     (dict(size=(0, 16)), P.PTG_ERR_INVALID), (dict(spc=3), P.PTG_ERR_UNSUPPORTED),
-    (dict(octaves=0), P.PTG_ERR_INVALID), (dict(lacunarity=2.5), P.PTG_ERR_UNSUPPORTED),
+    (dict(octaves=0), P.PTG_ERR_INVALID), (dict(lacunarity=0.5), P.PTG_ERR_INVALID),
     (dict(smoothness=9), P.PTG_ERR_INVALID), (dict(seed=1 << 24), P.PTG_ERR_INVALID),
 ])
 def test_invalid_arguments_write_nothing(ctx, kw, code):
