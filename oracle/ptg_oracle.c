@@ -470,6 +470,29 @@ static double perlin_eval(const double* corner, const double* t, int quintic)
     return h0 + sy * (h1 - h0);
 }
 
+/* Perlin's polynomial in 3D (Sec. 3.2 with a third axis): v_ijk = f (x - i) +
+ * g (y - j) + e (z - k) at each of the 8 corners, blended along x by S(x),
+ * then along y by S(y), then along z by S(z). */
+static double perlin_eval3(const double* corner, const double* t, int quintic)
+{
+    double v[2][2][2];
+    for (int k = 0; k < 2; ++k)
+        for (int j = 0; j < 2; ++j)
+            for (int i = 0; i < 2; ++i) {
+                const double* c = corner + (i + 2 * j + 4 * k) * 4;
+                v[i][j][k] = c[1] * (t[0] - i) + c[2] * (t[1] - j) + c[3] * (t[2] - k);
+            }
+    const double sx = quintic ? s5(t[0]) : s3(t[0]), sy = quintic ? s5(t[1]) : s3(t[1]);
+    const double sz = quintic ? s5(t[2]) : s3(t[2]);
+    double hz[2];
+    for (int k = 0; k < 2; ++k) {
+        const double h0 = v[0][0][k] + sx * (v[1][0][k] - v[0][0][k]);
+        const double h1 = v[0][1][k] + sx * (v[1][1][k] - v[0][1][k]);
+        hz[k] = h0 + sy * (h1 - h0);
+    }
+    return hz[0] + sz * (hz[1] - hz[0]);
+}
+
 /* One octave of a lattice method at (cell, t), t_k in [0, 1] (the cell's own
  * polynomial, also at t = 1 for one-sided difference tests). */
 static double lattice_octave(int dims, int method, const uint32_t* cell, const double* t, uint32_t seed,
@@ -479,6 +502,7 @@ static double lattice_octave(int dims, int method, const uint32_t* cell, const d
     if (method == PTGO_ZERO_GRAD || method == PTGO_PERLIN_S5 || method == PTGO_PERLIN_S3) {
         cell_corners(dims, cell, seed, octave, corner);
         if (method == PTGO_ZERO_GRAD) return zero_grad_eval(corner, t);
+        if (dims == 3) return perlin_eval3(corner, t, method == PTGO_PERLIN_S5);
         return perlin_eval(corner, t, method == PTGO_PERLIN_S5);
     }
     int n = method_degree(method);
@@ -538,7 +562,8 @@ static int desc_ok(const ptgo_desc* d)
     if (!(d->frequency == 0.0 || (d->frequency >= 1.0 && d->frequency <= 16.0))) return 0;
     for (int k = 0; k < d->dims; ++k)
         if (d->size[k] <= 0 || d->cells[k] <= 0 || d->size[k] % d->cells[k]) return 0;
-    if (d->method == PTGO_C1 || d->method == PTGO_C2) return 1;
+    if (d->method == PTGO_C1 || d->method == PTGO_C2 || d->method == PTGO_PERLIN_S5 || d->method == PTGO_PERLIN_S3)
+        return 1;
     if (d->dims == 2 && (d->method == PTGO_PAPER_GAUGE || d->method == PTGO_ZERO_GRAD ||
                          d->method == PTGO_PERLIN_S5 || d->method == PTGO_PERLIN_S3 ||
                          d->method == PTGO_OPENSIMPLEX))

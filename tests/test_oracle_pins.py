@@ -453,14 +453,53 @@ def test_perlin_edge_depends_on_edge_corners_only():
         assert np.abs(got - ref).max() < 1e-14
 
 
-def test_perlin_s5_is_c2_s3_is_c1():
+@pytest.mark.parametrize("dims", [2, 3])
+def test_perlin_s5_is_c2_s3_is_c1(dims):
+    cell0 = [7, 8, 9][:dims]
     for meth in (O.PERLIN_S5, O.PERLIN_S3):
-        for axis in range(2):
-            t_face = RNG.uniform(0, 1, size=(10, 2))
-            (hL, d1L, d2L), (hR, d1R, d2R) = _one_sided(meth, 2, axis, [7, 8], t_face, 1.0, 2, 1, 2)
+        for axis in range(dims):
+            t_face = RNG.uniform(0, 1, size=(10, dims))
+            (hL, d1L, d2L), (hR, d1R, d2R) = _one_sided(meth, dims, axis, cell0, t_face, 1.0, 2, 1, 2)
             assert np.abs(hL - hR).max() < 1e-13 and np.abs(d1L - d1R).max() < 1e-6
             if meth == O.PERLIN_S5:
                 assert np.abs(d2L - d2R).max() < 1e-3
+
+
+@pytest.mark.parametrize("meth", [O.PERLIN_S5, O.PERLIN_S3])
+def test_perlin_3d_zero_at_lattice_points_and_gradient(meth):
+    """3D Perlin: zero at the 8 corners, gradient there = hash words 1..3 of
+    the corner (pcg4d of (ix, iy, iz, key))."""
+    eps = 1e-6
+    for s in range(8):
+        b = np.array([s & 1, (s >> 1) & 1, s >> 2], float)
+        h = _grid_eval(meth, 3, [3, 4, 5], b[None, :])[0]
+        assert abs(h) < 1e-15
+        cc = np.array([[3 + (s & 1), 4 + ((s >> 1) & 1), 5 + (s >> 2), (7 << 8) | 3]], np.uint32)
+        hv = [O.unit(v) for v in O.hash_batch(3, cc)[0]]
+        for k in range(3):
+            d = np.zeros(3)
+            d[k] = eps if b[k] == 0 else -eps
+            hp = _grid_eval(meth, 3, [3, 4, 5], (b + d)[None, :])[0]
+            assert abs((hp - h) / d[k] - hv[1 + k]) < 1e-5
+
+
+def test_perlin_3d_face_is_2d_perlin_of_face_corners():
+    """On the face z = 0 the 3D cell is the 2D Perlin polynomial of the four
+    face corners with their x and y gradients (S(0) = 0, and z - 0 = 0)."""
+    t2 = RNG.uniform(0, 1, size=(64, 2))
+    for meth in (O.PERLIN_S5, O.PERLIN_S3):
+        got = _grid_eval(meth, 3, [3, 4, 5], np.concatenate([t2, np.zeros((64, 1))], 1))
+        S = _s5 if meth == O.PERLIN_S5 else _s3
+        g = {}
+        for a in (0, 1):
+            for b in (0, 1):
+                w = O.hash_batch(3, np.array([[3 + a, 4 + b, 5, (7 << 8) | 3]], np.uint32))[0]
+                g[a, b] = (O.unit(w[1]), O.unit(w[2]))
+        x, y = t2[:, 0], t2[:, 1]
+        v = {k: g[k][0] * (x - k[0]) + g[k][1] * (y - k[1]) for k in g}
+        h0 = v[0, 0] + S(x) * (v[1, 0] - v[0, 0])
+        h1 = v[0, 1] + S(x) * (v[1, 1] - v[0, 1])
+        assert np.abs(got - (h0 + S(y) * (h1 - h0))).max() < 1e-14
 
 
 SQ = (math.sqrt(3) - 1) / 2
