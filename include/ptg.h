@@ -159,8 +159,10 @@ int ptg_volume3d(ptg_ctx* ctx, const int64_t size[3], int32_t octaves, int32_t s
  * in 2D or 3D, the paper's D2M1N3 and zero-gradient models in 2D). */
 int ptg_field(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, void* stream);
 
-/* Perlin's polynomial (Sec. 3.2) with the same lattice, hash words 1..2 as
- * the corner gradient (unweighted), desc->variant selects S5 or S3.  2D. */
+/* Perlin's polynomial (Sec. 3.2) with the same lattice: at each corner the
+ * dot product of its gradient with the offset to the corner, blended by S
+ * along every axis.  The gradient is hash words 1..2 (2D, pcg3d) or 1..3
+ * (3D, pcg4d), unweighted; desc->variant selects S5 or S3.  2D or 3D. */
 int ptg_perlin(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, void* stream);
 
 /* OpenSimplex-style noise (Sec. 1, Sec. 5 baseline): the base lattice is

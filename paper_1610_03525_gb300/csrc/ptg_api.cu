@@ -52,8 +52,8 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
     if (d->struct_size != sizeof(ptg_field_desc))
         return ptg_fail(ctx, PTG_ERR_INVALID, "struct_size %u != %zu", d->struct_size, sizeof(ptg_field_desc));
     if (d->dims != 2 && d->dims != 3) return ptg_fail(ctx, PTG_ERR_INVALID, "dims must be 2 or 3");
-    if (kind != kKindField && d->dims != 2)
-        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "Perlin and OpenSimplex baselines are 2D");
+    if (kind == kKindSimplex && d->dims != 2)
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "the OpenSimplex baseline is 2D");
     const int s = log2_exact(d->spc);
     if (d->spc <= 0 || d->spc > (int64_t{1} << 30)) return ptg_fail(ctx, PTG_ERR_INVALID, "spc out of [1, 2^30]");
     if (s < 0) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "spc (samples per cell) must be a power of two");

@@ -1,5 +1,6 @@
 // ptg_fbm3d.cu -- fused all-octave 3D generator (D3M1N3 / D3M2N5 cells of
-// Thorimbert & Chopard, arXiv:1610.03525, Sec. 3.4; fractal sum of Sec. 4).
+// Thorimbert & Chopard, arXiv:1610.03525, Sec. 3.4; fractal sum of Sec. 4),
+// and Perlin's polynomial (Sec. 3.2) in 3D as a baseline.
 //
 // One CTA makes a 32 x 16 x 8 tile (x, y, z) with 128 threads; each thread
 // owns 8 consecutive x samples in 4 rows of one z plane (32 sums in
@@ -7,7 +8,10 @@
 // reduced along z,
 //    W_ab = v_ab0 + S(z) (v_ab1 - v_ab0) + B0(z) e_ab0 + B1(z) e_ab1,
 //    F_ab = f_ab0 + S(z) (f_ab1 - f_ab0),   G_ab = g_ab0 + S(z) (g_ab1 - g_ab0),
-// which leaves the 2D cell with (v, f, g) -> (W, F, G), handled as in 2D:
+// which leaves the 2D cell with (v, f, g) -> (W, F, G), handled as in 2D.
+// Perlin has v = 0 and its own B0 = (1 - S) t, B1 = S (t - 1), so the same
+// reduction gives W_ab = B0(z) e_ab0 + B1(z) e_ab1 (the z part of the corner
+// dot products) and the 2D Perlin cell with those values:
 // octaves whose cells are >= 8 samples wide evaluate node columns only and
 // interpolate once; cells of 4 and 2 samples use constant in-cell positions
 // along x and y; lattice octaves take one pcg4d corner value per sample.
@@ -83,8 +87,10 @@ __device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int 
             uint32_t x = bx + (uint32_t)cx, y = by + (uint32_t)cy, z = bz + (uint32_t)cz, w = op.key;
             pcg4d(x, y, z, w);
             cg[(cz * op.ncy + cy) * op.rowlen + corner_slot(cx)] =
-                make_float4(unit_value(x) * op.amp, unit_value(y) * op.ampw, unit_value(z) * op.ampw,
-                            unit_value(w) * op.ampw);
+                (METHOD == kPerlinS5 || METHOD == kPerlinS3)  // Perlin: no value, gradient unweighted
+                    ? make_float4(0.0f, unit_value(y) * op.amp, unit_value(z) * op.amp, unit_value(w) * op.amp)
+                    : make_float4(unit_value(x) * op.amp, unit_value(y) * op.ampw, unit_value(z) * op.ampw,
+                                  unit_value(w) * op.ampw);
         }
     }
 }
@@ -261,9 +267,10 @@ __global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__
         }
     if (s >= 2 && s - 2 < N) small_octave3<METHOD, 4>(acc, sm, P, s - 2, tx, ty, tz, n8);
     if (s >= 1 && s - 1 < N) small_octave3<METHOD, 2>(acc, sm, P, s - 1, tx, ty, tz, n8);
-    for (int i = s; i < N; ++i)
-        lattice_octave3(acc, P.oct[i], (uint32_t)(j0x + tx * kCols), (uint32_t)(j0y + ty * kRows),
-                        (uint32_t)(j0z + tz));
+    if (METHOD != kPerlinS5 && METHOD != kPerlinS3)  // Perlin is zero at lattice points
+        for (int i = s; i < N; ++i)
+            lattice_octave3(acc, P.oct[i], (uint32_t)(j0x + tx * kCols), (uint32_t)(j0y + ty * kRows),
+                            (uint32_t)(j0z + tz));
     store_tile3<OutT>(P, acc, x0 + tx * kCols, y0 + ty * kRows, z0 + tz);
 }
 
@@ -279,7 +286,14 @@ size_t smem_words3(const FieldPlan& P)
 
 size_t fbm3d_smem_bytes(const FieldPlan& P)
 {
-    return sizeof(float4) * (P.method == kC2 ? smem_words3<kC2>(P) : smem_words3<kC1>(P));
+    size_t w = 0;
+    switch (P.method) {
+    case kC2: w = smem_words3<kC2>(P); break;
+    case kPerlinS5: w = smem_words3<kPerlinS5>(P); break;
+    case kPerlinS3: w = smem_words3<kPerlinS3>(P); break;
+    default: w = smem_words3<kC1>(P); break;
+    }
+    return sizeof(float4) * w;
 }
 
 cudaError_t launch_fbm3d(const FieldPlan& P, int method, int /*s*/, cudaStream_t stream)
@@ -302,6 +316,8 @@ cudaError_t launch_fbm3d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
     switch (method) {
     case kC1: if (f16) PTG_LAUNCH3D(kC1, __half); else PTG_LAUNCH3D(kC1, float);
     case kC2: if (f16) PTG_LAUNCH3D(kC2, __half); else PTG_LAUNCH3D(kC2, float);
+    case kPerlinS5: if (f16) PTG_LAUNCH3D(kPerlinS5, __half); else PTG_LAUNCH3D(kPerlinS5, float);
+    case kPerlinS3: if (f16) PTG_LAUNCH3D(kPerlinS3, __half); else PTG_LAUNCH3D(kPerlinS3, float);
     default: return cudaErrorInvalidValue;
     }
 #undef PTG_LAUNCH3D

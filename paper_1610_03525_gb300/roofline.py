@@ -141,7 +141,7 @@ def lane_ops_3d(kind: str, size, spc: int, octaves: int) -> dict:
             evalops += threads * (2 * (32 + 4 + 1 + 3 * 9) + 24 * 4 + 8)
         else:
             evalops += threads * (8 * (32 + 4 + 1 + 9) + 80)
-    lattice = samples_padded * (octaves - len(st)) * 15
+    lattice = 0 if kind.startswith("perlin") else samples_padded * (octaves - len(st)) * 15
     tot = lut + corners + evalops + lattice
     return dict(total=float(tot), per_sample=tot / (w * h * dd), lut=lut, corners=corners, eval=evalops,
                 lattice=lattice)

@@ -66,7 +66,8 @@ def test_desc_layout_matches_header(P):
     (dict(seed=1 << 24), 0, -1),
     (dict(dtype=7), 0, -1),
     (dict(dims=4), 0, -1),
-    (dict(dims=3, size=(32, 32, 32)), 1, -2),
+    (dict(dims=3, size=(32, 32, 32)), 1, 0),          # Perlin in 3D
+    (dict(dims=3, size=(32, 32, 32)), 2, -2),         # OpenSimplex is 2D
     (dict(variant=5), 1, -1),
     (dict(offset=(32, 0, 0)), 0, -2),
     (dict(offset=(128, 64, 0)), 0, 0),

@@ -176,7 +176,7 @@ def test_ragged_and_tiny(ctx, kind, size, spc, octaves):
     assert err <= tol32(octaves, 0.6), err
 
 
-@pytest.mark.parametrize("kind", ["c1", "c2"])
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3"])
 @pytest.mark.parametrize("dtype", [P.PTG_F32, P.PTG_F16])
 def test_3d_world_offset(ctx, kind, dtype):
     size, spc, N, origin = (48, 40, 24), 8, 6, (1 << 20, 1 << 20, 0)
@@ -190,7 +190,7 @@ def test_3d_world_offset(ctx, kind, dtype):
 
 def test_3d_ragged(ctx):
     size, spc, N = (37, 19, 11), 4, 5
-    for kind in ("c1", "c2"):
+    for kind in ("c1", "c2", "perlin_s5", "perlin_s3"):
         out = gpu_field(ctx, kind, dims=3, size=size, spc=spc, octaves=N, origin=(-7, 3, -(1 << 30)), seed=2)
         idx = W.grid_indices_3d(*size)
         ref = oracle_at(kind, idx, dims=3, spc=spc, octaves=N, origin=(-7, 3, -(1 << 30)), seed=2)
@@ -313,12 +313,13 @@ def test_sampled_8192_n12(ctx, kind, seed, dtype):
         assert float(out.float().abs().max()) <= 1.5 * W.total_amplitude(12) + 1e-5
 
 
-def test_sampled_3d_512_n8(ctx):
+@pytest.mark.parametrize("kind", ["c1", "perlin_s5"])
+def test_sampled_3d_512_n8(ctx, kind):
     cfg = W.CONFIGS["3d_512_n8"]
-    out = gpu_field(ctx, "c1", dims=3, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"],
+    out = gpu_field(ctx, kind, dims=3, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"],
                     origin=cfg["origin"], seed=0, dtype=P.PTG_F16)
     idx = W.subsample(cfg["size"], every=256, n_random=1 << 15, seed=1)
-    ref = oracle_at("c1", idx, dims=3, spc=cfg["spc"], octaves=cfg["octaves"], origin=cfg["origin"], seed=0)
+    ref = oracle_at(kind, idx, dims=3, spc=cfg["spc"], octaves=cfg["octaves"], origin=cfg["origin"], seed=0)
     err = np.abs(gather(out, idx) - ref)
     assert np.all(err <= tol32(cfg["octaves"]) + half_ulp16(ref)), err.max()
 
@@ -336,9 +337,10 @@ def test_chunk_mosaic_bit_exact(ctx, kind):
             assert torch.equal(part, big[oy:oy + 192, ox:ox + 256])
 
 
-def test_3d_chunk_mosaic_bit_exact(ctx):
-    big = gpu_field(ctx, "c1", dims=3, size=(64, 32, 16), spc=16, octaves=7, seed=4)
-    part = gpu_field(ctx, "c1", dims=3, size=(32, 16, 8), spc=16, octaves=7, offset=(32, 16, 8), seed=4)
+@pytest.mark.parametrize("kind", ["c1", "perlin_s5"])
+def test_3d_chunk_mosaic_bit_exact(ctx, kind):
+    big = gpu_field(ctx, kind, dims=3, size=(64, 32, 16), spc=16, octaves=7, seed=4)
+    part = gpu_field(ctx, kind, dims=3, size=(32, 16, 8), spc=16, octaves=7, offset=(32, 16, 8), seed=4)
     assert torch.equal(part, big[8:16, 16:32, 32:64])
 
 
