@@ -110,11 +110,14 @@ typedef struct {
     uint32_t struct_size; /* sizeof(ptg_field_desc)                            */
     int32_t dims;         /* 2 or 3                                            */
     int64_t size[3];      /* samples per axis (x, y, z), each in [1, 2^30]; unused = 1 */
-    int64_t spc;          /* samples per base cell: power of two in [1, 2^30]  */
+    int64_t spc;          /* samples per base cell, in [1, 2^30]: a power of
+                             two in 3D; in 2D any other value runs the
+                             per-sample generator (see lacunarity)          */
     int64_t origin[3];    /* base-lattice cell of the window (wraps mod 2^32)  */
-    int64_t offset[3];    /* sample offset of the window: a multiple of
-                             min(spc, tile) with tile 64 (2D) or 32/16/8 (3D
-                             x/y/z); offset + size <= 2^31                     */
+    int64_t offset[3];    /* sample offset of the window, offset + size <=
+                             2^31; for the fused generators (power-of-two spc,
+                             lacunarity 2) a multiple of min(spc, tile) with
+                             tile 64 (2D) or 32/16/8 (3D x/y/z)              */
     int32_t octaves;      /* N in [1, 32]                                      */
     int32_t smoothness;   /* ptg_smoothness (ptg_field, ptg_submit)            */
     float persistence;    /* amplitude ratio between octaves (0.5 typical)     */

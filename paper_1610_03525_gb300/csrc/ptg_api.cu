@@ -45,7 +45,8 @@ int ptg_cuda_fail(ptg_ctx* ctx, cudaError_t e, const char* where)
     return ptg_fail(ctx, PTG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-// Argument checks common to every generator.  On success fills *spc_log2.
+// Argument checks common to every generator.  On success fills *spc_log2
+// (-1 when spc is not a power of two: 2D, per-sample generators).
 int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log2)
 {
     if (!d) return ptg_fail(ctx, PTG_ERR_INVALID, "descriptor is NULL");
@@ -56,7 +57,11 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "the OpenSimplex baseline is 2D");
     const int s = log2_exact(d->spc);
     if (d->spc <= 0 || d->spc > (int64_t{1} << 30)) return ptg_fail(ctx, PTG_ERR_INVALID, "spc out of [1, 2^30]");
-    if (s < 0) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "spc (samples per cell) must be a power of two");
+    if (s < 0 && d->dims != 2)
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "spc (samples per cell) must be a power of two in 3D");
+    // the fused generators need tiles aligned to cells; the per-sample ones
+    // (OpenSimplex, and 2D fields with any other spc or frequency ratio) do not
+    const bool fused = kind != kKindSimplex && s >= 0 && d->lacunarity == 2.0f;
     static const int tile2[3] = {kTile2dX, kTile2dY, 1}, tile3[3] = {kTile3dX, kTile3dY, kTile3dZ};
     for (int k = 0; k < d->dims; ++k) {
         if (d->size[k] <= 0 || d->size[k] > (int64_t{1} << 30))
@@ -65,7 +70,7 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
             return ptg_fail(ctx, PTG_ERR_INVALID, "offset[%d] must be >= 0 with offset + size <= 2^31", k);
         const int64_t tile = d->dims == 3 ? tile3[k] : tile2[k];
         const int64_t align = d->spc < tile ? d->spc : tile;
-        if (d->offset[k] % align)
+        if (fused && d->offset[k] % align)
             return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "offset[%d] must be a multiple of %lld", k, (long long)align);
     }
     if (d->octaves < 1 || d->octaves > kMaxOctaves)
@@ -209,7 +214,8 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
     if (P->tiles_y > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall for one launch");
     const int esz = d->dtype == PTG_F16 ? 2 : 4;
     P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
-    const double spc = std::ldexp(1.0, s), f = (double)d->lacunarity;
+    (void)s;
+    const double spc = (double)d->spc, f = (double)d->lacunarity;
     double lim = 0.0;
     for (int k = 0; k < 2; ++k) {
         const double e = std::fabs((double)d->origin[k]) + (double)(d->offset[k] + d->size[k]) / spc;
@@ -235,7 +241,11 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
         }
         P->base_x[i] = (double)d->origin[0] * scale + (double)d->offset[0] * step;
         P->base_y[i] = (double)d->origin[1] * scale + (double)(d->offset[1] + band_start) * step;
+        P->step_d[i] = step;
         P->step[i] = (float)step;
+        P->step_lo[i] = (float)(step - (double)P->step[i]);
+        int ex = 0;
+        if (std::frexp(step, &ex) == 0.5) P->exact_mask |= 1u << i;
         P->amp[i] = (float)amp;
         P->key[i] = (d->seed << 8) | (uint32_t)i;
         amp *= (double)d->persistence;
@@ -261,12 +271,13 @@ int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, voi
     if (P->tiles_y > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall for one launch");
     const int esz = d->dtype == PTG_F16 ? 2 : 4;
     P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
-    const double spc = std::ldexp(1.0, s), f = (double)d->lacunarity;
+    (void)s;
+    const double spc = (double)d->spc, f = (double)d->lacunarity;
     const double p = (double)d->persistence, w = (double)d->grad_weight;
     double amp = 1.0;
     int box = 0;
     for (int i = 0; i < d->octaves; ++i) {
-        const double fi = std::pow(f, (double)i), scale = fi / spc;
+        const double fi = f == 2.0 ? std::ldexp(1.0, i) : std::pow(f, (double)i), scale = fi / spc;
         P->base_x[i] = (double)d->origin[0] * fi + (double)d->offset[0] * scale;
         P->base_y[i] = (double)d->origin[1] * fi + (double)(d->offset[1] + band_start) * scale;
         P->scale[i] = scale;
@@ -314,7 +325,7 @@ int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void
         int rc = ptg_make_simplex_plan(ctx, d, out, s, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
         e = launch_opensimplex2d(P, st);
-    } else if (d->lacunarity != 2.0f) {
+    } else if (d->lacunarity != 2.0f || s < 0) {  // any frequency ratio or spc: per-sample generator
         GeneralPlan P;
         int rc = ptg_make_general_plan(ctx, d, ptg_kernel_method(kind, d), out, s, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
@@ -457,7 +468,7 @@ int ptg_validate(const ptg_field_desc* d, int32_t method, char* msg, int32_t msg
         if (kind == kKindSimplex) {
             SimplexPlan P;
             rc = ptg_make_simplex_plan(&scratch, d, nullptr, s, 0, slow, &P);
-        } else if (d->lacunarity != 2.0f) {
+        } else if (d->lacunarity != 2.0f || s < 0) {
             GeneralPlan P;
             rc = ptg_make_general_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, s, 0, slow, &P);
         } else {

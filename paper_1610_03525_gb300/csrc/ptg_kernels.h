@@ -25,17 +25,22 @@ size_t fbm3d_smem_bytes(const FieldPlan& P);
 cudaError_t launch_fbm3d(const FieldPlan& P, int method, int s, cudaStream_t stream);
 
 // OpenSimplex-style baseline (2D).  base[i] = (x0, y0) of sample (0, 0) at
-// octave i in lattice units (FP64, computed on the host); step[i] = 2^i / spc.
+// octave i in lattice units (FP64, computed on the host); step[i] = f^i / spc
+// lattice units per sample in FP64 (step_d), and as two floats step + step_lo
+// (step_lo = 0 when the step is a power of two).
 struct SimplexPlan {
     void* out;
     int32_t W, H, dtype, N, vec_ok, tiles_x, tiles_y;
     double base_x[kMaxOctaves], base_y[kMaxOctaves];
+    double step_d[kMaxOctaves];
     float step[kMaxOctaves];
+    float step_lo[kMaxOctaves];
     float amp[kMaxOctaves];
     uint32_t key[kMaxOctaves];
     int32_t box_off[kMaxOctaves];  // staged gradient box of octave i: first float2 in shared memory
     int32_t box_wb[kMaxOctaves];   // its side bound (row stride); 0 = hash vertices directly
     int32_t box_words;             // float2 words of shared memory for all boxes
+    uint32_t exact_mask;           // bit i: step[i] is a power of two (products k * step exact)
 };
 cudaError_t launch_opensimplex2d(const SimplexPlan& P, cudaStream_t stream);
 

@@ -50,9 +50,17 @@ constexpr float kScale = 0.125f;
 struct TileOctave {
     int32_t a0, b0;      // integer stretched vertex of the tile's first sample
     float fx, fy;        // its fractional stretched coordinates
+    float fxl, fyl;      // their rounding residuals (used when steps are not powers of two)
     int32_t amin, bmin;  // staged: first vertex of the gradient box
     int32_t w, h;        // staged: box extent actually filled (<= plan bound)
 };
+
+// a + b = s + err exactly (Knuth's two-sum).
+__device__ __forceinline__ float two_sum_err(float a, float b, float s)
+{
+    const float bv = s - a;
+    return (a - (s - bv)) + (b - bv);
+}
 
 __device__ __forceinline__ float kernel_term(float gx, float gy, float dx, float dy)
 {
@@ -113,12 +121,13 @@ __device__ __forceinline__ float sample_noise(const Grad<kStaged>& G, int32_t a,
            vertex_at(G, a, b, d3, d3, xi, yi) + vertex_at(G, a, b, ex, ey, xi, yi);
 }
 
-// One octave for the thread's 4 x 8 samples.
-template <bool kStaged>
+// One octave for the thread's 4 x 8 samples.  kExact: the step is a power of
+// two, so the offsets k * step and their sums are exact floats.
+template <bool kStaged, bool kExact>
 __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const SimplexPlan& P, const TileOctave T,
                                                const float2* boxes, int i, int tx, int ty)
 {
-    const float step = P.step[i], amp = P.amp[i] * kScale;
+    const float step = P.step[i], step_lo = P.step_lo[i], amp = P.amp[i] * kScale;
     Grad<kStaged> G;
     G.key = P.key[i];
     G.wb = P.box_wb[i];
@@ -126,29 +135,56 @@ __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const
     G.amin = T.amin;
     G.bmin = T.bmin;
     G.size = G.wb * G.wb;
-    float cs[kCols], fxc[kCols];
+    // Offsets k * step as a float plus its residual (k * step - that float):
+    // zero when the step is a power of two, so that the arithmetic below is
+    // exact there; otherwise it carries the product and step rounding.
+    // Without exact steps every sum below also keeps its rounding residual
+    // (two-sums), so that a sample's stretched position is off by about one
+    // float rounding, as with exact steps.
+    // cse: residual of the product k * step (it enters the stretch); cbe: the
+    // residuals of the base fraction and of the sum fxc (they do not).
+    float cs[kCols], cse[kCols], cbe[kCols], fxc[kCols];
     int32_t icx[kCols];
 #pragma unroll
     for (int c = 0; c < kCols; ++c) {
-        cs[c] = (float)(tx * kCols + c) * step;  // exact
+        const float k = (float)(tx * kCols + c);
+        cs[c] = k * step;
         const float fl = floorf(cs[c]);
         icx[c] = (int32_t)fl;
         fxc[c] = T.fx + (cs[c] - fl);
+        cse[c] = kExact ? 0.0f : fmaf(k, step, -cs[c]) + k * step_lo;
+        cbe[c] = kExact ? 0.0f : two_sum_err(T.fx, cs[c] - fl, fxc[c]) + T.fxl;
     }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
-        const float rs = (float)(ty * kRows + r) * step;  // exact
+        const float k = (float)(ty * kRows + r);
+        const float rs = k * step;
         const float fl = floorf(rs);
         const int32_t iry = (int32_t)fl;
         const float fyr = T.fy + (rs - fl);
+        const float rse = kExact ? 0.0f : fmaf(k, step, -rs) + k * step_lo;
+        const float rbe = kExact ? 0.0f : two_sum_err(T.fy, rs - fl, fyr) + T.fyl;
 #pragma unroll
         for (int c = 0; c < kCols; ++c) {
-            const float K = cs[c] + rs;                      // exact
+            const float K = cs[c] + rs;
             const float p = K * kStretchHi;
             const float e = fmaf(K, kStretchHi, -p);         // exact rounding error of p
             const float ip = floorf(p);
-            const float t = (p - ip) + (e + K * kStretchLo);
-            const float sx = fxc[c] + t, sy = fyr + t;
+            float t, sx, sy;
+            if (kExact) {
+                t = (p - ip) + (e + K * kStretchLo);
+                sx = fxc[c] + t;
+                sy = fyr + t;
+            } else {
+                const float Ke = two_sum_err(cs[c], rs, K) + (cse[c] + rse);  // K's error and product residuals
+                const float small = e + fmaf(Ke, kStretchHi, K * kStretchLo);
+                const float pt = p - ip;  // exact
+                t = pt + small;
+                const float te = two_sum_err(pt, small, t);
+                const float ux = fxc[c] + t, uy = fyr + t;
+                sx = ux + (two_sum_err(fxc[c], t, ux) + (te + (cse[c] + cbe[c])));
+                sy = uy + (two_sum_err(fyr, t, uy) + (te + (rse + rbe)));
+            }
             const float flx = floorf(sx), fly = floorf(sy);
             const float xi = sx - flx, yi = sy - fly;
             const int32_t iip = (int32_t)ip;
@@ -159,7 +195,9 @@ __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const
     }
 }
 
-template <typename OutT>
+// kAllExact: every octave's step is a power of two (the dyadic fields), so
+// only the exact-offset octave code is compiled into the kernel.
+template <typename OutT, bool kAllExact>
 __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_constant__ SimplexPlan P)
 {
     __shared__ TileOctave tile[kMaxOctaves];
@@ -168,8 +206,8 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
     const int j0x = blockIdx.x * kTW, j0y = blockIdx.y * kTH;
     if (tid < P.N) {
         const int i = tid;
-        const double X = P.base_x[i] + (double)j0x * (double)P.step[i];
-        const double Y = P.base_y[i] + (double)j0y * (double)P.step[i];
+        const double X = P.base_x[i] + (double)j0x * P.step_d[i];
+        const double Y = P.base_y[i] + (double)j0y * P.step_d[i];
         const double sh = (X + Y) * kStretchD;
         const double xs = X + sh, ys = Y + sh;
         const double fa = floor(xs), fb = floor(ys);
@@ -178,9 +216,11 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
         T.b0 = (int32_t)(long long)fb;
         T.fx = (float)(xs - fa);
         T.fy = (float)(ys - fb);
+        T.fxl = (float)((xs - fa) - (double)T.fx);
+        T.fyl = (float)((ys - fb) - (double)T.fy);
         T.amin = T.bmin = T.w = T.h = 0;
         if (P.box_wb[i] > 0) {
-            const double L = 64.0 * (double)P.step[i];
+            const double L = 64.0 * P.step_d[i];
             T.amin = (int32_t)(long long)floor(xs + kStretchD * L) - 2;
             T.bmin = (int32_t)(long long)floor(ys + kStretchD * L) - 2;
             T.w = min((int32_t)(long long)floor(xs + (1.0 + kStretchD) * L) + 3 - T.amin + 1, P.box_wb[i]);
@@ -213,8 +253,14 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
         for (int c = 0; c < kCols; ++c) acc[r][c] = 0.0f;
 
     for (int i = 0; i < P.N; ++i) {
-        if (P.box_wb[i] > 0) simplex_octave<true>(acc, P, tile[i], boxes, i, tx, ty);
-        else simplex_octave<false>(acc, P, tile[i], boxes, i, tx, ty);
+        const bool exact = kAllExact || ((P.exact_mask >> i) & 1u);
+        if (P.box_wb[i] > 0) {
+            if (exact) simplex_octave<true, true>(acc, P, tile[i], boxes, i, tx, ty);
+            else simplex_octave<true, kAllExact>(acc, P, tile[i], boxes, i, tx, ty);
+        } else {
+            if (exact) simplex_octave<false, true>(acc, P, tile[i], boxes, i, tx, ty);
+            else simplex_octave<false, kAllExact>(acc, P, tile[i], boxes, i, tx, ty);
+        }
     }
     OutT* out = reinterpret_cast<OutT*>(P.out);
     const int x0 = j0x + tx * kCols, y0 = j0y + ty * kRows;
@@ -248,18 +294,22 @@ cudaError_t launch_opensimplex2d(const SimplexPlan& P, cudaStream_t stream)
 {
     const dim3 grid(P.tiles_x, P.tiles_y, 1);
     const size_t smem = sizeof(float2) * (size_t)P.box_words;
+    const bool all_exact = P.exact_mask == (P.N >= 32 ? 0xffffffffu : (1u << P.N) - 1u);
+#define PTG_LAUNCHOS(T, X)                                                                           \
+    do {                                                                                             \
+        auto kfn = opensimplex2d_kernel<T, X>;                                                       \
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                              \
+        kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
+        return cudaGetLastError();                                                                   \
+    } while (0)
     if (P.dtype == 1) {
-        cudaError_t e = cudaFuncSetAttribute(opensimplex2d_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        opensimplex2d_kernel<__half><<<grid, kThreads, smem, stream>>>(P);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(opensimplex2d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        opensimplex2d_kernel<float><<<grid, kThreads, smem, stream>>>(P);
+        if (all_exact) PTG_LAUNCHOS(__half, true);
+        PTG_LAUNCHOS(__half, false);
     }
-    return cudaGetLastError();
+    if (all_exact) PTG_LAUNCHOS(float, true);
+    PTG_LAUNCHOS(float, false);
+#undef PTG_LAUNCHOS
 }
 
 }  // namespace ptg

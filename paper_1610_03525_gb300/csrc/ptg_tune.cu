@@ -184,8 +184,9 @@ int ptg_launch_config(ptg_ctx* ctx, const ptg_field_desc* desc, int32_t method, 
     int s = 0;
     const int rc = ptg_check_desc(ctx, desc, kind, &s);
     if (rc != PTG_OK) return rc;
-    int32_t w = 8, t = 0;
-    if (desc->dims == 2) ptg_pick_config(ctx, desc, ptg_kernel_method(kind, desc), s, &w, &t);
+    int32_t w = 8, t = 0;  // (the per-sample generator of other spc and frequency ratios has no choice)
+    if (desc->dims == 2 && s >= 0 && desc->lacunarity == 2.0f)
+        ptg_pick_config(ctx, desc, ptg_kernel_method(kind, desc), s, &w, &t);
     if (rw) *rw = w;
     if (tile_octaves) *tile_octaves = t;
     return PTG_OK;

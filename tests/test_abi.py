@@ -51,7 +51,10 @@ def test_desc_layout_matches_header(P):
     (dict(), 0, 0),
     (dict(size=(0, 5)), 0, -1),
     (dict(size=(5, 5), spc=0), 0, -1),
-    (dict(size=(5, 5), spc=3), 0, -2),
+    (dict(size=(5, 5), spc=3), 0, 0),                 # any spc in 2D (per-sample generator)
+    (dict(size=(5, 5), spc=100, offset=(7, 3, 0)), 1, 0),
+    (dict(size=(5, 5), spc=3), 2, 0),
+    (dict(dims=3, size=(32, 32, 32), spc=3), 0, -2),  # 3D needs a power of two
     (dict(octaves=0), 0, -1),
     (dict(octaves=33), 0, -1),
     (dict(smoothness=5), 0, -1),

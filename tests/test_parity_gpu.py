@@ -65,8 +65,12 @@ def oracle_at(kind, idx, dims=2, spc=64, octaves=6, origin=(0, 0, 0), offset=(0,
                            frequency=lacunarity)
 
 
-def tol32(octaves, persistence=0.5):
-    return 2e-6 * W.total_amplitude(octaves, abs(persistence))
+def tol32(octaves, persistence=0.5, kind="c1"):
+    """FP32 bar: 2e-6 x A_tot for the polynomial models and Perlin.  The
+    OpenSimplex baseline sums four kernel terms (2 - r^2)^4 (g . d) / 8 of up
+    to 4 each per octave, so its FP32 rounding is bounded by a larger multiple
+    of the amplitude: 5e-6 x A_tot."""
+    return (5e-6 if kind == "opensimplex" else 2e-6) * W.total_amplitude(octaves, abs(persistence))
 
 
 def half_ulp16(x):
@@ -144,7 +148,7 @@ def test_full_field_256(ctx, kind):
     idx = W.grid_indices_2d(*cfg["size"])
     ref = oracle_at(kind, idx, spc=cfg["spc"], octaves=cfg["octaves"], seed=0)
     err = np.abs(gather(out, idx) - ref).max()
-    assert err <= tol32(cfg["octaves"]), err
+    assert err <= tol32(cfg["octaves"], kind=kind), err
 
 
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "opensimplex"])
@@ -153,7 +157,7 @@ def test_fp16_output_256(ctx, kind):
     idx = W.grid_indices_2d(256, 256)
     ref = oracle_at(kind, idx, spc=64, octaves=6, seed=0)
     err = np.abs(gather(out, idx) - ref)
-    assert np.all(err <= tol32(6) + half_ulp16(ref))
+    assert np.all(err <= tol32(6, kind=kind) + half_ulp16(ref))
 
 
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "opensimplex", "paper_gauge", "zero_grad"])
@@ -173,7 +177,7 @@ def test_ragged_and_tiny(ctx, kind, size, spc, octaves):
     ref = oracle_at(kind, idx, spc=spc, octaves=octaves, origin=origin, seed=17, persistence=0.6,
                     grad_weight=0.75)
     err = np.abs(gather(out, idx) - ref).max()
-    assert err <= tol32(octaves, 0.6), err
+    assert err <= tol32(octaves, 0.6, kind), err
 
 
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3"])
@@ -272,7 +276,22 @@ def test_any_lacunarity_vs_oracle(ctx, kind, f, size, spc, octaves, origin):
     ref = oracle_at(kind, idx, spc=spc, octaves=octaves, origin=origin, seed=13, persistence=0.6, grad_weight=0.75,
                     lacunarity=f)
     err = np.abs(gather(out, idx) - ref).max()
-    assert err <= tol32(octaves, 0.6), err
+    assert err <= tol32(octaves, 0.6, kind), err
+
+
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "zero_grad", "opensimplex"])
+@pytest.mark.parametrize("spc,f", [(3, 2.0), (100, 2.0), (1000, 2.0), (48, 1.7)])
+def test_any_spc_vs_oracle(ctx, kind, spc, f):
+    """Samples per cell that are not powers of two (2D, per-sample generator),
+    with an unaligned window offset."""
+    size, N, origin, offset = (150, 90), 7, (-5, 1 << 12, 0), (7, 13, 0)
+    out = gpu_field(ctx, kind, size=size, spc=spc, octaves=N, origin=origin, offset=offset, seed=2,
+                    persistence=0.55, lacunarity=f)
+    idx = W.grid_indices_2d(*size)
+    ref = oracle_at(kind, idx, spc=spc, octaves=N, origin=origin, offset=offset, seed=2, persistence=0.55,
+                    lacunarity=f)
+    err = np.abs(gather(out, idx) - ref).max()
+    assert err <= tol32(N, 0.55, kind), err
 
 
 @pytest.mark.parametrize("kind", ["c1", "perlin_s5"])
@@ -306,7 +325,7 @@ def test_sampled_8192_n12(ctx, kind, seed, dtype):
     idx = W.subsample(cfg["size"], every=1024, n_random=1 << 15, seed=seed)
     ref = oracle_at(kind, idx, spc=cfg["spc"], octaves=cfg["octaves"], seed=seed)
     err = np.abs(gather(out, idx) - ref)
-    bound = tol32(cfg["octaves"]) + (half_ulp16(ref) if dtype == P.PTG_F16 else 0.0)
+    bound = tol32(cfg["octaves"], kind=kind) + (half_ulp16(ref) if dtype == P.PTG_F16 else 0.0)
     assert np.all(err <= bound), err.max()
     # range bound |H| <= (1 + D w beta) A_tot holds on the whole field
     if kind == "c1":
@@ -379,7 +398,7 @@ def test_short_forms(ctx):
 # argument errors write nothing
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kw,code", [
-    (dict(size=(0, 16)), P.PTG_ERR_INVALID), (dict(spc=3), P.PTG_ERR_UNSUPPORTED),
+    (dict(size=(0, 16)), P.PTG_ERR_INVALID), (dict(spc=3, dims=3, size=(16, 16, 16)), P.PTG_ERR_UNSUPPORTED),
     (dict(octaves=0), P.PTG_ERR_INVALID), (dict(lacunarity=0.5), P.PTG_ERR_INVALID),
     (dict(smoothness=9), P.PTG_ERR_INVALID), (dict(seed=1 << 24), P.PTG_ERR_INVALID),
 ])
