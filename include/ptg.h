@@ -55,7 +55,7 @@ typedef enum {
     PTG_OK = 0,
     PTG_PENDING = 1,
     PTG_ERR_INVALID = -1,     /* bad argument                                  */
-    PTG_ERR_UNSUPPORTED = -2, /* valid but not supported (e.g. 3D lacunarity != 2)*/
+    PTG_ERR_UNSUPPORTED = -2, /* valid but not supported (e.g. 3D OpenSimplex)  */
     PTG_ERR_NOMEM = -3,       /* an allocation failed                          */
     PTG_ERR_BUDGET = -4,      /* request can never fit the HBM budget          */
     PTG_ERR_CUDA = -5,        /* a CUDA call failed                            */
@@ -110,9 +110,9 @@ typedef struct {
     uint32_t struct_size; /* sizeof(ptg_field_desc)                            */
     int32_t dims;         /* 2 or 3                                            */
     int64_t size[3];      /* samples per axis (x, y, z), each in [1, 2^30]; unused = 1 */
-    int64_t spc;          /* samples per base cell, in [1, 2^30]: a power of
-                             two in 3D; in 2D any other value runs the
-                             per-sample generator (see lacunarity)          */
+    int64_t spc;          /* samples per base cell, in [1, 2^30]; a value
+                             that is not a power of two runs the per-sample
+                             generators (see lacunarity)                    */
     int64_t origin[3];    /* base-lattice cell of the window (wraps mod 2^32)  */
     int64_t offset[3];    /* sample offset of the window, offset + size <=
                              2^31; for the fused generators (power-of-two spc,
@@ -123,8 +123,9 @@ typedef struct {
     float persistence;    /* amplitude ratio between octaves (0.5 typical)     */
     float lacunarity;     /* frequency ratio f between octaves, in [1, 16]
                              (Sec. 4: frequency f^i at octave i).  f = 2 runs
-                             the fused generators; any other f (2D only) runs
-                             a per-sample generator in which the lattice
+                             the fused generators; any other f runs a
+                             per-sample generator (2D, or 3D C1/C2/Perlin)
+                             in which the lattice
                              coordinate (origin + (offset + j)/spc) f^i is
                              formed per tile in FP64 and must stay below 2^30
                              (else PTG_ERR_UNSUPPORTED); thread-shape and

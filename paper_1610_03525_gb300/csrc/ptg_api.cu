@@ -57,8 +57,6 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "the OpenSimplex baseline is 2D");
     const int s = log2_exact(d->spc);
     if (d->spc <= 0 || d->spc > (int64_t{1} << 30)) return ptg_fail(ctx, PTG_ERR_INVALID, "spc out of [1, 2^30]");
-    if (s < 0 && d->dims != 2)
-        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "spc (samples per cell) must be a power of two in 3D");
     // the fused generators need tiles aligned to cells; the per-sample ones
     // (OpenSimplex, and 2D fields with any other spc or frequency ratio) do not
     const bool fused = kind != kKindSimplex && s >= 0 && d->lacunarity == 2.0f;
@@ -97,11 +95,10 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
         return ptg_fail(ctx, PTG_ERR_INVALID, "persistence and grad_weight must be finite");
     if (!std::isfinite(d->lacunarity) || d->lacunarity < 1.0f || d->lacunarity > 16.0f)
         return ptg_fail(ctx, PTG_ERR_INVALID, "lacunarity (frequency ratio) must be in [1, 16]");
-    if (d->lacunarity != 2.0f) {
-        if (d->dims != 2) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "a lacunarity other than 2 is supported in 2D");
-        // every octave's lattice coordinates must stay below 2^30 in magnitude
+    if (d->lacunarity != 2.0f || s < 0) {
+        // per-sample generators: every octave's lattice coordinates must stay below 2^30 in magnitude
         const double fN = std::pow((double)d->lacunarity, (double)(d->octaves - 1));
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < d->dims; ++k) {
             const double e = std::fabs((double)d->origin[k]) + (double)(d->offset[k] + d->size[k]) / (double)d->spc;
             if (e * fN >= std::ldexp(1.0, 30))
                 return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "lattice coordinates (origin + extent) * f^(N-1) exceed 2^30");
@@ -305,6 +302,58 @@ int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, voi
     return PTG_OK;
 }
 
+// The same for a 3D field (or a band of planes of one).
+int ptg_make_general3_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int64_t band_start,
+                           int64_t band_len, General3Plan* P)
+{
+    memset(P, 0, sizeof *P);
+    P->out = out;
+    P->W = (int32_t)d->size[0];
+    P->H = (int32_t)d->size[1];
+    P->D = (int32_t)band_len;
+    P->dtype = d->dtype;
+    P->N = d->octaves;
+    P->method = method;
+    P->tiles_x = (P->W + kTile3dX - 1) / kTile3dX;
+    P->tiles_y = (P->H + kTile3dY - 1) / kTile3dY;
+    P->tiles_z = (P->D + kTile3dZ - 1) / kTile3dZ;
+    if (P->tiles_y > 65535 || P->tiles_z > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall");
+    const int esz = d->dtype == PTG_F16 ? 2 : 4;
+    P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
+    const double spc = (double)d->spc, f = (double)d->lacunarity;
+    const double p = (double)d->persistence, w = (double)d->grad_weight;
+    const int ext[3] = {kTile3dX - 1, kTile3dY - 1, kTile3dZ - 1};
+    double amp = 1.0;
+    int box = 0;
+    for (int i = 0; i < d->octaves; ++i) {
+        const double fi = f == 2.0 ? std::ldexp(1.0, i) : std::pow(f, (double)i), scale = fi / spc;
+        for (int a = 0; a < 3; ++a)
+            P->base[a][i] = (double)d->origin[a] * fi + (double)(d->offset[a] + (a == 2 ? band_start : 0)) * scale;
+        P->scale[i] = scale;
+        P->scale_hi[i] = (float)scale;
+        P->scale_lo[i] = (float)(scale - (double)P->scale_hi[i]);
+        P->amp[i] = (float)amp;
+        P->ampw[i] = (float)(amp * w);
+        P->key[i] = (d->seed << 8) | (uint32_t)i;
+        if (scale <= 0.5) {  // one cell before the base cell, ext * scale + 1 after it, one for rounding, +1 corner
+            int bw[3];
+            for (int a = 0; a < 3; ++a) bw[a] = (int)std::floor(ext[a] * scale) + 5;
+            const int n = bw[0] * bw[1] * bw[2];
+            if ((size_t)(box + n) * sizeof(float4) <= (size_t)96 * 1024) {
+                P->box_off[i] = box;
+                for (int a = 0; a < 3; ++a) P->box_w[a][i] = bw[a];
+                P->box_magic[0][i] = (uint32_t)(((uint64_t{1} << 32) + (uint64_t)bw[0] - 1) / (uint64_t)bw[0]);
+                const uint64_t wxy = (uint64_t)bw[0] * (uint64_t)bw[1];
+                P->box_magic[1][i] = (uint32_t)(((uint64_t{1} << 32) + wxy - 1) / wxy);
+                box += n;
+            }
+        }
+        amp *= p;
+    }
+    P->box_words = box;
+    return PTG_OK;
+}
+
 int ptg_kernel_method(int kind, const ptg_field_desc* d)
 {
     if (kind == kKindPerlin) return (d->variant & 0xff) == PTG_PERLIN_S3 ? kPerlinS3 : kPerlinS5;
@@ -325,6 +374,11 @@ int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void
         int rc = ptg_make_simplex_plan(ctx, d, out, s, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
         e = launch_opensimplex2d(P, st);
+    } else if ((d->lacunarity != 2.0f || s < 0) && d->dims == 3) {  // any frequency ratio or spc, 3D
+        General3Plan P;
+        int rc = ptg_make_general3_plan(ctx, d, ptg_kernel_method(kind, d), out, band_start, band_len, &P);
+        if (rc != PTG_OK) return rc;
+        e = launch_general3d(P, st);
     } else if (d->lacunarity != 2.0f || s < 0) {  // any frequency ratio or spc: per-sample generator
         GeneralPlan P;
         int rc = ptg_make_general_plan(ctx, d, ptg_kernel_method(kind, d), out, s, band_start, band_len, &P);
@@ -468,6 +522,9 @@ int ptg_validate(const ptg_field_desc* d, int32_t method, char* msg, int32_t msg
         if (kind == kKindSimplex) {
             SimplexPlan P;
             rc = ptg_make_simplex_plan(&scratch, d, nullptr, s, 0, slow, &P);
+        } else if ((d->lacunarity != 2.0f || s < 0) && d->dims == 3) {
+            General3Plan P;
+            rc = ptg_make_general3_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, 0, slow, &P);
         } else if (d->lacunarity != 2.0f || s < 0) {
             GeneralPlan P;
             rc = ptg_make_general_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, s, 0, slow, &P);

@@ -216,6 +216,23 @@ __device__ __forceinline__ float axis_t(uint32_t j, int i, int s)
     return (float)r * __uint_as_float((uint32_t)(127 - k) << 23);  // r * 2^-k, exact
 }
 
+// Per-sample generators (any spc or frequency ratio): offset k samples from
+// a tile's first sample, in cells of the octave.  fb = the first sample's
+// position in its cell, scale = hi + lo cells per sample; returns the whole
+// cells n past the first sample's cell and the position t in [0, 1).  k * hi
+// keeps its exact rounding error (an FMA), so t is good to about 2^-23.
+__device__ __forceinline__ void lattice_split(float k, float shi, float slo, float fb, int& n, float& t)
+{
+    const float p = k * shi;
+    const float e = fmaf(k, shi, -p);  // k * shi - p, exact
+    const float pf = floorf(p);
+    float w = (p - pf) + fb;           // p - pf is exact
+    w += fmaf(k, slo, e);
+    const float wf = floorf(w);
+    t = w - wf;
+    n = __float2int_rn(pf) + __float2int_rn(wf);
+}
+
 // Slot of corner column cx inside a staged 2D corner row: one pad slot after
 // every 8 corners, so that the 8 lanes of a quarter warp that read corners 1,
 // 2 or 4 apart (cells of 8, 4 or 2 samples) hit 8 different 16-byte bank

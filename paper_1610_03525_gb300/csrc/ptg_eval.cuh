@@ -218,6 +218,17 @@ __device__ __forceinline__ float eval_row(const Row& r, float Sx, float B0x, flo
 }
 
 
+// 3D cells: reduction along z of a corner pair (lo at z = 0, hi at z = 1;
+// each (v, f, g, e) with e the z gradient) at z-basis zb: the 2D corner
+// (W, F, G) of the thread's plane,
+//   W = v0 + S(z) (v1 - v0) + B0(z) e0 + B1(z) e1,  F = f0 + S(z) (f1 - f0),
+//   G = g0 + S(z) (g1 - g0).
+__device__ __forceinline__ float4 zreduce(float4 lo, float4 hi, float4 zb)
+{
+    return make_float4(fmaf(zb.z, hi.w, fmaf(zb.y, lo.w, fmaf(zb.x, hi.x - lo.x, lo.x))),
+                       fmaf(zb.x, hi.y - lo.y, lo.y), fmaf(zb.x, hi.z - lo.z, lo.z), 0.0f);
+}
+
 // Per-method cell model: the row collapse at a y-basis entry, the row at
 // t_y = 0, and the evaluation of a collapsed row at an x-basis entry.
 template <int METHOD>

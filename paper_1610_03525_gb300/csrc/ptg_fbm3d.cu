@@ -107,9 +107,7 @@ __device__ __forceinline__ Cell zcell(const float4* __restrict__ cg, const OctPl
 #pragma unroll
     for (int q = 0; q < 4; ++q) {  // q = a + 2 b
         const float4* p = p0 + (q >> 1) * op.rowlen + ((q & 1) ? s1 : s0);
-        const float4 lo = p[0], hi = p[plane];
-        r[q] = make_float4(fmaf(zb.z, hi.w, fmaf(zb.y, lo.w, fmaf(zb.x, hi.x - lo.x, lo.x))),
-                           fmaf(zb.x, hi.y - lo.y, lo.y), fmaf(zb.x, hi.z - lo.z, lo.z), 0.0f);
+        r[q] = zreduce(p[0], p[plane], zb);
     }
     Cell c;
     c.c00 = r[0];

@@ -27,20 +27,6 @@ namespace {
 constexpr int kTW = kTile2dX, kTH = kTile2dY, kThreads = 128;
 constexpr int kCols = 8, kRows = 4;  // per thread: 8 consecutive columns in 4 rows
 
-// Offset k (samples, 0..63) from the tile's first sample, in cells of the
-// octave: whole cells n past the tile's base cell, and the position t.
-__device__ __forceinline__ void lattice_split(float k, float shi, float slo, float fb, int& n, float& t)
-{
-    const float p = k * shi;
-    const float e = fmaf(k, shi, -p);  // k * shi - p, exact
-    const float pf = floorf(p);
-    float w = (p - pf) + fb;           // p - pf is exact
-    w += fmaf(k, slo, e);
-    const float wf = floorf(w);
-    t = w - wf;
-    n = __float2int_rn(pf) + __float2int_rn(wf);
-}
-
 // The four corners of cell (cx, cy) hashed in place (octaves whose cells are
 // too small to stage per tile).
 template <int METHOD>

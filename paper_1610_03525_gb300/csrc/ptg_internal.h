@@ -76,6 +76,8 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
                           int64_t band_len, ptg::SimplexPlan* P);
 int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int s, int64_t band_start,
                           int64_t band_len, ptg::GeneralPlan* P);
+int ptg_make_general3_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int64_t band_start,
+                           int64_t band_len, ptg::General3Plan* P);
 int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void* out, int64_t band_start,
                     int64_t band_len, cudaStream_t st);
 int ptg_kernel_method(int kind, const ptg_field_desc* d);

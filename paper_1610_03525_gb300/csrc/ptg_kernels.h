@@ -64,6 +64,24 @@ struct GeneralPlan {
 };
 cudaError_t launch_general2d(const GeneralPlan& P, cudaStream_t stream);
 
+// The same in 3D (C1, C2, Perlin): 32 x 16 x 8 tiles, corner boxes of
+// box_w[0..2][i] corners along x, y, z (0 = hash each sample's 8 corners).
+struct General3Plan {
+    void* out;
+    int32_t W, H, D, dtype, N, vec_ok, tiles_x, tiles_y, tiles_z, method;
+    int32_t box_words;  // float4 words of shared memory for all staged corner boxes
+    int32_t pad[1];
+    double base[3][kMaxOctaves];  // lattice coordinate of output sample (0, 0, 0) at octave i
+    double scale[kMaxOctaves];
+    float scale_hi[kMaxOctaves], scale_lo[kMaxOctaves];
+    float amp[kMaxOctaves], ampw[kMaxOctaves];
+    uint32_t key[kMaxOctaves];
+    int32_t box_off[kMaxOctaves];
+    int32_t box_w[3][kMaxOctaves];
+    uint32_t box_magic[2][kMaxOctaves];  // ceil(2^32 / wx), ceil(2^32 / (wx wy))
+};
+cudaError_t launch_general3d(const General3Plan& P, cudaStream_t stream);
+
 // Test hooks.
 cudaError_t launch_debug_hash(int dims, const uint32_t* keys, long long n, uint32_t* out, cudaStream_t stream);
 cudaError_t launch_debug_axis(long long origin, int s, int octave, const long long* j, long long n,

@@ -54,7 +54,8 @@ def test_desc_layout_matches_header(P):
     (dict(size=(5, 5), spc=3), 0, 0),                 # any spc in 2D (per-sample generator)
     (dict(size=(5, 5), spc=100, offset=(7, 3, 0)), 1, 0),
     (dict(size=(5, 5), spc=3), 2, 0),
-    (dict(dims=3, size=(32, 32, 32), spc=3), 0, -2),  # 3D needs a power of two
+    (dict(dims=3, size=(32, 32, 32), spc=3), 0, 0),   # any spc in 3D too
+    (dict(dims=3, size=(32, 32, 32), spc=3), 1, 0),
     (dict(octaves=0), 0, -1),
     (dict(octaves=33), 0, -1),
     (dict(smoothness=5), 0, -1),
@@ -62,7 +63,8 @@ def test_desc_layout_matches_header(P):
     (dict(smoothness=4, dims=3, size=(32, 32, 32)), 0, -2),
     (dict(lacunarity=3.0), 0, 0),                     # any frequency ratio in 2D
     (dict(lacunarity=1.5), 2, 0),
-    (dict(lacunarity=3.0, dims=3, size=(32, 32, 32)), 0, -2),
+    (dict(lacunarity=3.0, dims=3, size=(32, 32, 32)), 0, 0),   # 3D per-sample generator
+    (dict(lacunarity=3.0, dims=3, size=(32, 32, 32), smoothness=4), 0, -2),  # zero-gradient is 2D
     (dict(lacunarity=0.5), 0, -1),
     (dict(lacunarity=17.0), 0, -1),
     (dict(lacunarity=3.0, octaves=20, spc=64, size=(64, 64)), 0, -2),  # 3^19 lattice units

@@ -294,6 +294,22 @@ def test_any_spc_vs_oracle(ctx, kind, spc, f):
     assert err <= tol32(N, 0.55, kind), err
 
 
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "perlin_s3"])
+@pytest.mark.parametrize("spc,f,dtype", [(16, 1.7, P.PTG_F32), (12, 2.0, P.PTG_F32), (128, 2.6, P.PTG_F16),
+                                         (5, 1.3, P.PTG_F32)])
+def test_3d_any_spc_and_lacunarity_vs_oracle(ctx, kind, spc, f, dtype):
+    """3D per-sample generator: cells down to a fraction of a sample, world offset,
+    unaligned window offset."""
+    size, N, origin, offset = (45, 23, 19), 6, (1 << 12, -3, 77), (5, 9, 3)
+    out = gpu_field(ctx, kind, dims=3, size=size, spc=spc, octaves=N, origin=origin, offset=offset, seed=6,
+                    lacunarity=f, dtype=dtype)
+    idx = W.grid_indices_3d(*size)
+    ref = oracle_at(kind, idx, dims=3, spc=spc, octaves=N, origin=origin, offset=offset, seed=6, lacunarity=f)
+    err = np.abs(gather(out, idx) - ref)
+    bound = tol32(N, kind=kind) + (half_ulp16(ref) if dtype == P.PTG_F16 else 0.0)
+    assert np.all(err <= bound), err.max()
+
+
 @pytest.mark.parametrize("kind", ["c1", "perlin_s5"])
 def test_any_lacunarity_fp16_host_and_chunks(ctx, kind):
     f, size, spc, N = 1.75, (1000, 777), 128, 10
@@ -398,7 +414,7 @@ def test_short_forms(ctx):
 # argument errors write nothing
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kw,code", [
-    (dict(size=(0, 16)), P.PTG_ERR_INVALID), (dict(spc=3, dims=3, size=(16, 16, 16)), P.PTG_ERR_UNSUPPORTED),
+    (dict(size=(0, 16)), P.PTG_ERR_INVALID), (dict(smoothness=4, dims=3, size=(16, 16, 16)), P.PTG_ERR_UNSUPPORTED),
     (dict(octaves=0), P.PTG_ERR_INVALID), (dict(lacunarity=0.5), P.PTG_ERR_INVALID),
     (dict(smoothness=9), P.PTG_ERR_INVALID), (dict(seed=1 << 24), P.PTG_ERR_INVALID),
 ])
