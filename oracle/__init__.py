@@ -85,6 +85,9 @@ def lib():
         L.ptgo_axis_freq_batch.argtypes = [ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_double,
                                            ctypes.c_int, P, P]
         L.ptgo_num_threads.restype = ctypes.c_int
+        L.ptgo_box_counts.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_float, ctypes.c_int, P]
+        L.ptgo_histogram.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_int, ctypes.c_int, P]
         _lib = L
     return _lib
 
@@ -215,3 +218,32 @@ def opensimplex_points(seed: int, octave: int, xy: np.ndarray) -> np.ndarray:
 
 def num_threads() -> int:
     return lib().ptgo_num_threads()
+
+
+def box_counts(h: np.ndarray, level: float = 0.0, levels: int = 7) -> np.ndarray:
+    """Coastline box counts for squares of 1, 2, .. 2^(levels-1) samples (Sec. 5.3)."""
+    h = np.ascontiguousarray(h, dtype=np.float32)
+    out = np.zeros(levels, np.uint64)
+    lib().ptgo_box_counts(_ptr(h), h.shape[1], h.shape[0], float(np.float32(level)), levels, _ptr(out))
+    return out
+
+
+def histogram(h: np.ndarray, lo: float, hi: float, bins: int, what: int = 0) -> np.ndarray:
+    """Height (what 0) or slope-norm (what 1) histogram over maps h[..., H, W]
+    (Sec. 5.1); bins + 2 counts (below lo, the bins, at or above hi)."""
+    h = np.ascontiguousarray(h, dtype=np.float32)
+    H, W = h.shape[-2:]
+    count = int(np.prod(h.shape[:-2])) if h.ndim > 2 else 1
+    out = np.zeros(bins + 2, np.uint64)
+    lib().ptgo_histogram(_ptr(h), W, H, count, float(np.float32(lo)), float(np.float32(hi)), bins, what, _ptr(out))
+    return out
+
+
+def box_dimension(counts, first: int = 1, last: int = None) -> float:
+    """D of Sec. 5.3: N(eps) ~ eps^(-D), the least-squares slope of log N
+    against log eps over levels first .. last (eps = 2^k)."""
+    counts = np.asarray(counts, np.float64)
+    last = len(counts) - 1 if last is None else last
+    k = np.arange(first, last + 1)
+    y = np.log2(counts[first:last + 1])
+    return float(-np.polyfit(k, y, 1)[0])

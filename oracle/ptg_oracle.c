@@ -19,7 +19,9 @@
  *   - the cell polynomial, evaluated monomial by monomial;
  *   - the fractal (fBm) octave sum of Sec. 4;
  *   - Perlin's polynomial of Sec. 3.2 and an OpenSimplex-style simplex-lattice
- *     gradient noise summed by brute force over a superset of lattice vertices.
+ *     gradient noise summed by brute force over a superset of lattice vertices;
+ *   - the map statistics of Sec. 5: coastline box counts (Sec. 5.3) and the
+ *     frequency distributions of height and slope (Sec. 5.1).
  *
  * Readings of the paper that this file depends on (the paper is silent or
  * inconsistent on them):
@@ -705,4 +707,79 @@ int ptgo_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Map statistics of Sec. 5 (the paper's quality measurements).              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Coastline box counting (Sec. 5.3, fractal dimension): squares of side
+ * eps = 2^k samples cover the map; a square counts when it holds part of the
+ * coastline, i.e. samples below `level` and samples at or above it.  Square
+ * (bx, by) covers the samples bx eps .. bx eps + eps (inclusive, clipped to
+ * the map) along x, and likewise along y, so neighbouring squares share their
+ * edge samples and a crossing between two samples is always inside one
+ * square.  There are ceil((W - 1) / eps) x ceil((H - 1) / eps) squares.
+ * counts[k] for k = 0 .. levels-1.  h: row-major [H][W].
+ */
+void ptgo_box_counts(const float* h, int64_t W, int64_t H, float level, int levels, uint64_t* counts)
+{
+    for (int k = 0; k < levels; ++k) {
+        const int64_t eps = (int64_t)1 << k;
+        const int64_t nbx = (W - 1 + eps - 1) / eps, nby = (H - 1 + eps - 1) / eps;
+        uint64_t n = 0;
+        for (int64_t by = 0; by < nby; ++by)
+            for (int64_t bx = 0; bx < nbx; ++bx) {
+                int below = 0, above = 0;
+                const int64_t x1 = bx * eps + eps < W - 1 ? bx * eps + eps : W - 1;
+                const int64_t y1 = by * eps + eps < H - 1 ? by * eps + eps : H - 1;
+                for (int64_t y = by * eps; y <= y1; ++y)
+                    for (int64_t x = bx * eps; x <= x1; ++x) {
+                        if (h[y * W + x] < level) below = 1;
+                        else above = 1;
+                    }
+                n += (uint64_t)(below && above);
+            }
+        counts[k] = n;
+    }
+}
+
+/*
+ * Frequency distribution of heights (what = 0) or of the slope norm
+ * (what = 1) over `count` maps of W x H samples ([count][H][W], Sec. 5.1:
+ * distributions of height and of the first gradient norm).  The slope at an
+ * interior sample is |(central differences in x and y) / 2| in height per
+ * sample; border samples have none.  Bins of width (hi - lo) / bins in FP32:
+ * b = floor((v - lo) * (bins / (hi - lo))), hist[0] = below lo, hist[1 + b],
+ * hist[bins + 1] = at or above hi.  hist has bins + 2 entries, accumulated.
+ */
+void ptgo_histogram(const float* h, int64_t W, int64_t H, int64_t count, float lo, float hi, int bins, int what,
+                    uint64_t* hist)
+{
+    const float scale = (float)bins / (hi - lo);
+    for (int64_t f = 0; f < count; ++f) {
+        const float* m = h + f * W * H;
+        for (int64_t y = 0; y < H; ++y)
+            for (int64_t x = 0; x < W; ++x) {
+                float v;
+                if (what == 0) {
+                    v = m[y * W + x];
+                } else {
+                    if (x == 0 || y == 0 || x == W - 1 || y == H - 1) continue;
+                    const float dx = (m[y * W + x + 1] - m[y * W + x - 1]) * 0.5f;
+                    const float dy = (m[(y + 1) * W + x] - m[(y - 1) * W + x]) * 0.5f;
+                    const float s2 = dx * dx;
+                    const float t2 = dy * dy;
+                    v = sqrtf(s2 + t2);
+                }
+                const float u = (v - lo) * scale;
+                const float fb = floorf(u);
+                int64_t b;
+                if (!(fb >= 0.0f)) b = 0;
+                else if (fb >= (float)bins) b = bins + 1;
+                else b = (int64_t)fb + 1;
+                hist[b] += 1;
+            }
+    }
 }
