@@ -272,6 +272,57 @@ def bench_batched(P, ctx, stream, torch, n_chunks=4096, reps=5):
             "speedup": ms_single / ms_batch}
 
 
+def bench_quality(P, ctx, stream, torch):
+    """The paper's map statistics on the device (Sec. 5.3, 5.1): coastline
+    fractal dimension D (level 0, box sides 2..64 samples) against the octave
+    count N for R = 1024 maps with base frequency 2 (spc 512), p = 0.5, four
+    seeds; and the height / slope-norm distributions of 100 maps of 512^2
+    (N = 8, spc 256), with the statistics kernels' times."""
+    import numpy as np
+    res = {"workload": "D: 1024^2, spc 512, p 0.5, seeds 0..3, boxes 2..64; distributions: 100 maps 512^2, N 8"}
+    m = torch.empty((1024, 1024), dtype=torch.float32, device="cuda")
+    kinds = [("c1", P.ptg_field, dict(smoothness=P.PTG_C1)),
+             ("zero_gradient", P.ptg_field, dict(smoothness=P.PTG_ZERO_GRADIENT)),
+             ("perlin_s5", P.ptg_perlin, dict(variant=P.PTG_PERLIN_S5))]
+    for name, fn, kw in kinds:
+        ds = {}
+        for N in (1, 2, 3, 4, 6, 8, 10):
+            vals = []
+            for seed in range(4):
+                d = P.make_desc(dims=2, size=(1024, 1024), spc=512, octaves=N, seed=seed, **kw)
+                fn(ctx, d, m, stream)
+                vals.append(P.box_dimension(P.ptg_box_counts(ctx, m, 0.0, 7, stream), 1, 6))
+            ds[str(N)] = round(float(np.mean(vals)), 4)
+        res[name + "_D_vs_N"] = ds
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    for _ in range(10):
+        P.ptg_box_counts(ctx, m, 0.0, 7, stream)
+    res["box_counts_ms_1024"] = (time.perf_counter() - t0) * 100.0
+    del m
+    maps = torch.empty((100, 512, 512), dtype=torch.float32, device="cuda")
+    for name, fn, kw in kinds:
+        for k in range(100):
+            d = P.make_desc(dims=2, size=(512, 512), spc=256, octaves=8, seed=k, **kw)
+            fn(ctx, d, maps[k], stream)
+        out = {}
+        for what, lo, hi, bins in [(0, -2.0, 2.0, 80), (1, 0.0, 0.1, 100)]:
+            P.ptg_histogram(ctx, maps, lo, hi, bins, what, stream=stream)  # warm-up
+            a.record(stream)
+            hist = P.ptg_histogram(ctx, maps, lo, hi, bins, what, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            h = hist.cpu().numpy().astype(np.float64)[1:-1]
+            centres = lo + (np.arange(bins) + 0.5) * (hi - lo) / bins
+            mean = float((h * centres).sum() / h.sum())
+            std = float(np.sqrt((h * (centres - mean) ** 2).sum() / h.sum()))
+            key = "height" if what == 0 else "slope"
+            out[key] = {"mean": round(mean, 5), "std": round(std, 5), "ms": round(a.elapsed_time(b), 4)}
+        res[name + "_distributions"] = out
+    del maps
+    return res
+
+
 def bench_serving(P, torch, duration_s=2.0, warmup_s=0.5, rate_hz=20000.0, budget=40 << 30, slots=256):
     """Poisson request stream through ptg_submit / ptg_poll (80% 2D 128..2048,
     20% 3D 32..256, octaves 4..12, C1/C2) under a 40 GB budget."""
@@ -535,6 +586,7 @@ def main():
             line["octave_sweep"] = bench_octave_sweep(P, ctx, stream, torch)
             line["batched"] = bench_batched(P, ctx, stream, torch)
             line["serving"] = bench_serving(P, torch, duration_s=args.serve_seconds)
+            line["quality"] = bench_quality(P, ctx, stream, torch)
 
         # end to end through the C ABI into pinned host memory
         host = torch.empty((SIZE[1], SIZE[0]), dtype=torch.float32).pin_memory()

@@ -279,6 +279,29 @@ int ptg_launch_config(ptg_ctx* ctx, const ptg_field_desc* desc, int32_t method, 
  * NULL). */
 int ptg_validate(const ptg_field_desc* desc, int32_t method, char* msg, int32_t msg_len);
 
+/* --- Map statistics (the paper's quality measurements, Sec. 5) ---------- */
+
+/* Coastline box counts for the fractal dimension (Sec. 5.3): squares of side
+ * eps = 2^k samples, k = 0 .. levels-1, cover a W x H map (device, row-major
+ * FP32); square (bx, by) holds the samples bx eps .. bx eps + eps (inclusive,
+ * clipped) along x and likewise along y, and counts when it holds samples
+ * below `level` and samples at or above it.  counts: host array of `levels`
+ * entries.  D is the slope of log counts against -log eps.  Blocks on
+ * `stream`; uses context-owned device memory of about (W-1)(H-1) 1.25 bytes
+ * (grown on demand, kept).  Returns PTG_OK, PTG_ERR_INVALID or PTG_ERR_CUDA. */
+int ptg_box_counts(ptg_ctx* ctx, const float* map, int64_t W, int64_t H, float level, int32_t levels,
+                   uint64_t* counts, void* stream);
+
+/* Frequency distribution of heights (what = 0) or of the slope norm
+ * (what = 1) over `count` maps of W x H samples (device, [count][H][W] FP32)
+ * (Sec. 5.1).  The slope at an interior sample is |central differences| / 2
+ * in height per sample; border samples have none.  Bin of a value v:
+ * floor((v - lo) * (bins / (hi - lo))) in FP32, hist[0] below lo, hist[1 + b],
+ * hist[bins + 1] at or above hi.  hist: device array of bins + 2 counters,
+ * added to (zero it first).  bins in [1, 4096].  Asynchronous on `stream`. */
+int ptg_histogram(ptg_ctx* ctx, const float* maps, int64_t W, int64_t H, int64_t count, float lo, float hi,
+                  int32_t bins, int32_t what, uint64_t* hist, void* stream);
+
 /* Text of the last error reported on this context ("" if none). */
 const char* ptg_last_error(ptg_ctx* ctx);
 

@@ -88,6 +88,8 @@ def lib():
             "ptg_cancel": ([P, U64], ctypes.c_int),
             "ptg_debug_hold": ([P, I32], ctypes.c_int),
             "ptg_autotune": ([P, I32, ctypes.c_char_p], ctypes.c_int),
+            "ptg_box_counts": ([P, P, I64, I64, F, I32, P, P], ctypes.c_int),
+            "ptg_histogram": ([P, P, I64, I64, I64, F, F, I32, I32, P, P], ctypes.c_int),
             "ptg_launch_config": ([P, P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
             "ptg_last_error": ([P], ctypes.c_char_p),
             "ptg_validate": ([P, I32, ctypes.c_char_p, I32], ctypes.c_int),
@@ -315,6 +317,39 @@ def ptg_launch_config(ctx: Context, desc: ptg_field_desc, method: int = METHOD_F
     rw, nt = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(ctx, lib().ptg_launch_config(ctx.handle, ctypes.byref(desc), method, ctypes.byref(rw), ctypes.byref(nt)))
     return rw.value, nt.value
+
+
+def ptg_box_counts(ctx: Context, field, level: float = 0.0, levels: int = 7, stream=None):
+    """Coastline box counts of a 2D FP32 device map for squares of 1 .. 2^(levels-1) samples (Sec. 5.3)."""
+    import numpy as np
+    H, W = field.shape[-2:]
+    out = np.zeros(levels, np.uint64)
+    _check(ctx, lib().ptg_box_counts(ctx.handle, _ptr(field), W, H, float(level), levels,
+                                     out.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return out
+
+
+def ptg_histogram(ctx: Context, maps, lo: float, hi: float, bins: int, what: int = 0, hist=None, stream=None):
+    """Height (what 0) or slope-norm (what 1) histogram of FP32 device maps [..., H, W] (Sec. 5.1),
+    accumulated into the device tensor hist (bins + 2 int64; created zeroed if None)."""
+    import torch
+    H, W = maps.shape[-2:]
+    count = maps.numel() // (H * W)
+    if hist is None:
+        hist = torch.zeros(bins + 2, dtype=torch.int64, device=maps.device)
+    _check(ctx, lib().ptg_histogram(ctx.handle, _ptr(maps), W, H, count, float(lo), float(hi), bins, what,
+                                    _ptr(hist), _stream(stream)))
+    return hist
+
+
+def box_dimension(counts, first: int = 1, last: int | None = None) -> float:
+    """D of Sec. 5.3 from box counts (N(eps) ~ eps^-D): the least-squares slope of
+    log2 N against -k over levels first .. last (host arithmetic on the counts)."""
+    import numpy as np
+    counts = np.asarray(counts, np.float64)
+    last = len(counts) - 1 if last is None else last
+    k = np.arange(first, last + 1)
+    return float(-np.polyfit(k, np.log2(counts[first:last + 1]), 1)[0])
 
 
 def ptg_debug_hold(ctx: Context, hold: int) -> int:

@@ -470,6 +470,7 @@ int ptg_destroy(ptg_ctx* ctx)
     cudaStreamSynchronize(ctx->stream);
     ptg_host_release(ctx);
     ptg_batch_release(ctx);
+    if (ctx->stat_buf) cudaFree(ctx->stat_buf);
     cudaStreamDestroy(ctx->stream);
     delete ctx;
     return PTG_OK;
@@ -538,6 +539,62 @@ int ptg_validate(const ptg_field_desc* d, int32_t method, char* msg, int32_t msg
         msg[msg_len - 1] = 0;
     }
     return rc;
+}
+
+int ptg_box_counts(ptg_ctx* ctx, const float* map, int64_t W, int64_t H, float level, int32_t levels,
+                   uint64_t* counts, void* stream)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+    ctx->err.clear();
+    if (!map || !counts) return ptg_fail(ctx, PTG_ERR_INVALID, "map and counts must not be NULL");
+    if (W < 2 || H < 2 || W > (int64_t{1} << 30) || H > (int64_t{1} << 30))
+        return ptg_fail(ctx, PTG_ERR_INVALID, "map size must be in [2, 2^30] per axis");
+    if (levels < 1 || levels > 31) return ptg_fail(ctx, PTG_ERR_INVALID, "levels must be in [1, 31]");
+    if (!std::isfinite(level)) return ptg_fail(ctx, PTG_ERR_INVALID, "level must be finite");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return ptg_fail(ctx, PTG_ERR_CUDA, "cudaSetDevice(%d) failed", ctx->device);
+    const size_t n0 = (size_t)(W - 1) * (size_t)(H - 1), n1 = (size_t)(W / 2) * (size_t)(H / 2);
+    const size_t off_counts = (n0 + n1 + 15) & ~size_t{15};
+    const size_t need = off_counts + 32 * sizeof(unsigned long long);
+    cudaError_t e = cudaSuccess;
+    if (ctx->stat_bytes < need) {
+        if (ctx->stat_buf) cudaFree(ctx->stat_buf);
+        ctx->stat_buf = nullptr;
+        ctx->stat_bytes = 0;
+        e = cudaMalloc(&ctx->stat_buf, need);
+        if (e != cudaSuccess) return ptg_cuda_fail(ctx, e, "cudaMalloc (box-count pyramid)");
+        ctx->stat_bytes = need;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long* dcounts = reinterpret_cast<unsigned long long*>(ctx->stat_buf + off_counts);
+    e = cudaMemsetAsync(dcounts, 0, sizeof(unsigned long long) * (size_t)levels, st);
+    if (e == cudaSuccess)
+        e = launch_box_counts(map, W, H, level, levels, ctx->stat_buf, ctx->stat_buf + n0, dcounts, ctx->num_sms, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(counts, dcounts, sizeof(unsigned long long) * (size_t)levels, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "box counts");
+}
+
+int ptg_histogram(ptg_ctx* ctx, const float* maps, int64_t W, int64_t H, int64_t count, float lo, float hi,
+                  int32_t bins, int32_t what, uint64_t* hist, void* stream)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+    ctx->err.clear();
+    if (!maps || !hist) return ptg_fail(ctx, PTG_ERR_INVALID, "maps and hist must not be NULL");
+    if (W < 1 || H < 1 || count < 1 || W > (int64_t{1} << 30) || H > (int64_t{1} << 30) ||
+        count > (int64_t{1} << 30))
+        return ptg_fail(ctx, PTG_ERR_INVALID, "bad map size or count");
+    if (bins < 1 || bins > 4096) return ptg_fail(ctx, PTG_ERR_INVALID, "bins must be in [1, 4096]");
+    if (what != 0 && what != 1) return ptg_fail(ctx, PTG_ERR_INVALID, "what must be 0 (height) or 1 (slope)");
+    if (!std::isfinite(lo) || !std::isfinite(hi) || !(lo < hi)) return ptg_fail(ctx, PTG_ERR_INVALID, "need lo < hi");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return ptg_fail(ctx, PTG_ERR_CUDA, "cudaSetDevice(%d) failed", ctx->device);
+    const float scale = (float)bins / (hi - lo);
+    const cudaError_t e = launch_histogram(maps, W, H, count, lo, scale, bins, what,
+                                           reinterpret_cast<unsigned long long*>(hist), ctx->num_sms,
+                                           (cudaStream_t)stream);
+    return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "histogram");
 }
 
 int ptg_debug_hash(ptg_ctx* ctx, int32_t dims, const uint32_t* keys, int64_t n, uint32_t* out, void* stream)

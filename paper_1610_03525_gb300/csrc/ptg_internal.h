@@ -55,6 +55,9 @@ struct ptg_ctx {
     cudaEvent_t batch_uploaded = nullptr;
     // request loop
     PtgServer* server = nullptr;
+    // map statistics (ptg_box_counts): pyramid bytes and level counters
+    uint8_t* stat_buf = nullptr;
+    size_t stat_bytes = 0;
     // 2D launch-configuration table filled by ptg_autotune, per [method
     // index][dtype][tile octaves 0..8][16..32-sample-cell octaves 0..2][finer
     // octaves follow]: run width (8 / 16) | 0x80 when the tile octaves are

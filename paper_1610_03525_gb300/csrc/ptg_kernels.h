@@ -82,6 +82,14 @@ struct General3Plan {
 };
 cudaError_t launch_general3d(const General3Plan& P, cudaStream_t stream);
 
+// Map statistics (Sec. 5): coastline box-count pyramid (buf0 >= (W-1)(H-1)
+// bytes, buf1 >= a quarter of that rounded up; counts[levels] zeroed) and the
+// height / slope histogram (hist[bins + 2] accumulated).
+cudaError_t launch_box_counts(const float* map, long long W, long long H, float level, int levels, uint8_t* buf0,
+                              uint8_t* buf1, unsigned long long* counts, int num_sms, cudaStream_t stream);
+cudaError_t launch_histogram(const float* maps, long long W, long long H, long long count, float lo, float scale,
+                             int bins, int what, unsigned long long* hist, int num_sms, cudaStream_t stream);
+
 // Test hooks.
 cudaError_t launch_debug_hash(int dims, const uint32_t* keys, long long n, uint32_t* out, cudaStream_t stream);
 cudaError_t launch_debug_axis(long long origin, int s, int octave, const long long* j, long long n,
