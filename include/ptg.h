@@ -235,7 +235,9 @@ int ptg_submit(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, uint64_t* re
 
 /* Non-blocking status of a request: *st = PTG_PENDING or its final status;
  * ts_ns (may be NULL) = submit, admit, start and end times in ns of a
- * monotonic host clock (0 where not reached yet).  Returns PTG_OK or
+ * monotonic host clock (0 where not reached yet).  End is when the request
+ * loop saw the request complete; start is end minus the device time between
+ * timing events recorded around the request's kernels (not before admit).  Returns PTG_OK or
  * PTG_ERR_INVALID (unknown id). */
 int ptg_poll(ptg_ctx* ctx, uint64_t req_id, ptg_status* st, uint64_t ts_ns[4]);
 

@@ -7,6 +7,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "ptg.h"
@@ -26,6 +28,27 @@ int log2_exact(int64_t v)
 }
 
 }  // namespace
+
+namespace ptg {
+
+cudaError_t set_kernel_smem(const void* kfn, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;  // (device, kernel) -> largest limit set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find({dev, kfn});
+    if (it != done.end() && it->second >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) done[{dev, kfn}] = smem;
+    return e;
+}
+
+}  // namespace ptg
 
 int ptg_fail(ptg_ctx* ctx, int code, const char* fmt, ...)
 {

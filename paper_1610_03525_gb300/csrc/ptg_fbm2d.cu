@@ -597,15 +597,6 @@ size_t smem_words(const FieldPlan& P)
     return xw + (size_t)ng * 64 + rbw + (size_t)P.ncorner + grid;
 }
 
-template <typename K>
-cudaError_t set_smem(K kfn, size_t smem)
-{
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    return e;
-}
-
 }  // namespace
 
 size_t fbm2d_smem_bytes(const FieldPlan& P)
@@ -629,7 +620,7 @@ cudaError_t launch_fbm2d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
 #define PTG_LAUNCH2D_RW(M, RW)                                                                       \
     do {                                                                                             \
         auto kfn = fbm2d_kernel<M, RW>;                                                              \
-        cudaError_t e = set_smem(kfn, smem);                                                         \
+        cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
         return cudaGetLastError();                                                                   \
@@ -655,7 +646,7 @@ cudaError_t launch_fbm2d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
 cudaError_t launch_fbm2d_batch(const FieldPlan* plans, const long long* tile_start, int n,
                                unsigned long long* counter, size_t smem, int blocks, cudaStream_t stream)
 {
-    cudaError_t e = set_smem(fbm2d_batch_kernel, smem);
+    cudaError_t e = set_kernel_smem((const void*)fbm2d_batch_kernel, smem);
     if (e != cudaSuccess) return e;
     fbm2d_batch_kernel<<<blocks, kThreads, smem, stream>>>(plans, tile_start, n, counter);
     return cudaGetLastError();
@@ -664,7 +655,7 @@ cudaError_t launch_fbm2d_batch(const FieldPlan* plans, const long long* tile_sta
 int fbm2d_batch_blocks_per_sm(size_t smem)
 {
     int nb = 0;
-    set_smem(fbm2d_batch_kernel, smem);
+    set_kernel_smem((const void*)fbm2d_batch_kernel, smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fbm2d_batch_kernel, kThreads, smem) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;

@@ -302,11 +302,7 @@ cudaError_t launch_fbm3d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
 #define PTG_LAUNCH3D(M, T)                                                                           \
     do {                                                                                             \
         auto kfn = fbm3d_kernel<M, T>;                                                               \
-        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                                             (int)smem);                                             \
-        if (e != cudaSuccess) return e;                                                              \
-        e = cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout,                \
-                                 cudaSharedmemCarveoutMaxShared);                                    \
+        cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
         return cudaGetLastError();                                                                   \

@@ -164,15 +164,6 @@ __global__ void __launch_bounds__(kThreads) general2d_kernel(const __grid_consta
     }
 }
 
-template <typename K>
-cudaError_t set_smem(K kfn, size_t smem)
-{
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    return e;
-}
-
 }  // namespace
 
 cudaError_t launch_general2d(const GeneralPlan& P, cudaStream_t stream)
@@ -182,7 +173,7 @@ cudaError_t launch_general2d(const GeneralPlan& P, cudaStream_t stream)
 #define PTG_LAUNCHG(M)                                                                               \
     do {                                                                                             \
         auto kfn = general2d_kernel<M>;                                                              \
-        cudaError_t e = set_smem(kfn, smem);                                                         \
+        cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
         return cudaGetLastError();                                                                   \

@@ -173,7 +173,7 @@ cudaError_t launch_general3d(const General3Plan& P, cudaStream_t stream)
 #define PTG_LAUNCHG3(M)                                                                              \
     do {                                                                                             \
         auto kfn = general3d_kernel<M>;                                                              \
-        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
         return cudaGetLastError();                                                                   \

@@ -8,6 +8,12 @@
 
 namespace ptg {
 
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes (and
+// prefer the largest shared-memory carveout) on the current device.  The
+// attribute calls are made once per kernel, device and larger size; later
+// launches skip them.
+cudaError_t set_kernel_smem(const void* kfn, size_t smem);
+
 // Tile shapes (samples) of the fused generators.
 constexpr int kTile2dX = 64, kTile2dY = 64;
 constexpr int kTile3dX = 32, kTile3dY = 16, kTile3dZ = 8;

@@ -298,7 +298,7 @@ cudaError_t launch_opensimplex2d(const SimplexPlan& P, cudaStream_t stream)
 #define PTG_LAUNCHOS(T, X)                                                                           \
     do {                                                                                             \
         auto kfn = opensimplex2d_kernel<T, X>;                                                       \
-        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
         return cudaGetLastError();                                                                   \

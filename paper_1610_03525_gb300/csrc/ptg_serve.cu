@@ -6,10 +6,13 @@
 // within the context's HBM budget; it is then enqueued on that slot's own
 // stream, so requests admitted while others run overlap on the device
 // (continuous batching: slots and budget free up as requests finish, and the
-// queue advances at every call into the loop).  Timestamps: submit and admit
-// are taken on the host; start and end by host functions enqueued around the
-// kernel on the slot's stream.  There is no background thread and no device
-// spin: progress is made inside ptg_submit / ptg_poll / ptg_wait.
+// queue advances at every call into the loop).  Timestamps: submit, admit and
+// end are taken on the host (end = when the loop sees the request's completion
+// event); start = end minus the device time between the two timing events
+// recorded around the request's kernels.  Nothing but the kernels and the two
+// events enters the slot's stream (no host callbacks, which would stall it).
+// There is no background thread and no device spin: progress is made inside
+// ptg_submit / ptg_poll / ptg_wait.
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -40,11 +43,7 @@ struct Request {
     uint64_t bytes = 0;
     int status = PTG_PENDING;
     uint64_t ts[4] = {0, 0, 0, 0};
-    std::atomic<uint64_t> t_start{0}, t_end{0};
 };
-
-void CUDART_CB on_start(void* p) { static_cast<Request*>(p)->t_start.store(now_ns()); }
-void CUDART_CB on_end(void* p) { static_cast<Request*>(p)->t_end.store(now_ns()); }
 
 // Test hook: blocks a slot's stream on the host (not on the device) until
 // released or kHoldLimitNs passes, to simulate a stalled device.
@@ -66,6 +65,7 @@ struct PtgServer {
     std::unordered_map<uint64_t, Request*> reqs;
     Request* running[kSlots] = {};
     cudaStream_t streams[kSlots] = {};
+    cudaEvent_t begin[kSlots] = {};  // timing events around each slot's current request
     cudaEvent_t done[kSlots] = {};
     uint64_t admitted = 0;
     uint64_t next_id = 1;
@@ -82,10 +82,11 @@ PtgServer* server(ptg_ctx* ctx)
     if (!S) return nullptr;
     for (int k = 0; k < kSlots; ++k) {
         if (cudaStreamCreateWithFlags(&S->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&S->done[k], cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreate(&S->begin[k]) != cudaSuccess || cudaEventCreate(&S->done[k]) != cudaSuccess) {
             cudaGetLastError();
             for (int j = 0; j <= k; ++j) {
                 if (S->streams[j]) cudaStreamDestroy(S->streams[j]);
+                if (S->begin[j]) cudaEventDestroy(S->begin[j]);
                 if (S->done[j]) cudaEventDestroy(S->done[j]);
             }
             delete S;
@@ -100,9 +101,14 @@ void finish(PtgServer* S, int slot, int status)
 {
     Request* r = S->running[slot];
     r->status = status;
-    r->ts[2] = r->t_start.load();
-    r->ts[3] = r->t_end.load();
-    if (!r->ts[3]) r->ts[3] = now_ns();
+    r->ts[3] = now_ns();
+    float ms = 0.0f;
+    uint64_t dev_ns = 0;
+    if (status == PTG_OK && cudaEventElapsedTime(&ms, S->begin[slot], S->done[slot]) == cudaSuccess && ms > 0.0f)
+        dev_ns = (uint64_t)((double)ms * 1e6);
+    cudaGetLastError();
+    const uint64_t span = r->ts[3] - r->ts[1];
+    r->ts[2] = r->ts[3] - (dev_ns < span ? dev_ns : span);
     S->admitted -= r->bytes;
     S->running[slot] = nullptr;
 }
@@ -135,7 +141,7 @@ void progress(ptg_ctx* ctx, PtgServer* S)
             S->hold_next = 0;
             cudaLaunchHostFunc(st, on_hold, &S->hold);
         }
-        cudaLaunchHostFunc(st, on_start, r);
+        cudaEventRecord(S->begin[slot], st);
         const int64_t slow = r->d.dims == 3 ? r->d.size[2] : r->d.size[1];
         const int rc = ptg_launch_plan(ctx, kKindField, &r->d, r->s, r->out, 0, slow, st);
         if (rc != PTG_OK) {
@@ -143,7 +149,6 @@ void progress(ptg_ctx* ctx, PtgServer* S)
             r->ts[2] = r->ts[3] = now_ns();
             continue;
         }
-        cudaLaunchHostFunc(st, on_end, r);
         cudaEventRecord(S->done[slot], st);
         S->running[slot] = r;
         S->admitted += r->bytes;
@@ -160,6 +165,7 @@ void ptg_serve_shutdown(ptg_ctx* ctx)
     for (int k = 0; k < kSlots; ++k) {
         cudaStreamSynchronize(S->streams[k]);
         cudaStreamDestroy(S->streams[k]);
+        cudaEventDestroy(S->begin[k]);
         cudaEventDestroy(S->done[k]);
     }
     for (auto& kv : S->reqs) delete kv.second;
