@@ -80,6 +80,8 @@ def lib():
         L.ptgo_octave_at.restype = ctypes.c_int
         L.ptgo_opensimplex_points.argtypes = [ctypes.c_uint32, ctypes.c_int, P, ctypes.c_int64, P]
         L.ptgo_opensimplex_points.restype = ctypes.c_int
+        L.ptgo_opensimplex3_points.argtypes = [ctypes.c_uint32, ctypes.c_int, P, ctypes.c_int64, P]
+        L.ptgo_opensimplex3_points.restype = ctypes.c_int
         L.ptgo_hash_batch.argtypes = [ctypes.c_int, P, ctypes.c_int64, P]
         L.ptgo_axis_batch.argtypes = [ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_int, P, P]
         L.ptgo_axis_freq_batch.argtypes = [ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int64, ctypes.c_double,
@@ -213,6 +215,15 @@ def opensimplex_points(seed: int, octave: int, xy: np.ndarray) -> np.ndarray:
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     out = np.empty(xy.shape[0], np.float64)
     lib().ptgo_opensimplex_points(seed, octave, _ptr(xy), xy.shape[0], _ptr(out))
+    return out
+
+
+def opensimplex3_points(seed: int, octave: int, xyz: np.ndarray) -> np.ndarray:
+    """3D OpenSimplex-style noise of one octave at real lattice positions
+    (n x 3)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    out = np.empty(xyz.shape[0], np.float64)
+    lib().ptgo_opensimplex3_points(seed, octave, _ptr(xyz), xyz.shape[0], _ptr(out))
     return out
 
 

@@ -43,7 +43,8 @@
  *   - The zero-gradient model of Eq. (zg) is taken with the sign of the xy
  *     term that the Sec. 3.1 coefficients give (-xy), not the printed +xy.
  *   - OpenSimplex-style noise: stretch (1/sqrt(3) - 1)/2, squish
- *     (sqrt(3) - 1)/2, kernel (2 - r^2)^4 (g . d), hashed gradients, scale 1/8.
+ *     (sqrt(3) - 1)/2, kernel (2 - r^2)^4 (g . d), hashed gradients, scale 1/8;
+ *     in 3D stretch -1/6, squish 1/3, the same kernel and scale.
  */
 #include <math.h>
 #include <stdint.h>
@@ -556,6 +557,86 @@ double ptgo_opensimplex_at(double x, double y, uint32_t seed, int octave)
 }
 
 /* ------------------------------------------------------------------------ */
+/* 3D OpenSimplex-style noise: the same construction one dimension up.       */
+/* Squishing Z^3 along its main diagonal by (sqrt(4) - 1)/3 = 1/3 gives a    */
+/* lattice whose nearest vertices are sqrt(2) apart (face-centred cubic); a   */
+/* point's stretched coordinates are x_k - (x + y + z)/6 (the inverse map).   */
+/* Every vertex within distance sqrt(2) adds (2 - r^2)^4 (g . d), g = words   */
+/* 1..3 of pcg4d(a, b, c, key).  Brute force over the 7 x 7 x 7 block of the  */
+/* stretched lattice around the point (every vertex in range has stretched   */
+/* offsets in -1..2 from the point's cell).  Same scale 1/8 as in 2D (the   */
+/* raw 3D sum has about the spread of the raw 2D one times 8 as well).       */
+/* ------------------------------------------------------------------------ */
+/* Sum over the vertices a0 + (da, db, dc) for a point at stretched fraction
+ * xi in [0, 1)^3 of cell a0: its displacement from a vertex is u + (sum u)/3
+ * per axis, u = xi - (da, db, dc). */
+static double os3_sum(const int64_t a0[3], const double xi[3], uint32_t key)
+{
+    double sum = 0.0;
+    for (int da = -3; da <= 3; ++da)
+        for (int db = -3; db <= 3; ++db)
+            for (int dc = -3; dc <= 3; ++dc) {
+                const double u0 = xi[0] - da, u1 = xi[1] - db, u2 = xi[2] - dc;
+                const double sq = (u0 + u1 + u2) / 3.0;
+                const double d0 = u0 + sq, d1 = u1 + sq, d2 = u2 + sq;
+                const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                if (r2 < 2.0) {
+                    uint32_t in[4] = {(uint32_t)(a0[0] + da), (uint32_t)(a0[1] + db), (uint32_t)(a0[2] + dc), key};
+                    uint32_t h[4];
+                    ptgo_pcg4d(in, h);
+                    const double k = 2.0 - r2;
+                    sum += k * k * k * k * (ptgo_unit(h[1]) * d0 + ptgo_unit(h[2]) * d1 + ptgo_unit(h[3]) * d2);
+                }
+            }
+    return sum * OS_SCALE;
+}
+
+/* At a real lattice position (x, y, z) of octave i. */
+double ptgo_opensimplex3_at(double x, double y, double z, uint32_t seed, int octave)
+{
+    const double sh = -(x + y + z) / 6.0;
+    const double s[3] = {x + sh, y + sh, z + sh};
+    int64_t a0[3];
+    double xi[3];
+    for (int k = 0; k < 3; ++k) {
+        const double fl = floor(s[k]);
+        a0[k] = (int64_t)fl;
+        xi[k] = s[k] - fl;
+    }
+    return os3_sum(a0, xi, octave_key(seed, octave));
+}
+
+/* Sample (j_x, j_y, j_z) at octave i of a field with frequency ratio 2:
+ * lattice coordinate x_k = I_k + F_k exactly, with the integer
+ * I_k = origin_k 2^i + floor(j_k 2^i / spc_k) and the fraction
+ * F_k = (j_k 2^i mod spc_k) / spc_k.  Then 6 s_k = (6 I_k - sum I) + (6 F_k -
+ * sum F): the stretch needs no rounding at any distance from the origin. */
+static double os3_dyadic(const int64_t* origin, const int64_t* spc, const int64_t* j, uint32_t seed, int octave)
+{
+    int64_t I[3], sumI = 0;
+    double F[3], sumF = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const int64_t q = j[k] << octave;
+        I[k] = origin[k] * ((int64_t)1 << octave) + q / spc[k];
+        F[k] = (double)(q % spc[k]) / (double)spc[k];
+        sumI += I[k];
+        sumF += F[k];
+    }
+    int64_t a0[3];
+    double xi[3];
+    for (int k = 0; k < 3; ++k) {
+        const double G = 6.0 * F[k] - sumF; /* in (-3, 6) */
+        const double fG = floor(G);
+        const int64_t T = 6 * I[k] - sumI + (int64_t)fG;
+        int64_t a = T / 6;
+        if (T - 6 * a < 0) a -= 1; /* floor division */
+        a0[k] = a;
+        xi[k] = ((double)(T - 6 * a) + (G - fG)) / 6.0;
+    }
+    return os3_sum(a0, xi, octave_key(seed, octave));
+}
+
+/* ------------------------------------------------------------------------ */
 /* Fields                                                                    */
 /* ------------------------------------------------------------------------ */
 static int desc_ok(const ptgo_desc* d)
@@ -564,7 +645,8 @@ static int desc_ok(const ptgo_desc* d)
     if (!(d->frequency == 0.0 || (d->frequency >= 1.0 && d->frequency <= 16.0))) return 0;
     for (int k = 0; k < d->dims; ++k)
         if (d->size[k] <= 0 || d->cells[k] <= 0 || d->size[k] % d->cells[k]) return 0;
-    if (d->method == PTGO_C1 || d->method == PTGO_C2 || d->method == PTGO_PERLIN_S5 || d->method == PTGO_PERLIN_S3)
+    if (d->method == PTGO_C1 || d->method == PTGO_C2 || d->method == PTGO_PERLIN_S5 || d->method == PTGO_PERLIN_S3 ||
+        d->method == PTGO_OPENSIMPLEX)
         return 1;
     if (d->dims == 2 && (d->method == PTGO_PAPER_GAUGE || d->method == PTGO_ZERO_GRAD ||
                          d->method == PTGO_PERLIN_S5 || d->method == PTGO_PERLIN_S3 ||
@@ -611,7 +693,17 @@ int ptgo_field_samples(const ptgo_desc* d, const int64_t* idx, int64_t n, double
                     else
                         ptgo_axis_freq(d->origin[k], spc[k], idx[m * dims + k], d->frequency, i, &cell[k], &t[k]);
                 }
-                if (d->method == PTGO_OPENSIMPLEX) {
+                if (d->method == PTGO_OPENSIMPLEX && dims == 3) {
+                    if (dyadic(d)) {
+                        h = os3_dyadic(d->origin, spc, idx + m * dims, d->seed, i);
+                    } else {
+                        const double scale = pow(d->frequency, (double)i);
+                        double x[3];
+                        for (int k = 0; k < 3; ++k)
+                            x[k] = ((double)d->origin[k] + (double)idx[m * dims + k] / (double)spc[k]) * scale;
+                        h = ptgo_opensimplex3_at(x[0], x[1], x[2], d->seed, i);
+                    }
+                } else if (d->method == PTGO_OPENSIMPLEX) {
                     /* real position in octave-i lattice units: (origin + j/spc) f^i */
                     double scale = dyadic(d) ? ldexp(1.0, i) : pow(d->frequency, (double)i);
                     double x = ((double)d->origin[0] + (double)idx[m * dims] / (double)spc[0]) * scale;
@@ -682,6 +774,14 @@ int ptgo_octave_at(int dims, int method, uint32_t seed, int octave, double w, co
 int ptgo_opensimplex_points(uint32_t seed, int octave, const double* xy, int64_t n, double* out)
 {
     for (int64_t m = 0; m < n; ++m) out[m] = ptgo_opensimplex_at(xy[2 * m], xy[2 * m + 1], seed, octave);
+    return 0;
+}
+
+/* 3D OpenSimplex-style noise of one octave at real lattice positions. */
+int ptgo_opensimplex3_points(uint32_t seed, int octave, const double* xyz, int64_t n, double* out)
+{
+    for (int64_t m = 0; m < n; ++m)
+        out[m] = ptgo_opensimplex3_at(xyz[3 * m], xyz[3 * m + 1], xyz[3 * m + 2], seed, octave);
     return 0;
 }
 

@@ -556,3 +556,81 @@ def test_hash_statistics(dims):
     assert abs(diff - 0.5) < 0.02
     # unit(): exact grid of 2^-22 in [-1, 1)
     assert O.unit(0) == -1.0 and O.unit(0xFFFFFFFF) == 1.0 - 2.0**-22
+
+
+# --------------------------------------------------------------------------
+# 3D OpenSimplex-style noise: squish 1/3, stretch -1/6, nearest vertices
+# sqrt(2) apart, kernel (2 - r^2)^4 (g . d), scale 1/8
+# --------------------------------------------------------------------------
+def _vertex3(a, b, c):
+    s = (a + b + c) / 3.0
+    return np.array([a + s, b + s, c + s])
+
+
+def test_opensimplex3_zero_at_vertices_and_gradient():
+    """At a vertex only that vertex is in range (its neighbours sit at r^2 = 2
+    exactly, where the kernel vanishes with three derivatives): h = 0 and
+    grad h = 16 g / 8 = 2 g, g = pcg4d words 1..3."""
+    eps = 1e-6
+    for a, b, c in [(0, 0, 0), (3, -2, 5), (10, 7, -1), (-5, 12, 4)]:
+        p = _vertex3(a, b, c)
+        assert abs(O.opensimplex3_points(4, 2, p[None])[0]) < 1e-12
+        w = O.hash_batch(3, np.array([[a % 2**32, b % 2**32, c % 2**32, (4 << 8) | 2]], np.uint32))[0]
+        g = np.array([O.unit(w[1]), O.unit(w[2]), O.unit(w[3])])
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = eps
+            hk = O.opensimplex3_points(4, 2, (p + e)[None])[0]
+            assert abs(hk / eps - 2 * g[k]) < 1e-4
+
+
+def test_opensimplex3_neighbours_are_sqrt2_apart():
+    """The squished lattice is face-centred cubic: the twelve stretched offsets
+    +-e_k and e_i - e_j are at distance sqrt(2); the next shell is at 2."""
+    base = _vertex3(0, 0, 0)
+    offs = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, -1, 0), (1, 0, -1), (0, 1, -1)]
+    for o in offs:
+        for sgn in (1, -1):
+            v = _vertex3(*(sgn * np.array(o)))
+            assert abs(np.sum((v - base) ** 2) - 2.0) < 1e-12
+    for o in [(1, 1, 0), (1, 1, 1), (2, 0, 0), (1, 1, -1)]:
+        assert np.sum((_vertex3(*o) - base) ** 2) >= 4.0 - 1e-12
+
+
+def test_opensimplex3_is_smooth():
+    """The kernel vanishes with three derivatives at r^2 = 2: the field is C1,
+    also across the faces of the simplices."""
+    pts = RNG.uniform(-10, 10, size=(200, 3))
+    e = 1e-4
+    for k in range(3):
+        dv = np.zeros(3)
+        dv[k] = 1.0
+        f = lambda s: O.opensimplex3_points(1, 0, pts + s * dv)
+        d_c = (f(e) - f(-e)) / (2 * e)
+        d_c2 = (f(2 * e) - f(-2 * e)) / (4 * e)
+        assert np.abs(d_c - d_c2).max() < 1e-5
+
+
+def test_opensimplex3_field_routes_agree():
+    """The field's exact integer / fraction route to the stretched lattice
+    (dyadic frequencies) equals the real-position route, octave by octave,
+    at origins on both sides of zero."""
+    size, cells, origin = (12, 10, 9), (3, 2, 3), (5, -3, 7)
+    spc = [s // c for s, c in zip(size, cells)]
+    rng = np.random.default_rng(3)
+    idx = np.stack([rng.integers(0, s, 300) for s in size], 1)
+    for i in range(4):
+        one = O.field_samples(3, size, cells, idx, origin=origin, octaves=i + 1, method=O.OPENSIMPLEX, seed=9,
+                              persistence=1.0)
+        prev = O.field_samples(3, size, cells, idx, origin=origin, octaves=i, method=O.OPENSIMPLEX, seed=9,
+                               persistence=1.0) if i else 0.0
+        pos = np.stack([(origin[k] + idx[:, k] / spc[k]) * 2.0**i for k in range(3)], 1)
+        assert np.abs((one - prev) - O.opensimplex3_points(9, i, pos)).max() < 1e-12
+
+
+def test_opensimplex3_range_and_mean():
+    """|h| stays below the sum of the kernel maxima of the vertices in range;
+    the hashed gradients are centred, so the field is too."""
+    h = O.opensimplex3_points(2, 1, RNG.uniform(-40, 40, size=(100000, 3)))
+    assert abs(h.mean()) < 0.01 and 0.2 < h.std() < 0.5
+    assert np.abs(h).max() < 2.0
