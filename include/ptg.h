@@ -55,7 +55,7 @@ typedef enum {
     PTG_OK = 0,
     PTG_PENDING = 1,
     PTG_ERR_INVALID = -1,     /* bad argument                                  */
-    PTG_ERR_UNSUPPORTED = -2, /* valid but not supported (e.g. 3D OpenSimplex)  */
+    PTG_ERR_UNSUPPORTED = -2, /* valid but not supported (e.g. a too-tall field) */
     PTG_ERR_NOMEM = -3,       /* an allocation failed                          */
     PTG_ERR_BUDGET = -4,      /* request can never fit the HBM budget          */
     PTG_ERR_CUDA = -5,        /* a CUDA call failed                            */
@@ -173,9 +173,12 @@ int ptg_perlin(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, void* stream
  * squished into equilateral triangles of edge sqrt(2) (stretch
  * (1/sqrt(3) - 1)/2, squish (sqrt(3) - 1)/2); every vertex (a, b) within
  * distance sqrt(2) of the point adds (2 - r^2)^4 (g . d), g from hash words
- * 1..2 of (a, b, seed << 8 | i); the sum is scaled by 1/8.  2D; the
- * finest octave's lattice coordinates must stay below 2^30 in magnitude
- * ((|origin| + (offset + size)/spc) * 2^(N-1) < 2^30), else
+ * 1..2 of pcg3d(a, b, seed << 8 | i); the sum is scaled by 1/8.  In 3D the
+ * squish is 1/3 and the stretch -1/6 (nearest vertices sqrt(2) apart, the
+ * face-centred cubic lattice), g = hash words 1..3 of pcg4d(a, b, c,
+ * seed << 8 | i), with the same kernel and scale.  2D or 3D; the finest
+ * octave's lattice coordinates must stay below 2^30 in magnitude
+ * ((|origin| + (offset + size)/spc) * f^(N-1) < 2^30), else
  * PTG_ERR_UNSUPPORTED. */
 int ptg_opensimplex(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, void* stream);
 

@@ -76,8 +76,6 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
     if (d->struct_size != sizeof(ptg_field_desc))
         return ptg_fail(ctx, PTG_ERR_INVALID, "struct_size %u != %zu", d->struct_size, sizeof(ptg_field_desc));
     if (d->dims != 2 && d->dims != 3) return ptg_fail(ctx, PTG_ERR_INVALID, "dims must be 2 or 3");
-    if (kind == kKindSimplex && d->dims != 2)
-        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "the OpenSimplex baseline is 2D");
     const int s = log2_exact(d->spc);
     if (d->spc <= 0 || d->spc > (int64_t{1} << 30)) return ptg_fail(ctx, PTG_ERR_INVALID, "spc out of [1, 2^30]");
     // the fused generators need tiles aligned to cells; the per-sample ones
@@ -274,6 +272,66 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
     return PTG_OK;
 }
 
+// Launch plan of a 3D OpenSimplex field (or of a band of planes of one).
+int ptg_make_simplex3_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int64_t band_start, int64_t band_len,
+                           Simplex3Plan* P)
+{
+    memset(P, 0, sizeof *P);
+    P->out = out;
+    P->W = (int32_t)d->size[0];
+    P->H = (int32_t)d->size[1];
+    P->D = (int32_t)band_len;
+    P->dtype = d->dtype;
+    P->N = d->octaves;
+    P->tiles_x = (P->W + kTile3dX - 1) / kTile3dX;
+    P->tiles_y = (P->H + kTile3dY - 1) / kTile3dY;
+    P->tiles_z = (P->D + kTile3dZ - 1) / kTile3dZ;
+    if (P->tiles_y > 65535 || P->tiles_z > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall");
+    const int esz = d->dtype == PTG_F16 ? 2 : 4;
+    P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
+    const double spc = (double)d->spc, f = (double)d->lacunarity;
+    double lim = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double e = std::fabs((double)d->origin[k]) + (double)(d->offset[k] + d->size[k]) / spc;
+        if (e > lim) lim = e;
+    }
+    if (lim * std::pow(f, (double)(d->octaves - 1)) >= std::ldexp(1.0, 30))
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "OpenSimplex lattice coordinates exceed 2^30");
+    const double ext[3] = {kTile3dX - 1, kTile3dY - 1, kTile3dZ - 1};
+    constexpr int kBoxMax = 4096;  // vertices (float4 each) of the shared gradient box: 64 KB
+    double amp = 1.0;
+    int box = 0;
+    for (int i = 0; i < d->octaves; ++i) {
+        const double scale = f == 2.0 ? std::ldexp(1.0, i) : std::pow(f, (double)i);
+        const double step = scale / spc;
+        for (int k = 0; k < 3; ++k)
+            P->base[k][i] = (double)d->origin[k] * scale + (double)(d->offset[k] + (k == 2 ? band_start : 0)) * step;
+        P->step_d[i] = step;
+        P->step[i] = (float)step;
+        P->step_lo[i] = (float)(step - (double)P->step[i]);
+        int ex = 0;
+        if (std::frexp(step, &ex) == 0.5) P->exact_mask |= 1u << i;
+        P->amp[i] = (float)amp;
+        P->key[i] = (d->seed << 8) | (uint32_t)i;
+        amp *= (double)d->persistence;
+        // stage while the lattice is coarser than the samples and the box
+        // fits: the tile spans (5/6) L_k + (1/6)(sum L - L_k) stretched units
+        // along axis k (L = tile extent), widened by 1e-5 on each side; its
+        // floors take at most floor(span) + 2 values, plus one vertex of
+        // margin below and two above
+        if (step >= 1.0) continue;
+        const double L[3] = {ext[0] * step, ext[1] * step, ext[2] * step}, sumL = L[0] + L[1] + L[2];
+        int bw[3];
+        for (int k = 0; k < 3; ++k) bw[k] = (int)std::floor((5.0 * L[k] + (sumL - L[k])) / 6.0 + 1e-4) + 5;
+        const int n = bw[0] * bw[1] * bw[2];
+        if (n > kBoxMax) continue;
+        for (int k = 0; k < 3; ++k) P->box_w[k][i] = bw[k];
+        if (n > box) box = n;
+    }
+    P->box_words = box;
+    return PTG_OK;
+}
+
 // Launch plan of a 2D polynomial / Perlin field with a frequency ratio other
 // than 2 (or of a band of one), for the per-sample generator.
 int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int s, int64_t band_start,
@@ -392,7 +450,12 @@ int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void
                     int64_t band_len, cudaStream_t st)
 {
     cudaError_t e;
-    if (kind == kKindSimplex) {
+    if (kind == kKindSimplex && d->dims == 3) {
+        Simplex3Plan P;
+        int rc = ptg_make_simplex3_plan(ctx, d, out, band_start, band_len, &P);
+        if (rc != PTG_OK) return rc;
+        e = launch_opensimplex3d(P, st);
+    } else if (kind == kKindSimplex) {
         SimplexPlan P;
         int rc = ptg_make_simplex_plan(ctx, d, out, s, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
@@ -543,7 +606,10 @@ int ptg_validate(const ptg_field_desc* d, int32_t method, char* msg, int32_t msg
     int rc = ptg_check_desc(&scratch, d, kind, &s);
     if (rc == PTG_OK) {
         const int64_t slow = d->dims == 3 ? d->size[2] : d->size[1];
-        if (kind == kKindSimplex) {
+        if (kind == kKindSimplex && d->dims == 3) {
+            Simplex3Plan P;
+            rc = ptg_make_simplex3_plan(&scratch, d, nullptr, 0, slow, &P);
+        } else if (kind == kKindSimplex) {
             SimplexPlan P;
             rc = ptg_make_simplex_plan(&scratch, d, nullptr, s, 0, slow, &P);
         } else if ((d->lacunarity != 2.0f || s < 0) && d->dims == 3) {

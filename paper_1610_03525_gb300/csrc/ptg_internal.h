@@ -77,6 +77,8 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
                         int64_t band_len, ptg::FieldPlan* P);
 int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int s, int64_t band_start,
                           int64_t band_len, ptg::SimplexPlan* P);
+int ptg_make_simplex3_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int64_t band_start, int64_t band_len,
+                           ptg::Simplex3Plan* P);
 int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int s, int64_t band_start,
                           int64_t band_len, ptg::GeneralPlan* P);
 int ptg_make_general3_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int64_t band_start,

@@ -50,6 +50,25 @@ struct SimplexPlan {
 };
 cudaError_t launch_opensimplex2d(const SimplexPlan& P, cudaStream_t stream);
 
+// 3D OpenSimplex-style noise.  base[k][i] = real lattice coordinate along
+// axis k of the launch's sample (0, 0, 0) at octave i (FP64, host); step_d[i]
+// = lattice units per sample (also as float hi + lo).  Octaves whose gradient
+// box fits are staged one at a time into one shared buffer of box_words
+// float4; box_w[k][i] bounds the box extent along axis k (0 = hash per sample).
+struct Simplex3Plan {
+    void* out;
+    int32_t W, H, D, dtype, N, vec_ok, tiles_x, tiles_y, tiles_z;
+    int32_t box_words;
+    uint32_t exact_mask;  // bit i: step[i] is a power of two (products k * step exact)
+    int32_t pad;
+    double base[3][kMaxOctaves];
+    double step_d[kMaxOctaves];
+    float step[kMaxOctaves], step_lo[kMaxOctaves], amp[kMaxOctaves];
+    uint32_t key[kMaxOctaves];
+    int32_t box_w[3][kMaxOctaves];
+};
+cudaError_t launch_opensimplex3d(const Simplex3Plan& P, cudaStream_t stream);
+
 // Polynomial and Perlin fields with any frequency ratio f between octaves
 // (2D).  base[i] = lattice coordinate of output sample (0, 0) at octave i
 // (FP64, host); scale[i] = f^i / spc lattice units per sample, also split

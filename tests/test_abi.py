@@ -72,7 +72,10 @@ def test_desc_layout_matches_header(P):
     (dict(dtype=7), 0, -1),
     (dict(dims=4), 0, -1),
     (dict(dims=3, size=(32, 32, 32)), 1, 0),          # Perlin in 3D
-    (dict(dims=3, size=(32, 32, 32)), 2, -2),         # OpenSimplex is 2D
+    (dict(dims=3, size=(32, 32, 32)), 2, 0),          # OpenSimplex in 3D
+    (dict(dims=3, size=(32, 32, 32), spc=12, lacunarity=1.7), 2, 0),
+    (dict(dims=3, size=(32, 32, 32), origin=(1 << 25, 0, 0), octaves=8, spc=16), 2, -2),  # 2^32 lattice units
+    (dict(variant=0x100, dims=3, size=(32, 32, 32)), 2, -2),
     (dict(variant=5), 1, -1),
     (dict(offset=(32, 0, 0)), 0, -2),
     (dict(offset=(128, 64, 0)), 0, 0),
