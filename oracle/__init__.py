@@ -44,7 +44,7 @@ class Desc(ctypes.Structure):
         ("cells", ctypes.c_int64 * 3),
         ("origin", ctypes.c_int64 * 3),
         ("octaves", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("ridged", ctypes.c_int32),
         ("persistence", ctypes.c_double),
         ("grad_weight", ctypes.c_double),
         ("seed", ctypes.c_uint32),
@@ -99,10 +99,11 @@ def _ptr(a: np.ndarray):
 
 
 def make_desc(dims, size, cells, origin=(0, 0, 0), octaves=1, method=C1, persistence=0.5,
-              grad_weight=1.0, seed=0, frequency=2.0) -> Desc:
+              grad_weight=1.0, seed=0, frequency=2.0, ridged=False) -> Desc:
     d = Desc()
     d.dims = dims
     d.method = method
+    d.ridged = 1 if ridged else 0
     for k in range(3):
         d.size[k] = int(size[k]) if k < len(size) else 1
         d.cells[k] = int(cells[k]) if k < len(cells) else 1

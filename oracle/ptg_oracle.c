@@ -17,7 +17,8 @@
  *     built row by row from the derivative definition and solved numerically
  *     with LU and partial pivoting (never from a closed form);
  *   - the cell polynomial, evaluated monomial by monomial;
- *   - the fractal (fBm) octave sum of Sec. 4;
+ *   - the fractal (fBm) octave sum of Sec. 4, and the ridged multifractal
+ *     sum the paper renders its mountains with (Sec. 5.1, Fig. render2);
  *   - Perlin's polynomial of Sec. 3.2 and an OpenSimplex-style simplex-lattice
  *     gradient noise summed by brute force over a superset of lattice vertices;
  *   - the map statistics of Sec. 5: coastline box counts (Sec. 5.3) and the
@@ -42,6 +43,10 @@
  *     spc = size / cells; cell indices wrap modulo 2^32.
  *   - The zero-gradient model of Eq. (zg) is taken with the sign of the xy
  *     term that the Sec. 3.1 coefficients give (-xy), not the printed +xy.
+ *   - Ridged noise (shown in Sec. 5.1, defined by reference only): Musgrave's
+ *     ridged multifractal (Ebert et al., "Texturing and Modeling", ch. 16) with
+ *     offset 1 and gain 2 -- octave i contributes p^i r_i, r_i = (1 - |h_i|)^2
+ *     w_i, w_0 = 1, w_{i+1} = clamp(2 r_i, 0, 1); h_i the unit-amplitude octave.
  *   - OpenSimplex-style noise: stretch (1/sqrt(3) - 1)/2, squish
  *     (sqrt(3) - 1)/2, kernel (2 - r^2)^4 (g . d), hashed gradients, scale 1/8;
  *     in 3D stretch -1/6, squish 1/3, the same kernel and scale.
@@ -74,7 +79,7 @@ typedef struct {
     int64_t cells[3];     /* base-lattice cells per axis                    */
     int64_t origin[3];    /* base-lattice cell of sample 0 (integer)        */
     int32_t octaves;      /* N, octaves 0 .. N-1                            */
-    int32_t pad;
+    int32_t ridged;       /* 1: ridged multifractal sum instead of fBm      */
     double persistence;   /* p: amplitude ratio between octaves             */
     double grad_weight;   /* w of Sec. 4                                    */
     uint32_t seed;        /* < 2^24                                         */
@@ -682,7 +687,7 @@ int ptgo_field_samples(const ptgo_desc* d, const int64_t* idx, int64_t n, double
 #pragma omp for schedule(dynamic, 64)
 #endif
         for (int64_t m = 0; m < n; ++m) {
-            double H = 0.0, amp = 1.0;
+            double H = 0.0, amp = 1.0, weight = 1.0;
             for (int i = 0; i < d->octaves; ++i) {
                 uint32_t cell[3];
                 double t[3];
@@ -713,7 +718,18 @@ int ptgo_field_samples(const ptgo_desc* d, const int64_t* idx, int64_t n, double
                     h = lattice_octave(dims, d->method, cell, t, d->seed, i, d->grad_weight, coef[i], ccell[i],
                                        &cok[i]);
                 }
-                H += amp * h;
+                if (d->ridged) {
+                    /* ridged multifractal: the octave's ridge (1 - |h|)^2,
+                     * weighted by the previous octave's weighted ridge times
+                     * 2, clamped to [0, 1] */
+                    const double ridge = (1.0 - fabs(h)) * (1.0 - fabs(h)) * weight;
+                    H += amp * ridge;
+                    weight = 2.0 * ridge;
+                    if (weight > 1.0) weight = 1.0;
+                    if (weight < 0.0) weight = 0.0;
+                } else {
+                    H += amp * h;
+                }
                 amp *= d->persistence;
             }
             out[m] = H;

@@ -634,3 +634,54 @@ def test_opensimplex3_range_and_mean():
     h = O.opensimplex3_points(2, 1, RNG.uniform(-40, 40, size=(100000, 3)))
     assert abs(h.mean()) < 0.01 and 0.2 < h.std() < 0.5
     assert np.abs(h).max() < 2.0
+
+
+# --------------------------------------------------------------------------
+# Ridged multifractal sum (the paper's ridged mountains, Sec. 5.1): octave i
+# adds p^i r_i, r_i = (1 - |h_i|)^2 w_i, w_0 = 1, w_{i+1} = clamp(2 r_i, 0, 1)
+# --------------------------------------------------------------------------
+def _ridged_field(method, N, p=0.5, dims=2, size=(40, 24), cells=(2, 3), origin=(3, -5), seed=7):
+    return O.field_grid(dims, size, cells, origin=origin, octaves=N, method=method, persistence=p, seed=seed,
+                        ridged=True)
+
+
+@pytest.mark.parametrize("method", [O.C1, O.C2, O.ZERO_GRAD, O.PERLIN_S5])
+def test_ridged_one_octave_is_the_squared_ridge(method):
+    h = O.field_grid(2, (40, 24), (2, 3), origin=(3, -5), octaves=1, method=method, seed=7)
+    assert np.abs(_ridged_field(method, 1) - (1 - np.abs(h)) ** 2).max() < 1e-15
+
+
+def test_ridged_at_the_lattice_origin_uses_corner_values():
+    """At sample (0, 0) every octave sits on a corner, so h_i is corner value
+    v_i (hash word 0) and the sum follows from the hash alone."""
+    N, p, seed = 6, 0.6, 9
+    got = O.field_grid(2, (8, 8), (1, 1), origin=(0, 0), octaves=N, method=O.C1, persistence=p, seed=seed,
+                       ridged=True)[0, 0]
+    keys = np.array([[0, 0, (seed << 8) | i] for i in range(N)], np.uint32)
+    v = [O.unit(w[0]) for w in O.hash_batch(2, keys)]
+    want, weight, amp = 0.0, 1.0, 1.0
+    for i in range(N):
+        r = (1 - abs(v[i])) ** 2 * weight
+        want += amp * r
+        amp *= float(np.float32(p))  # the persistence enters as the float32 the GPU path receives
+        weight = min(max(2 * r, 0.0), 1.0)
+    assert abs(got - want) < 1e-15
+
+
+@pytest.mark.parametrize("method", [O.C1, O.ZERO_GRAD, O.PERLIN_S3])
+def test_ridged_range_and_monotone_in_octaves(method):
+    """|h_i| <= 1.5 for these models, so 0 <= r_i <= 1 and 0 <= H <= A_tot;
+    every octave adds a non-negative term."""
+    prev = np.zeros((24, 40))
+    for N in range(1, 7):
+        H = _ridged_field(method, N, p=0.7)
+        assert H.min() >= 0.0 and H.max() <= sum(0.7 ** i for i in range(N)) + 1e-12
+        assert np.all(H >= prev - 1e-15)
+        prev = H
+
+
+def test_ridged_3d_and_any_frequency():
+    h = O.field_grid(3, (12, 10, 8), (2, 2, 2), origin=(1, 2, 3), octaves=1, method=O.C1, seed=3, frequency=1.7)
+    r = O.field_grid(3, (12, 10, 8), (2, 2, 2), origin=(1, 2, 3), octaves=1, method=O.C1, seed=3, frequency=1.7,
+                     ridged=True)
+    assert np.abs(r - (1 - np.abs(h)) ** 2).max() < 1e-15
