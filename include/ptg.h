@@ -105,6 +105,17 @@ typedef enum { PTG_SHAPE_AUTO = 0, PTG_SHAPE_8X4 = 0x100, PTG_SHAPE_16X2 = 0x200
  * only.  No counterpart in the paper: a GPU tuning choice. */
 typedef enum { PTG_COARSE_AUTO = 0, PTG_COARSE_RUNS = 0x400, PTG_COARSE_TILE = 0x800 } ptg_coarse;
 
+/* Ridged noise, or-ed into desc->variant of ptg_field / ptg_perlin (2D or
+ * 3D): the ridged mountains the paper renders (Sec. 5.1, figure of ridged
+ * zero-gradient D2M1N3 noise), which it defines only by reference to a noise
+ * library.  Read as Musgrave's ridged multifractal (Ebert et al., "Texturing
+ * and Modeling", ch. 16) with offset 1 and gain 2: octave i contributes
+ * p^i r_i with r_i = (1 - |h_i|)^2 w_i, h_i the unit-amplitude octave field,
+ * w_0 = 1 and w_{i+1} = clamp(2 r_i, 0, 1).  The octaves interact, so these
+ * fields run the per-sample generators in octave order (thread-shape and
+ * coarse-octave bits are ignored); batches (ptg_batch*) do not take them. */
+#define PTG_RIDGED 0x1000
+
 /* Full description of one field (Sec. 2.1 cell lattice, Sec. 4 octaves). */
 typedef struct {
     uint32_t struct_size; /* sizeof(ptg_field_desc)                            */
@@ -136,7 +147,8 @@ typedef struct {
     int32_t dtype;        /* ptg_dtype                                         */
     int32_t variant;      /* low byte: ptg_perlin_blend for ptg_perlin, else 0;
                              bits 8..9: ptg_shape, bits 10..11: ptg_coarse
-                             (2D field / Perlin only)                          */
+                             (2D field / Perlin only); bit 12: PTG_RIDGED
+                             (field / Perlin)                                  */
 } ptg_field_desc;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the

@@ -23,6 +23,7 @@ PTG_F32, PTG_F16 = 0, 1
 PTG_PERLIN_S5, PTG_PERLIN_S3 = 0, 1
 PTG_SHAPE_AUTO, PTG_SHAPE_8X4, PTG_SHAPE_16X2 = 0, 0x100, 0x200
 PTG_COARSE_AUTO, PTG_COARSE_RUNS, PTG_COARSE_TILE = 0, 0x400, 0x800
+PTG_RIDGED = 0x1000
 METHOD_FIELD, METHOD_PERLIN, METHOD_OPENSIMPLEX = 0, 1, 2
 
 STATUS_NAMES = {

@@ -68,6 +68,13 @@ int ptg_cuda_fail(ptg_ctx* ctx, cudaError_t e, const char* where)
     return ptg_fail(ctx, PTG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+// Polynomial / Perlin fields that run the per-sample generators: a frequency
+// ratio other than 2, spc not a power of two, or ridged noise.
+bool ptg_per_sample(const ptg_field_desc* d, int spc_log2)
+{
+    return d->lacunarity != 2.0f || spc_log2 < 0 || (d->variant & PTG_RIDGED) != 0;
+}
+
 // Argument checks common to every generator.  On success fills *spc_log2
 // (-1 when spc is not a power of two: 2D, per-sample generators).
 int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log2)
@@ -80,7 +87,7 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
     if (d->spc <= 0 || d->spc > (int64_t{1} << 30)) return ptg_fail(ctx, PTG_ERR_INVALID, "spc out of [1, 2^30]");
     // the fused generators need tiles aligned to cells; the per-sample ones
     // (OpenSimplex, and 2D fields with any other spc or frequency ratio) do not
-    const bool fused = kind != kKindSimplex && s >= 0 && d->lacunarity == 2.0f;
+    const bool fused = kind != kKindSimplex && s >= 0 && d->lacunarity == 2.0f && !(d->variant & PTG_RIDGED);
     static const int tile2[3] = {kTile2dX, kTile2dY, 1}, tile3[3] = {kTile3dX, kTile3dY, kTile3dZ};
     for (int k = 0; k < d->dims; ++k) {
         if (d->size[k] <= 0 || d->size[k] > (int64_t{1} << 30))
@@ -99,24 +106,27 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
     if (kind == kKindField && d->dims == 3 && d->smoothness != PTG_C1 && d->smoothness != PTG_C2)
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "the paper's D2M1N3 and zero-gradient models are 2D");
     const int blend = d->variant & 0xff, shape = d->variant & 0x300, coarse = d->variant & 0xc00;
-    if (d->variant & ~0xfff) return ptg_fail(ctx, PTG_ERR_INVALID, "variant: unknown bits 0x%x", (unsigned)d->variant);
+    const bool ridged = (d->variant & PTG_RIDGED) != 0;
+    if (d->variant & ~0x1fff) return ptg_fail(ctx, PTG_ERR_INVALID, "variant: unknown bits 0x%x", (unsigned)d->variant);
+    if (ridged && kind == kKindSimplex)
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "ridged noise is built for the polynomial models and Perlin");
     if (shape == 0x300) return ptg_fail(ctx, PTG_ERR_INVALID, "variant: unknown thread-shape bits");
     if (coarse == 0xc00) return ptg_fail(ctx, PTG_ERR_INVALID, "variant: unknown coarse-octave bits");
     if (kind == kKindPerlin && blend != PTG_PERLIN_S5 && blend != PTG_PERLIN_S3)
         return ptg_fail(ctx, PTG_ERR_INVALID, "Perlin variant must be PTG_PERLIN_S5 or PTG_PERLIN_S3");
     if (kind != kKindPerlin && blend != 0)
         return ptg_fail(ctx, PTG_ERR_INVALID, "variant: the low byte is the Perlin blend, 0 for other generators");
-    if ((shape | coarse) != 0 && (kind == kKindSimplex || d->dims != 2))
+    if ((shape | coarse) != 0 && (kind == kKindSimplex || d->dims != 2) && !ridged)
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "thread shape and coarse-octave mode apply to 2D polynomial and "
                                                   "Perlin fields");
-    if (coarse == PTG_COARSE_TILE && ((kind == kKindField && d->smoothness == PTG_C2) ||
-                                      (kind == kKindPerlin && blend == PTG_PERLIN_S5)))
+    if (coarse == PTG_COARSE_TILE && !ridged && ((kind == kKindField && d->smoothness == PTG_C2) ||
+                                                 (kind == kKindPerlin && blend == PTG_PERLIN_S5)))
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "tile nodes apply to models of degree <= 4 (not C2, not Perlin S5)");
     if (!std::isfinite(d->persistence) || !std::isfinite(d->grad_weight))
         return ptg_fail(ctx, PTG_ERR_INVALID, "persistence and grad_weight must be finite");
     if (!std::isfinite(d->lacunarity) || d->lacunarity < 1.0f || d->lacunarity > 16.0f)
         return ptg_fail(ctx, PTG_ERR_INVALID, "lacunarity (frequency ratio) must be in [1, 16]");
-    if (d->lacunarity != 2.0f || s < 0) {
+    if (d->lacunarity != 2.0f || s < 0 || ridged) {
         // per-sample generators: every octave's lattice coordinates must stay below 2^30 in magnitude
         const double fN = std::pow((double)d->lacunarity, (double)(d->octaves - 1));
         for (int k = 0; k < d->dims; ++k) {
@@ -344,6 +354,7 @@ int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, voi
     P->dtype = d->dtype;
     P->N = d->octaves;
     P->method = method;
+    P->ridged = (d->variant & PTG_RIDGED) ? 1 : 0;
     P->tiles_x = (P->W + kTile2dX - 1) / kTile2dX;
     P->tiles_y = (P->H + kTile2dY - 1) / kTile2dY;
     if (P->tiles_y > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall for one launch");
@@ -361,8 +372,9 @@ int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, voi
         P->scale[i] = scale;
         P->scale_hi[i] = (float)scale;
         P->scale_lo[i] = (float)(scale - (double)P->scale_hi[i]);
-        P->amp[i] = (float)amp;
-        P->ampw[i] = (float)(amp * w);
+        P->amp[i] = P->ridged ? 1.0f : (float)amp;
+        P->ampw[i] = P->ridged ? (float)w : (float)(amp * w);
+        P->wgt[i] = (float)amp;
         P->key[i] = (d->seed << 8) | (uint32_t)i;
         // stage the corners of the cells a tile spans while cells cover two or
         // more samples: one cell before the base cell, floor(63 scale) + 1
@@ -395,6 +407,7 @@ int ptg_make_general3_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, vo
     P->dtype = d->dtype;
     P->N = d->octaves;
     P->method = method;
+    P->ridged = (d->variant & PTG_RIDGED) ? 1 : 0;
     P->tiles_x = (P->W + kTile3dX - 1) / kTile3dX;
     P->tiles_y = (P->H + kTile3dY - 1) / kTile3dY;
     P->tiles_z = (P->D + kTile3dZ - 1) / kTile3dZ;
@@ -413,8 +426,9 @@ int ptg_make_general3_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, vo
         P->scale[i] = scale;
         P->scale_hi[i] = (float)scale;
         P->scale_lo[i] = (float)(scale - (double)P->scale_hi[i]);
-        P->amp[i] = (float)amp;
-        P->ampw[i] = (float)(amp * w);
+        P->amp[i] = P->ridged ? 1.0f : (float)amp;
+        P->ampw[i] = P->ridged ? (float)w : (float)(amp * w);
+        P->wgt[i] = (float)amp;
         P->key[i] = (d->seed << 8) | (uint32_t)i;
         if (scale <= 0.5) {  // one cell before the base cell, ext * scale + 1 after it, one for rounding, +1 corner
             int bw[3];
@@ -460,12 +474,12 @@ int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void
         int rc = ptg_make_simplex_plan(ctx, d, out, s, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
         e = launch_opensimplex2d(P, st);
-    } else if ((d->lacunarity != 2.0f || s < 0) && d->dims == 3) {  // any frequency ratio or spc, 3D
+    } else if (ptg_per_sample(d, s) && d->dims == 3) {  // any frequency ratio or spc, ridged: 3D
         General3Plan P;
         int rc = ptg_make_general3_plan(ctx, d, ptg_kernel_method(kind, d), out, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
         e = launch_general3d(P, st);
-    } else if (d->lacunarity != 2.0f || s < 0) {  // any frequency ratio or spc: per-sample generator
+    } else if (ptg_per_sample(d, s)) {  // any frequency ratio or spc, ridged: per-sample generator
         GeneralPlan P;
         int rc = ptg_make_general_plan(ctx, d, ptg_kernel_method(kind, d), out, s, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
@@ -612,10 +626,10 @@ int ptg_validate(const ptg_field_desc* d, int32_t method, char* msg, int32_t msg
         } else if (kind == kKindSimplex) {
             SimplexPlan P;
             rc = ptg_make_simplex_plan(&scratch, d, nullptr, s, 0, slow, &P);
-        } else if ((d->lacunarity != 2.0f || s < 0) && d->dims == 3) {
+        } else if (ptg_per_sample(d, s) && d->dims == 3) {
             General3Plan P;
             rc = ptg_make_general3_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, 0, slow, &P);
-        } else if (d->lacunarity != 2.0f || s < 0) {
+        } else if (ptg_per_sample(d, s)) {
             GeneralPlan P;
             rc = ptg_make_general_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, s, 0, slow, &P);
         } else {

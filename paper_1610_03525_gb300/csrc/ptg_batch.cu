@@ -33,9 +33,9 @@ int build_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, in
         int rc = ptg_check_desc(ctx, d, kKindField, &s);
         if (rc != PTG_OK) return ptg_fail(ctx, rc, "batch field %d: %s", f, ctx->err.c_str());
         if (d->dims != 2) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "batch field %d: batches are 2D", f);
-        if (d->lacunarity != 2.0f || s < 0)
+        if (ptg_per_sample(d, s))
             return ptg_fail(ctx, PTG_ERR_UNSUPPORTED,
-                            "batch field %d: batches need lacunarity 2 and a power-of-two spc", f);
+                            "batch field %d: batches need lacunarity 2, a power-of-two spc and no ridged noise", f);
         if (!outs[f]) return ptg_fail(ctx, PTG_ERR_INVALID, "batch field %d: out is NULL", f);
         rc = ptg_make_field_plan(ctx, d, ptg_kernel_method(kKindField, d), outs[f], s, 0, d->size[1], plans + f);
         if (rc != PTG_OK) return ptg_fail(ctx, rc, "batch field %d: %s", f, ctx->err.c_str());

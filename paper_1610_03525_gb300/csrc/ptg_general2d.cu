@@ -48,7 +48,10 @@ __device__ __forceinline__ Cell hashed_cell(uint32_t cx, uint32_t cy, uint32_t k
     return c;
 }
 
-template <int METHOD>
+// kRidged: each octave adds wgt_i r with r = (1 - |h|)^2 w, w the clamped
+// doubled ridge of the octave before (1 at octave 0); otherwise the octave
+// value (its amplitude already in the corner data).
+template <int METHOD, bool kRidged>
 __global__ void __launch_bounds__(kThreads) general2d_kernel(const __grid_constant__ GeneralPlan P)
 {
     extern __shared__ float4 sm[];
@@ -89,11 +92,14 @@ __global__ void __launch_bounds__(kThreads) general2d_kernel(const __grid_consta
     }
     __syncthreads();
 
-    float acc[kRows][kCols];
+    float acc[kRows][kCols], wt[kRows][kCols];
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) acc[r][c] = 0.0f;
+        for (int c = 0; c < kCols; ++c) {
+            acc[r][c] = 0.0f;
+            wt[r][c] = 1.0f;
+        }
     const float kx0 = (float)(tx * kCols), ky0 = (float)(ty * kRows);
     for (int i = 0; i < N; ++i) {
         const float shi = P.scale_hi[i], slo = P.scale_lo[i];
@@ -127,7 +133,15 @@ __global__ void __launch_bounds__(kThreads) general2d_kernel(const __grid_consta
                     cell = hashed_cell<METHOD>(s_cx[i] + (uint32_t)nx[c], s_cy[i] + (uint32_t)ny, P.key[i], P.amp[i],
                                                P.ampw[i]);
                 }
-                acc[r][c] += Model<METHOD>::eval(Model<METHOD>::row(cell, yb), xb[c]);
+                const float h = Model<METHOD>::eval(Model<METHOD>::row(cell, yb), xb[c]);
+                if (kRidged) {
+                    const float a = 1.0f - fabsf(h);
+                    const float ridge = a * a * wt[r][c];
+                    acc[r][c] = fmaf(P.wgt[i], ridge, acc[r][c]);
+                    wt[r][c] = __saturatef(2.0f * ridge);
+                } else {
+                    acc[r][c] += h;
+                }
             }
         }
     }
@@ -172,7 +186,7 @@ cudaError_t launch_general2d(const GeneralPlan& P, cudaStream_t stream)
     const size_t smem = sizeof(float4) * (size_t)P.box_words;
 #define PTG_LAUNCHG(M)                                                                               \
     do {                                                                                             \
-        auto kfn = general2d_kernel<M>;                                                              \
+        auto kfn = P.ridged ? general2d_kernel<M, true> : general2d_kernel<M, false>;                \
         cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \

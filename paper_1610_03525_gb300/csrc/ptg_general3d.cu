@@ -26,7 +26,8 @@ __device__ __forceinline__ float4 corner3(uint32_t cx, uint32_t cy, uint32_t cz,
     return make_float4(unit_value(x) * amp, unit_value(y) * ampw, unit_value(z) * ampw, unit_value(w) * ampw);
 }
 
-template <int METHOD>
+// kRidged: ridged noise, as in the 2D per-sample generator.
+template <int METHOD, bool kRidged>
 __global__ void __launch_bounds__(kThreads) general3d_kernel(const __grid_constant__ General3Plan P)
 {
     extern __shared__ float4 sm[];
@@ -66,11 +67,14 @@ __global__ void __launch_bounds__(kThreads) general3d_kernel(const __grid_consta
     }
     __syncthreads();
 
-    float acc[kRows][kCols];
+    float acc[kRows][kCols], wt[kRows][kCols];
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) acc[r][c] = 0.0f;
+        for (int c = 0; c < kCols; ++c) {
+            acc[r][c] = 0.0f;
+            wt[r][c] = 1.0f;
+        }
     const float kx0 = (float)(tx * kCols), ky0 = (float)(ty * kRows), kz = (float)tz;
     for (int i = 0; i < N; ++i) {
         const float shi = P.scale_hi[i], slo = P.scale_lo[i];
@@ -124,7 +128,15 @@ __global__ void __launch_bounds__(kThreads) general3d_kernel(const __grid_consta
                 cell.c01 = zreduce(lo[2], hi[2], zb);
                 cell.c11 = zreduce(lo[3], hi[3], zb);
                 const Row R = row_of(cell, yb.x, yb.y, yb.z);
-                acc[r][c] += eval_row(R, xb[c].x, xb[c].y, xb[c].z);
+                const float h = eval_row(R, xb[c].x, xb[c].y, xb[c].z);
+                if (kRidged) {
+                    const float a = 1.0f - fabsf(h);
+                    const float ridge = a * a * wt[r][c];
+                    acc[r][c] = fmaf(P.wgt[i], ridge, acc[r][c]);
+                    wt[r][c] = __saturatef(2.0f * ridge);
+                } else {
+                    acc[r][c] += h;
+                }
             }
         }
     }
@@ -172,7 +184,7 @@ cudaError_t launch_general3d(const General3Plan& P, cudaStream_t stream)
     const size_t smem = sizeof(float4) * (size_t)P.box_words;
 #define PTG_LAUNCHG3(M)                                                                              \
     do {                                                                                             \
-        auto kfn = general3d_kernel<M>;                                                              \
+        auto kfn = P.ridged ? general3d_kernel<M, true> : general3d_kernel<M, false>;                \
         cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \

@@ -73,15 +73,18 @@ cudaError_t launch_opensimplex3d(const Simplex3Plan& P, cudaStream_t stream);
 // (2D).  base[i] = lattice coordinate of output sample (0, 0) at octave i
 // (FP64, host); scale[i] = f^i / spc lattice units per sample, also split
 // into two floats (hi + lo) for the per-sample offsets inside a tile.
+// Ridged noise (ridged = 1): the corners carry unit amplitude (amp = 1,
+// ampw = w) and wgt[i] = p^i weights octave i's ridge.
 struct GeneralPlan {
     void* out;
     int32_t W, H, dtype, N, vec_ok, tiles_x, tiles_y, method;
     int32_t box_words;  // float4 words of shared memory for all staged corner boxes
-    int32_t pad[3];
+    int32_t ridged;
+    int32_t pad[2];
     double base_x[kMaxOctaves], base_y[kMaxOctaves];
     double scale[kMaxOctaves];
     float scale_hi[kMaxOctaves], scale_lo[kMaxOctaves];
-    float amp[kMaxOctaves], ampw[kMaxOctaves];
+    float amp[kMaxOctaves], ampw[kMaxOctaves], wgt[kMaxOctaves];
     uint32_t key[kMaxOctaves];
     int32_t box_off[kMaxOctaves];  // staged corner box of octave i: first float4 in shared memory
     int32_t box_w[kMaxOctaves];    // its side (cells + 1); 0 = hash the corners of each sample
@@ -95,11 +98,11 @@ struct General3Plan {
     void* out;
     int32_t W, H, D, dtype, N, vec_ok, tiles_x, tiles_y, tiles_z, method;
     int32_t box_words;  // float4 words of shared memory for all staged corner boxes
-    int32_t pad[1];
+    int32_t ridged;     // as in GeneralPlan
     double base[3][kMaxOctaves];  // lattice coordinate of output sample (0, 0, 0) at octave i
     double scale[kMaxOctaves];
     float scale_hi[kMaxOctaves], scale_lo[kMaxOctaves];
-    float amp[kMaxOctaves], ampw[kMaxOctaves];
+    float amp[kMaxOctaves], ampw[kMaxOctaves], wgt[kMaxOctaves];
     uint32_t key[kMaxOctaves];
     int32_t box_off[kMaxOctaves];
     int32_t box_w[3][kMaxOctaves];

@@ -86,7 +86,13 @@ def test_desc_layout_matches_header(P):
     (dict(variant=0x100), 0, 0),                      # thread shape 8 x 4
     (dict(variant=0x201), 1, 0),                      # Perlin S3, shape 16 x 2
     (dict(variant=0x300), 0, -1),                     # unknown shape bits
-    (dict(variant=0x1000), 0, -1),
+    (dict(variant=0x2000), 0, -1),
+    (dict(variant=0x1000), 0, 0),                     # ridged C1 (per-sample generator)
+    (dict(variant=0x1001), 1, 0),                     # ridged Perlin S3
+    (dict(variant=0x1000, dims=3, size=(32, 32, 32)), 0, 0),
+    (dict(variant=0x1000), 2, -2),                    # not for OpenSimplex
+    (dict(variant=0x1800, smoothness=2), 0, 0),       # coarse bits ignored when ridged
+    (dict(variant=0x1000, smoothness=4, dims=3, size=(32, 32, 32)), 0, -2),
     (dict(variant=0x800), 0, 0),                      # C1 at the tile nodes
     (dict(variant=0x801), 1, 0),                      # Perlin S3 at the tile nodes
     (dict(variant=0x800), 1, -2),                     # not Perlin S5 (degree 6)

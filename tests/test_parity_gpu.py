@@ -35,9 +35,11 @@ def ctx():
 
 def gpu_field(ctx, kind, dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 0, 0), offset=(0, 0, 0),
               seed=0, persistence=0.5, grad_weight=1.0, dtype=P.PTG_F32, shape=P.PTG_SHAPE_AUTO, coarse=0,
-              lacunarity=2.0):
+              lacunarity=2.0, ridged=False):
     smooth = SMOOTH.get(kind, P.PTG_C1)
     variant = (P.PTG_PERLIN_S3 if kind == "perlin_s3" else P.PTG_PERLIN_S5) | shape | coarse
+    if ridged:
+        variant |= P.PTG_RIDGED
     d = P.make_desc(dims=dims, size=size, spc=spc, origin=origin, offset=offset, octaves=octaves,
                     smoothness=smooth, persistence=persistence, grad_weight=grad_weight, seed=seed, dtype=dtype,
                     variant=variant, lacunarity=lacunarity)
@@ -55,14 +57,14 @@ def gpu_field(ctx, kind, dims=2, size=(256, 256), spc=64, octaves=6, origin=(0, 
 
 
 def oracle_at(kind, idx, dims=2, spc=64, octaves=6, origin=(0, 0, 0), offset=(0, 0, 0), seed=0,
-              persistence=0.5, grad_weight=1.0, lacunarity=2.0):
+              persistence=0.5, grad_weight=1.0, lacunarity=2.0, ridged=False):
     """Oracle values at sample indices idx (n, dims) of the window."""
     idx = np.asarray(idx, np.int64) + np.asarray(offset[:dims], np.int64)[None, :]
     size = (spc,) * dims
     cells = (1,) * dims
     return O.field_samples(dims, size, cells, idx, octaves=octaves, method=KIND_ORACLE[kind],
                            persistence=persistence, grad_weight=grad_weight, seed=seed, origin=origin,
-                           frequency=lacunarity)
+                           frequency=lacunarity, ridged=ridged)
 
 
 def tol32(octaves, persistence=0.5, kind="c1"):
@@ -71,8 +73,11 @@ def tol32(octaves, persistence=0.5, kind="c1"):
     to 4 each per octave, so its FP32 rounding is bounded by a larger multiple
     of the amplitude: 5e-6 x A_tot.  In 3D at most eight of the nineteen
     evaluated terms are in range (six on average), each at most
-    16 |g| |d| / 8 < 5, and the same bar holds."""
-    return (5e-6 if kind == "opensimplex" else 2e-6) * W.total_amplitude(octaves, abs(persistence))
+    16 |g| |d| / 8 < 5, and the same bar holds.  Ridged noise: the ridge
+    (1 - |h|)^2 w at most doubles an octave's rounding (|h| <= 2), and the
+    weight clamp(2 r) carries at most twice the previous ridge's: twice the
+    fBm bar, 4e-6 x A_tot (measured up to 7e-7 x A_tot)."""
+    return ({"opensimplex": 5e-6, "ridged": 4e-6}.get(kind, 2e-6)) * W.total_amplitude(octaves, abs(persistence))
 
 
 def half_ulp16(x):
@@ -347,6 +352,43 @@ def test_3d_opensimplex_windows_and_host(ctx):
     host = torch.empty(dev.shape, dtype=dev.dtype).pin_memory()
     P.ptg_generate_host(ctx, d, 2, host)
     assert torch.equal(host, dev.cpu())
+
+
+# ---------------------------------------------------------------------------
+# ridged noise (the paper's ridged mountains, Sec. 5.1), per-sample generators
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["c1", "c2", "zero_grad", "paper_gauge", "perlin_s5", "perlin_s3"])
+@pytest.mark.parametrize("size,spc,octaves,origin,f,dtype", [
+    ((256, 192), 64, 8, (0, 0, 0), 2.0, P.PTG_F32),
+    ((130, 70), 1024, 12, (-(1 << 10) + 3, 345, 0), 2.0, P.PTG_F32),   # ragged; down to on-lattice octaves
+    ((96, 64), 48, 7, (1 << 12, -5, 0), 1.8, P.PTG_F16),
+])
+def test_ridged_vs_oracle(ctx, kind, size, spc, octaves, origin, f, dtype):
+    out = gpu_field(ctx, kind, size=size, spc=spc, octaves=octaves, origin=origin, seed=19, persistence=0.6,
+                    lacunarity=f, dtype=dtype, ridged=True)
+    idx = W.grid_indices_2d(*size)
+    ref = oracle_at(kind, idx, spc=spc, octaves=octaves, origin=origin, seed=19, persistence=0.6, lacunarity=f,
+                    ridged=True)
+    err = np.abs(gather(out, idx) - ref)
+    bound = tol32(octaves, 0.6, "ridged") + (half_ulp16(ref) if dtype == P.PTG_F16 else 0.0)
+    assert np.all(err <= bound), err.max()
+
+
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5"])
+def test_ridged_3d_vs_oracle(ctx, kind):
+    size, spc, N, origin = (45, 23, 19), 16, 6, (1 << 12, -3, 77)
+    out = gpu_field(ctx, kind, dims=3, size=size, spc=spc, octaves=N, origin=origin, seed=5, ridged=True)
+    idx = W.grid_indices_3d(*size)
+    ref = oracle_at(kind, idx, dims=3, spc=spc, octaves=N, origin=origin, seed=5, ridged=True)
+    assert np.abs(gather(out, idx) - ref).max() <= tol32(N, kind="ridged")
+
+
+def test_ridged_is_not_batched(ctx):
+    d = P.make_desc(dims=2, size=(64, 64), spc=64, octaves=4, variant=P.PTG_RIDGED)
+    out = torch.empty((64, 64), device="cuda")
+    with pytest.raises(P.PtgError) as e:
+        P.ptg_batch(ctx, [d], [out])
+    assert e.value.code == P.PTG_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("kind", ["c1", "perlin_s5"])
