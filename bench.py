@@ -583,6 +583,16 @@ def main():
             dL = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, seed=0, lacunarity=1.9, **kw)
             general[name + "_f32"] = time_fn(lambda o, fn=fn, dL=dL: fn(ctx, dL, o, stream), reps=3)
         line["lacunarity_1.9"] = general
+        # ridged noise (the paper's ridged mountains), same size and octave count, per-sample generator
+        ridged = {}
+        for name, fn, kw in [("zero_gradient", P.ptg_field, dict(smoothness=P.PTG_ZERO_GRADIENT)),
+                             ("c1", P.ptg_field, dict(smoothness=P.PTG_C1)),
+                             ("perlin_s5", P.ptg_perlin, dict())]:
+            kw = dict(kw)
+            kw["variant"] = kw.get("variant", 0) | P.PTG_RIDGED
+            dR = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, seed=0, **kw)
+            ridged[name + "_f32"] = time_fn(lambda o, fn=fn, dR=dR: fn(ctx, dR, o, stream), reps=3)
+        line["ridged"] = ridged
         if rank == 0:
             line["volume3d_512_n8"] = bench_3d(P, R, ctx, stream, torch)
             line["octave_sweep"] = bench_octave_sweep(P, ctx, stream, torch)
