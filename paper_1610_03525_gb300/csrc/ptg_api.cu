@@ -178,7 +178,7 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
     int ncoarse = s - 6;
     ncoarse = ncoarse < 0 ? 0 : (ncoarse < d->octaves ? ncoarse : d->octaves);
     int coff = 0, count = 0, cend = 0;
-    double amp = 1.0;
+    double amp = 1.0, lat_bias = 0.0;
     const double p = (double)d->persistence, w = (double)d->grad_weight;
     for (int i = 0; i < d->octaves; ++i) {
         OctPlan& o = P->oct[i];
@@ -212,8 +212,10 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
         o.oz = is3d ? (uint32_t)((uint64_t)d->origin[2] << i) : 0u;
         o.amp = (float)amp;
         o.ampw = (float)(amp * w);
+        if (i >= s) lat_bias -= 3.0 * (double)o.amp;
         amp *= p;
     }
+    P->lat_bias = (float)lat_bias;
     P->ncorner = cend;
     P->ncount = count;
     P->method = method;

@@ -60,7 +60,8 @@ struct FieldPlan {
     int32_t s;              // log2(samples per cell)
     int32_t rw;             // 2D thread shape: run width 8 (8 x 4 samples a thread) or 16 (16 x 2)
     int32_t nt;             // 2D: octaves summed at the tile nodes (cells >= 64 samples), 0 = none
-    int32_t pad[3];
+    float lat_bias;         // sum over the lattice octaves of -3 amp (see unit_mant)
+    int32_t pad[2];
     OctPlan oct[kMaxOctaves];
 };
 static_assert(sizeof(FieldPlan) % 16 == 0, "FieldPlan is copied in 16-byte words");
@@ -162,6 +163,13 @@ __device__ __forceinline__ float unit_value(uint32_t u)
 {
     return __uint_as_float(0x40000000u + (u >> 9)) - 3.0f;
 }
+
+// The same float before the subtraction: unit_value(u) + 3, in [2, 4).
+__device__ __forceinline__ float unit_mant(uint32_t u) { return __uint_as_float(0x40000000u + (u >> 9)); }
+
+// a * unit_value(u) as one FMA, a m - 3a with m3a = -3a (one rounding of a
+// product and sum that are exact when 3a is a float, e.g. a a power of two).
+__device__ __forceinline__ float unit_scaled(uint32_t u, float a, float m3a) { return fmaf(unit_mant(u), a, m3a); }
 
 // ---------------------------------------------------------------------------
 // Per-axis bases.  Every method's octave term is, inside a cell,

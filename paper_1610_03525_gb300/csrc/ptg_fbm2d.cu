@@ -369,7 +369,9 @@ __device__ __forceinline__ void add_tile_grid(float (&nacc)[Shape<RW>::RR][Deg<M
     }
 }
 
-// One lattice octave: every sample sits on a lattice point.
+// One lattice octave: every sample sits on a lattice point.  Each adds
+// amp unit_mant(h) = amp (unit_value(h) + 3): the -3 amp terms of all lattice
+// octaves are added once, at the store (FieldPlan::lat_bias).
 template <int RW>
 __device__ __forceinline__ void lattice_octave(float (&acc)[Shape<RW>::RR][RW], const OctPlan& op, uint32_t jx,
                                                uint32_t jy)
@@ -384,7 +386,7 @@ __device__ __forceinline__ void lattice_octave(float (&acc)[Shape<RW>::RR][RW], 
 #pragma unroll
         for (int c = 0; c < RW; ++c) {
             const uint32_t h = pcg3d_run_value(base + (uint32_t)c * dx, y1, z1);
-            acc[r][c] = fmaf(op.amp, unit_value(h), acc[r][c]);
+            acc[r][c] = fmaf(op.amp, unit_mant(h), acc[r][c]);
         }
     }
 }
@@ -508,9 +510,14 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     if (RW == 16 && s >= 3 && s - 3 < N) small_octave<METHOD, RW, (RW == 16 ? 8 : 4)>(acc, fine, tx, ty);
     if (s >= 2 && s - 2 < N) small_octave<METHOD, RW, 4>(acc, fine, tx, ty);
     if (s >= 1 && s - 1 < N) small_octave<METHOD, RW, 2>(acc, fine, tx, ty);
-    if (METHOD != kPerlinS5 && METHOD != kPerlinS3)
+    if (METHOD != kPerlinS5 && METHOD != kPerlinS3 && s < N) {
         for (int i = s; i < N; ++i)
             lattice_octave<RW>(acc, P.oct[i], (uint32_t)(j0x + tx * RW), (uint32_t)(j0y + ty * RR));
+#pragma unroll
+        for (int r = 0; r < RR; ++r)
+#pragma unroll
+            for (int c = 0; c < RW; ++c) acc[r][c] += P.lat_bias;
+    }
     store_tile<RW>(P, acc, x0 + tx * RW, y0 + ty * RR);
 }
 

@@ -79,6 +79,7 @@ __device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int 
         const uint32_t bx = op.ox + ((uint32_t)j0x >> op.k), by = op.oy + ((uint32_t)j0y >> op.k);
         const uint32_t bz = op.oz + ((uint32_t)j0z >> op.k);
         float4* cg = corners + op.coff;
+        const float m3a = -3.0f * op.amp, m3w = -3.0f * op.ampw;
         for (int e = e0; e < n; e += step) {
             const int cz = (int)__umulhi((uint32_t)e, op.magic2);
             const int rem = e - cz * nxy;
@@ -88,9 +89,10 @@ __device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int 
             pcg4d(x, y, z, w);
             cg[(cz * op.ncy + cy) * op.rowlen + corner_slot(cx)] =
                 (METHOD == kPerlinS5 || METHOD == kPerlinS3)  // Perlin: no value, gradient unweighted
-                    ? make_float4(0.0f, unit_value(y) * op.amp, unit_value(z) * op.amp, unit_value(w) * op.amp)
-                    : make_float4(unit_value(x) * op.amp, unit_value(y) * op.ampw, unit_value(z) * op.ampw,
-                                  unit_value(w) * op.ampw);
+                    ? make_float4(0.0f, unit_scaled(y, op.amp, m3a), unit_scaled(z, op.amp, m3a),
+                                  unit_scaled(w, op.amp, m3a))
+                    : make_float4(unit_scaled(x, op.amp, m3a), unit_scaled(y, op.ampw, m3w),
+                                  unit_scaled(z, op.ampw, m3w), unit_scaled(w, op.ampw, m3w));
         }
     }
 }
@@ -182,6 +184,8 @@ __device__ __forceinline__ void small_octave3(float (&acc)[kRows][kCols], const 
     }
 }
 
+// Adds amp unit_mant(h); the -3 amp terms of all lattice octaves are added
+// once, at the store (FieldPlan::lat_bias).
 __device__ __forceinline__ void lattice_octave3(float (&acc)[kRows][kCols], const OctPlan& op, uint32_t jx,
                                                 uint32_t jy, uint32_t jz)
 {
@@ -195,7 +199,7 @@ __device__ __forceinline__ void lattice_octave3(float (&acc)[kRows][kCols], cons
 #pragma unroll
         for (int c = 0; c < kCols; ++c) {
             const uint32_t h = pcg4d_run_value(base + (uint32_t)c * dx, y1, z1, w1);
-            acc[r][c] = fmaf(op.amp, unit_value(h), acc[r][c]);
+            acc[r][c] = fmaf(op.amp, unit_mant(h), acc[r][c]);
         }
     }
 }
@@ -265,10 +269,14 @@ __global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__
         }
     if (s >= 2 && s - 2 < N) small_octave3<METHOD, 4>(acc, sm, P, s - 2, tx, ty, tz, n8);
     if (s >= 1 && s - 1 < N) small_octave3<METHOD, 2>(acc, sm, P, s - 1, tx, ty, tz, n8);
-    if (METHOD != kPerlinS5 && METHOD != kPerlinS3)  // Perlin is zero at lattice points
-        for (int i = s; i < N; ++i)
-            lattice_octave3(acc, P.oct[i], (uint32_t)(j0x + tx * kCols), (uint32_t)(j0y + ty * kRows),
-                            (uint32_t)(j0z + tz));
+    if (METHOD != kPerlinS5 && METHOD != kPerlinS3 && s < N) {  // Perlin is zero at lattice points
+        const uint32_t jx = (uint32_t)(j0x + tx * kCols), jy = (uint32_t)(j0y + ty * kRows), jz = (uint32_t)(j0z + tz);
+        for (int i = s; i < N; ++i) lattice_octave3(acc, P.oct[i], jx, jy, jz);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) acc[r][c] += P.lat_bias;
+    }
     store_tile3<OutT>(P, acc, x0 + tx * kCols, y0 + ty * kRows, z0 + tz);
 }
 

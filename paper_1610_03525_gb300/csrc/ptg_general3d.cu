@@ -21,9 +21,11 @@ __device__ __forceinline__ float4 corner3(uint32_t cx, uint32_t cy, uint32_t cz,
 {
     uint32_t x = cx, y = cy, z = cz, w = key;
     pcg4d(x, y, z, w);
+    const float m3a = -3.0f * amp, m3w = -3.0f * ampw;
     if (METHOD == kPerlinS5 || METHOD == kPerlinS3)  // Perlin: no value, gradient unweighted
-        return make_float4(0.0f, unit_value(y) * amp, unit_value(z) * amp, unit_value(w) * amp);
-    return make_float4(unit_value(x) * amp, unit_value(y) * ampw, unit_value(z) * ampw, unit_value(w) * ampw);
+        return make_float4(0.0f, unit_scaled(y, amp, m3a), unit_scaled(z, amp, m3a), unit_scaled(w, amp, m3a));
+    return make_float4(unit_scaled(x, amp, m3a), unit_scaled(y, ampw, m3w), unit_scaled(z, ampw, m3w),
+                       unit_scaled(w, ampw, m3w));
 }
 
 // kRidged: ridged noise, as in the 2D per-sample generator.

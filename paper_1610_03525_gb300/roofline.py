@@ -15,8 +15,11 @@ in RR rows (RW x RR = 8 x 4 or 16 x 2, the thread shape), with d = 3 (C1), 5
 RW samples wide ("run" octaves):
   basis tables: nrun x ((64/RW)(d+1) + 64) entries x (5 coordinate + basis
                 ops: C1 7, C2 14, Perlin-S5 9, Perlin-S3 8);
-  corners:      per staged corner 31 (pcg3d 15, three word->float maps 9,
-                three amplitude scalings 3, grid index 4);
+  corners:      per staged corner 15 for pcg3d, 3 a hash word used (shift
+                and add to a float in [2, 4), one FMA for amplitude and the
+                -3 offset; three words for the Hermite cells, two for Perlin,
+                one for the zero-gradient model) and 4 for the grid index:
+                28, 25 and 22;
   run octaves, per thread and octave: prep + RR rows x (row reduction + eval
                 at each of the d+1 node columns); once per thread, RR rows x
                 (RW - d - 1) columns x (d+1) FMA of interpolation;
@@ -34,18 +37,21 @@ RW samples wide ("run" octaves):
                 (4, 9, 4) for the Hermite cells and Perlin, (4, 4, 3) for the
                 zero-gradient model and (25, 8, 4) for the paper's D2M1N3
                 coefficients;
-  lattice octave: per sample 14 -- pcg3d word 0 of (x, y, key) with the
+  lattice octave: per sample 13 -- pcg3d word 0 of (x, y, key) with the
                 row-invariant words' LCG steps and the x-word addend y*z
                 hoisted out of the row: x's LCG step 1 (it advances by a
                 per-octave constant along the run), y and z multiply-adds 2,
-                three xorshifts 6, the final multiply-add 1; word->float 3;
-                FMA 1.  Perlin's lattice octaves are zero, no work.
+                three xorshifts 6, the final multiply-add 1; word->float 2;
+                FMA 1 (the -3 offsets of all lattice octaves are one add per
+                sample, counted once).  Perlin's lattice octaves are zero, no
+                work.
 3D tiles of 32 x 16 x 8 (each thread 8 x 4 x 1): the same regimes, with a
 reduction along z of the cell's four corner columns (32 ops) before each cell
-is used, basis tables of n8 x (4 (d+1) + 24) entries, corners 42 (pcg4d 20,
-four word->float maps 12, four scalings 4, index 6) and lattice samples 15
-(pcg4d word 0 with the row-invariant terms hoisted: 1 + 3 multiply-adds + 3
-xorshifts (6) + 1, word->float 3, FMA 1).
+is used, basis tables of n8 x (4 (d+1) + 24) entries, corners 38 (pcg4d 20,
+four words 12, index 6; Perlin three words: 35) and lattice samples 14 (pcg4d
+word 0 with the row-invariant terms hoisted: 1 + 3 multiply-adds + 3
+xorshifts (6) + 1, word->float 2, FMA 1; plus one add per sample for the
+offsets).
 OpenSimplex-style: per sample and octave 150 (4 vertices x 33 + 18).
 3D OpenSimplex-style (tiles of 32 x 16 x 8): per sample and octave 40
 (stretched position 20, reflection 12, squish 4, amplitude 4) + 19 candidate
@@ -114,7 +120,7 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8, nt: int = 
     for i, spci in st:
         k = spci.bit_length() - 1
         ncx = (63 >> min(k, 31)) + 2
-        corners += tiles * ncx * ncx * (19 if kind == "zero_grad" else 31)
+        corners += tiles * ncx * ncx * {"zero_grad": 22, "perlin_s5": 25, "perlin_s3": 25}.get(kind, 28)
         if i < nt:
             continue
         if spci >= rw:
@@ -122,7 +128,7 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8, nt: int = 
         else:
             evalops += threads * small_cell_ops(kind, rw, spci)
     n_lattice = octaves - len(st)
-    lattice = 0 if kind.startswith("perlin") else samples_padded * n_lattice * 14
+    lattice = 0 if kind.startswith("perlin") or n_lattice == 0 else samples_padded * (n_lattice * 13 + 1)
     tot = lut + corners + evalops + lattice
     return dict(total=float(tot), per_sample=tot / (w * h), lut=lut, corners=corners, eval=evalops,
                 lattice=lattice)
@@ -160,14 +166,15 @@ def lane_ops_3d(kind: str, size, spc: int, octaves: int, f: float = 2.0) -> dict
     for i, spci in st:
         k = spci.bit_length() - 1
         nc = ((31 >> min(k, 31)) + 2) * ((15 >> min(k, 31)) + 2) * ((7 >> min(k, 31)) + 2)
-        corners += tiles * nc * 42
+        corners += tiles * nc * (35 if kind.startswith("perlin") else 38)
         if spci >= 8:
             evalops += threads * (32 + 4 + 4 * (9 + 4 * (d + 1)))
         elif spci == 4:
             evalops += threads * (2 * (32 + 4 + 1 + 3 * 9) + 24 * 4 + 8)
         else:
             evalops += threads * (8 * (32 + 4 + 1 + 9) + 80)
-    lattice = 0 if kind.startswith("perlin") else samples_padded * (octaves - len(st)) * 15
+    nl = octaves - len(st)
+    lattice = 0 if kind.startswith("perlin") or nl == 0 else samples_padded * (nl * 14 + 1)
     tot = lut + corners + evalops + lattice
     return dict(total=float(tot), per_sample=tot / (w * h * dd), lut=lut, corners=corners, eval=evalops,
                 lattice=lattice)
