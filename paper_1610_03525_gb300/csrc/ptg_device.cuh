@@ -231,7 +231,10 @@ __device__ __forceinline__ float axis_t(uint32_t j, int i, int s)
 // keeps its exact rounding error (an FMA), so t is good to about 2^-23.
 __device__ __forceinline__ void lattice_split(float k, float shi, float slo, float fb, int& n, float& t)
 {
-    const float p = k * shi;
+    // __fmul_rn: the rounded product, never contracted into an FMA with a later
+    // subtraction (p - pf would then carry the product's rounding error, which
+    // e adds again)
+    const float p = __fmul_rn(k, shi);
     const float e = fmaf(k, shi, -p);  // k * shi - p, exact
     const float pf = floorf(p);
     float w = (p - pf) + fb;           // p - pf is exact

@@ -148,7 +148,7 @@ __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const
 #pragma unroll
     for (int c = 0; c < kCols; ++c) {
         const float k = (float)(tx * kCols + c);
-        cs[c] = k * step;
+        cs[c] = __fmul_rn(k, step);  // rounded and never contracted: cse carries its rounding error
         const float fl = floorf(cs[c]);
         icx[c] = (int32_t)fl;
         fxc[c] = T.fx + (cs[c] - fl);
@@ -158,7 +158,7 @@ __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
         const float k = (float)(ty * kRows + r);
-        const float rs = k * step;
+        const float rs = __fmul_rn(k, step);
         const float fl = floorf(rs);
         const int32_t iry = (int32_t)fl;
         const float fyr = T.fy + (rs - fl);
@@ -167,7 +167,7 @@ __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const
 #pragma unroll
         for (int c = 0; c < kCols; ++c) {
             const float K = cs[c] + rs;
-            const float p = K * kStretchHi;
+            const float p = __fmul_rn(K, kStretchHi);  // e carries its rounding error
             const float e = fmaf(K, kStretchHi, -p);         // exact rounding error of p
             const float ip = floorf(p);
             float t, sx, sy;

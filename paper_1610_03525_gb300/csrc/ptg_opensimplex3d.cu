@@ -160,7 +160,7 @@ __device__ __forceinline__ void simplex3_octave(float (&acc)[kRows][kCols], cons
 
     // per-axis offsets: float, integer part, fraction added to the tile base, residuals
     auto axis = [&](float k, int ax, int32_t& io, float& u, float& o, float& oe, float& be) {
-        o = k * step;
+        o = __fmul_rn(k, step);  // rounded and never contracted: oe carries its rounding error
         const float fl = floorf(o);
         io = (int32_t)fl;
         u = T.f[ax] + (o - fl);
@@ -184,7 +184,7 @@ __device__ __forceinline__ void simplex3_octave(float (&acc)[kRows][kCols], cons
             float ux, ox, oex, bex;  // recomputed per row: fewer live registers
             axis((float)(lx + 8 * c), 0, iox, ux, ox, oex, bex);
             const float K = ox + oyz;
-            const float p = K * kStretchHi;
+            const float p = __fmul_rn(K, kStretchHi);  // e carries its rounding error
             const float e = fmaf(K, kStretchHi, -p);  // exact rounding error of p
             const float ip = floorf(p);
             float s0, s1, s2;

@@ -286,6 +286,25 @@ def test_any_lacunarity_vs_oracle(ctx, kind, f, size, spc, octaves, origin):
     assert err <= tol32(octaves, 0.6, kind), err
 
 
+@pytest.mark.parametrize("kind", ["c1", "perlin_s5", "opensimplex"])
+@pytest.mark.parametrize("dims", [2, 3])
+def test_large_steps_any_frequency(ctx, kind, dims):
+    """Frequency ratio 1.8175 and spc 8 over 12 octaves at persistence 1: the
+    finest octaves step about 90 lattice units a sample, so a product's
+    rounding error (a few 1e-4 units) must be carried exactly once -- a
+    multiply contracted into an FMA with the next subtraction carries it twice
+    and shows as errors of 1e-4 per octave."""
+    size = (45, 121) if dims == 2 else (40, 21, 9)
+    origin, offset = (2216, 407, 0), (69, 99, 5)
+    out = gpu_field(ctx, kind, dims=dims, size=size, spc=8, octaves=12, origin=origin, offset=offset, seed=783621,
+                    persistence=1.0, lacunarity=1.8175)
+    idx = W.grid_indices_2d(*size) if dims == 2 else W.grid_indices_3d(*size)
+    ref = oracle_at(kind, idx, dims=dims, spc=8, octaves=12, origin=origin, offset=offset, seed=783621,
+                    persistence=1.0, lacunarity=1.8175)
+    err = np.abs(gather(out, idx) - ref).max()
+    assert err <= tol32(12, 1.0, kind), err
+
+
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "zero_grad", "opensimplex"])
 @pytest.mark.parametrize("spc,f", [(3, 2.0), (100, 2.0), (1000, 2.0), (48, 1.7)])
 def test_any_spc_vs_oracle(ctx, kind, spc, f):
