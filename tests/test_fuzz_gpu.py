@@ -21,14 +21,19 @@ DEGREE_LE4 = {"c1", "paper_gauge", "zero_grad", "perlin_s3"}
 N_CASES = 72
 
 
-def draw(idx):
-    """One random case: a dict of gpu_field keyword arguments plus the kind."""
-    rng = np.random.default_rng(20161012 + idx)
+def draw(idx, wrap=False):
+    """One random case: a dict of gpu_field keyword arguments plus the kind.
+    wrap: fused generators only (power-of-two spc, f = 2), origins anywhere in
+    the 32-bit lattice (cell indices wrap mod 2^32) and up to 24 octaves."""
+    rng = np.random.default_rng(20161012 + idx + (100000 if wrap else 0))
     dims = 3 if rng.random() < 0.3 else 2
-    kind = str(rng.choice(KINDS_3D if dims == 3 else KINDS_2D))
-    spc = int(2 ** rng.integers(0, 12)) if rng.random() < 0.6 else int(rng.integers(1, 301))
-    f = 2.0 if rng.random() < 0.7 else float(np.float32(rng.uniform(1.2, 3.5)))
-    ridged = kind != "opensimplex" and rng.random() < 0.2
+    kinds = KINDS_3D if dims == 3 else KINDS_2D
+    if wrap:
+        kinds = [k for k in kinds if k != "opensimplex"]
+    kind = str(rng.choice(kinds))
+    spc = int(2 ** rng.integers(0, 12)) if wrap or rng.random() < 0.6 else int(rng.integers(1, 301))
+    f = 2.0 if wrap or rng.random() < 0.7 else float(np.float32(rng.uniform(1.2, 3.5)))
+    ridged = kind != "opensimplex" and not wrap and rng.random() < 0.2
     if dims == 2:
         size = (int(rng.integers(1, 151)), int(rng.integers(1, 151)), 1)
     else:
@@ -42,13 +47,17 @@ def draw(idx):
         else:
             offset.append(int(rng.integers(0, 101)))
     offset += [0] * (3 - dims)
-    origin = [int(rng.integers(-(1 << 12), (1 << 12) + 1)) for _ in range(dims)] + [0] * (3 - dims)
-    # octaves: as many as keep every lattice coordinate below 2^30 (and at most 14)
-    extent = max(abs(origin[k]) + (offset[k] + size[k]) / spc for k in range(dims))
-    nmax = 1
-    while nmax < 14 and extent * f ** nmax < 2 ** 29:
-        nmax += 1
-    octaves = int(rng.integers(1, nmax + 1))
+    lim = (1 << 31) if wrap else (1 << 12)
+    origin = [int(rng.integers(-lim, lim + 1)) for _ in range(dims)] + [0] * (3 - dims)
+    if wrap:
+        octaves = int(rng.integers(1, 25))
+    else:
+        # octaves: as many as keep every lattice coordinate below 2^30 (and at most 14)
+        extent = max(abs(origin[k]) + (offset[k] + size[k]) / spc for k in range(dims))
+        nmax = 1
+        while nmax < 14 and extent * f ** nmax < 2 ** 29:
+            nmax += 1
+        octaves = int(rng.integers(1, nmax + 1))
     kw = dict(dims=dims, size=size[:dims] if dims == 3 else size[:2], spc=spc, octaves=octaves,
               origin=tuple(origin), offset=tuple(offset), seed=int(rng.integers(0, 1 << 24)),
               persistence=float(np.float32(rng.uniform(0.3, 0.9))), lacunarity=f, ridged=ridged,
@@ -73,9 +82,9 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("idx", range(N_CASES))
-def test_random_descriptor_vs_oracle(ctx, idx):
-    kind, kw = draw(idx)
+@pytest.mark.parametrize("idx,wrap", [(i, False) for i in range(N_CASES)] + [(i, True) for i in range(24)])
+def test_random_descriptor_vs_oracle(ctx, idx, wrap):
+    kind, kw = draw(idx, wrap)
     method = 2 if kind == "opensimplex" else (1 if kind.startswith("perlin") else 0)
     variant = (P.PTG_PERLIN_S3 if kind == "perlin_s3" else 0) | kw.get("shape", 0) | kw.get("coarse", 0)
     variant |= P.PTG_RIDGED if kw["ridged"] else 0
