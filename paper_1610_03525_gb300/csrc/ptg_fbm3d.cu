@@ -15,6 +15,14 @@
 // octaves whose cells are >= 8 samples wide evaluate node columns only and
 // interpolate once; cells of 4 and 2 samples use constant in-cell positions
 // along x and y; lattice octaves take one pcg4d corner value per sample.
+//
+// Tile octaves (C1): an octave whose cells are 32 samples or more covers the
+// whole tile with one cell (tiles start at multiples of min(spc, tile)), so
+// over the tile it is one polynomial of degree 3 per axis, and so is the sum
+// of all such octaves.  With two or more of them the CTA evaluates that sum
+// at 4 x 4 x 4 tile nodes ({0, 9, 22, 31} x {0, 4, 11, 15} x {0, 2, 5, 7},
+// Lebesgue constants 1.42, 1.55, 1.4) and every thread interpolates it to its
+// rows and node columns (exact for the tricubic up to rounding).
 #include "ptg_device.cuh"
 #include "ptg_eval.cuh"
 #include "ptg_kernels.h"
@@ -40,21 +48,73 @@ __device__ __forceinline__ int n_run8(const FieldPlan& P)
     return n < 0 ? 0 : (n < P.N ? n : P.N);
 }
 
+// Tile octaves (cells >= 32 samples, octaves 0 .. s - 5), used for C1 when
+// there are at least two of them; else 0.
+template <int METHOD>
+__host__ __device__ __forceinline__ int n_tile3(const FieldPlan& P)
+{
+    if (METHOD != kC1) return 0;
+    int n = P.s - 4;
+    n = n < 0 ? 0 : (n < P.N ? n : P.N);
+    return n >= 2 ? n : 0;
+}
+
+// Tile node position q along axis a (x, y, z), packed one byte each.
+__host__ __device__ constexpr int node3(int a, int q)
+{
+    return (int)(((a == 0 ? 0x1F160900u : (a == 1 ? 0x0F0B0400u : 0x07050200u)) >> (8 * q)) & 0xffu);
+}
+
+// Lagrange weight of node q at integer position p along axis a.
+__host__ __device__ constexpr float lagrange3(int a, int p, int q)
+{
+    long long num = 1, den = 1;
+    for (int m = 0; m < 4; ++m) {
+        if (m == q) continue;
+        num *= (long long)(p - node3(a, m));
+        den *= (long long)(node3(a, q) - node3(a, m));
+    }
+    return (float)((double)num / (double)den);
+}
+
+// Interpolation weights of the tile nodes: along z for each plane, along y
+// for each row, along x for each thread's node columns (x = 8 tx + node_col).
+struct alignas(16) Tile3Weights {
+    float wz[kTD][4];
+    float wy[kTH][4];
+    float wx[4][4][4];  // [tx][node column q][tile node a]
+};
+
+constexpr Tile3Weights make_tile3_weights()
+{
+    Tile3Weights W{};
+    for (int p = 0; p < kTD; ++p)
+        for (int q = 0; q < 4; ++q) W.wz[p][q] = lagrange3(2, p, q);
+    for (int p = 0; p < kTH; ++p)
+        for (int q = 0; q < 4; ++q) W.wy[p][q] = lagrange3(1, p, q);
+    for (int t = 0; t < 4; ++t)
+        for (int c = 0; c < 4; ++c)
+            for (int q = 0; q < 4; ++q) W.wx[t][c][q] = lagrange3(0, 8 * t + node_col<3>(c), q);
+    return W;
+}
+
+__device__ const Tile3Weights kTile3Weights = make_tile3_weights();
+
 template <int METHOD>
 __device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int j0x, int j0y, int j0z)
 {
     constexpr int NN = Deg<METHOD>::value + 1;
-    const int tid = threadIdx.x, s = P.s, n8 = n_run8(P);
+    const int tid = threadIdx.x, s = P.s, n8 = n_run8(P), nt = n_tile3<METHOD>(P);
     float4* xnode = sm;
     float4* ylut = sm + xnode_words3<METHOD>(n8);
     float4* zlut = ylut + n8 * 16;
     float4* corners = sm + corner_base3<METHOD>(n8);
-    for (int e = tid; e < n8 * NN * 4; e += kThreads) {
+    for (int e = tid + nt * NN * 4; e < n8 * NN * 4; e += kThreads) {  // no tables for the tile octaves
         const int i = e / (NN * 4), rem = e - i * (NN * 4);
         const int q = rem >> 2, tx = rem & 3;
         xnode[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0x + tx * 8 + node_col<Deg<METHOD>::value>(q)), i, s));
     }
-    for (int e = tid; e < n8 * 24; e += kThreads) {
+    for (int e = tid + nt * 24; e < n8 * 24; e += kThreads) {
         const int i = e / 24, slot = e - i * 24;
         if (slot < 16) {  // y: slot = r * 4 + ty, row 4 ty + r
             const int row = (slot & 3) * 4 + (slot >> 2);
@@ -117,6 +177,59 @@ __device__ __forceinline__ Cell zcell(const float4* __restrict__ cg, const OctPl
     c.c01 = r[2];
     c.c11 = r[3];
     return c;
+}
+
+// The tile octaves' sum at the 64 tile nodes, into G[(z * 4 + y) * 4 + x]:
+// two lanes a node, each taking every other octave, added by one shuffle.
+template <int METHOD>
+__device__ __forceinline__ void tile_grid3(const FieldPlan& P, const float4* __restrict__ corners, float* G, int j0x,
+                                           int j0y, int j0z, int nt)
+{
+    const int tid = threadIdx.x, node = tid >> 1, part = tid & 1;
+    const uint32_t jx = (uint32_t)(j0x + node3(0, node & 3)), jy = (uint32_t)(j0y + node3(1, (node >> 2) & 3));
+    const uint32_t jz = (uint32_t)(j0z + node3(2, node >> 4));
+    float v = 0.0f;
+    for (int i = part; i < nt; i += 2) {
+        const OctPlan& op = P.oct[i];
+        const float4 xb = axis_basis<METHOD>(axis_t(jx, i, P.s)), yb = axis_basis<METHOD>(axis_t(jy, i, P.s));
+        const float4 zb = axis_basis<METHOD>(axis_t(jz, i, P.s));
+        const Cell c = zcell(corners + op.coff, op, 0, 0, 0, zb);  // the tile's one cell of this octave
+        const Row R = row_of(c, yb.x, yb.y, yb.z);
+        v += eval_row(R, xb.x, xb.y, xb.z);
+    }
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    if (part == 0) G[node] = v;
+}
+
+// Interpolate the tile nodes to the thread's plane, rows and node columns.
+__device__ __forceinline__ void add_tile_grid3(float (&nacc)[kRows][4], const float* __restrict__ G, int tx, int ty,
+                                               int tz)
+{
+    const Tile3Weights& W = kTile3Weights;
+    const float4 wz = __ldg(reinterpret_cast<const float4*>(W.wz[tz]));
+    float hz[4][4];  // [y node][x node] in the thread's plane
+    const float4* G4 = reinterpret_cast<const float4*>(G);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const float4 g0 = G4[b], g1 = G4[4 + b], g2 = G4[8 + b], g3 = G4[12 + b];
+        hz[b][0] = fmaf(wz.w, g3.x, fmaf(wz.z, g2.x, fmaf(wz.y, g1.x, wz.x * g0.x)));
+        hz[b][1] = fmaf(wz.w, g3.y, fmaf(wz.z, g2.y, fmaf(wz.y, g1.y, wz.x * g0.y)));
+        hz[b][2] = fmaf(wz.w, g3.z, fmaf(wz.z, g2.z, fmaf(wz.y, g1.z, wz.x * g0.z)));
+        hz[b][3] = fmaf(wz.w, g3.w, fmaf(wz.z, g2.w, fmaf(wz.y, g1.w, wz.x * g0.w)));
+    }
+    float4 wx[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) wx[q] = __ldg(reinterpret_cast<const float4*>(W.wx[tx][q]));
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        const float4 wy = __ldg(reinterpret_cast<const float4*>(W.wy[ty * kRows + r]));
+        float hy[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) hy[a] = fmaf(wy.w, hz[3][a], fmaf(wy.z, hz[2][a], fmaf(wy.y, hz[1][a], wy.x * hz[0][a])));
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            nacc[r][q] = fmaf(wx[q].w, hy[3], fmaf(wx[q].z, hy[2], fmaf(wx[q].y, hy[1], fmaf(wx[q].x, hy[0], nacc[r][q]))));
+    }
 }
 
 template <int METHOD>
@@ -242,16 +355,26 @@ __global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__
     const int tid = threadIdx.x, tx = tid & 3, ty = (tid >> 2) & 3, tz = tid >> 4;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH, z0 = blockIdx.z * kTD;  // output tile
     const int j0x = x0 + P.jx0, j0y = y0 + P.jy0, j0z = z0 + P.jz0;                  // sample indices
-    const int s = P.s, N = P.N, n8 = n_run8(P);
+    const int s = P.s, N = P.N, n8 = n_run8(P), nt = n_tile3<METHOD>(P);
     stage_tile3<METHOD>(P, sm, j0x, j0y, j0z);
     __syncthreads();
+
+    // tile octaves: their sum at the tile nodes (read back after the barrier below)
+    float* G = reinterpret_cast<float*>(sm + corner_base3<METHOD>(n8) + P.ncorner);
+    if (nt > 0) tile_grid3<METHOD>(P, sm + corner_base3<METHOD>(n8), G, j0x, j0y, j0z, nt);
 
     float nacc[kRows][NN];
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
-    for (int i = 0; i < n8; ++i) run8_octave3<METHOD>(nacc, sm, P, i, tx, ty, tz, n8);
+    for (int i = nt; i < n8; ++i) run8_octave3<METHOD>(nacc, sm, P, i, tx, ty, tz, n8);
+    if constexpr (NN == 4) {
+        if (nt > 0) {  // uniform over the CTA
+            __syncthreads();
+            add_tile_grid3(nacc, G, tx, ty, tz);
+        }
+    }
     float acc[kRows][kCols];
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
@@ -285,7 +408,7 @@ size_t smem_words3(const FieldPlan& P)
 {
     int n8 = P.s - 2;
     n8 = n8 < 0 ? 0 : (n8 < P.N ? n8 : P.N);
-    return (size_t)corner_base3<METHOD>(n8) + (size_t)P.ncorner;
+    return (size_t)corner_base3<METHOD>(n8) + (size_t)P.ncorner + (n_tile3<METHOD>(P) > 0 ? 16 : 0);
 }
 
 }  // namespace

@@ -47,7 +47,9 @@ RW samples wide ("run" octaves):
                 work.
 3D tiles of 32 x 16 x 8 (each thread 8 x 4 x 1): the same regimes, with a
 reduction along z of the cell's four corner columns (32 ops) before each cell
-is used, basis tables of n8 x (4 (d+1) + 24) entries, corners 38 (pcg4d 20,
+is used; for C1 with two or more octaves of cells >= 32 samples, those are
+tile octaves: 64 nodes x nt x (3 x (coordinate + basis) + 32 + 9 + 4 + 1) + 64
+a tile and 3 x 64 FMA of interpolation a thread, no basis tables; basis tables of n8 x (4 (d+1) + 24) entries, corners 38 (pcg4d 20,
 four words 12, index 6; Perlin three words: 35) and lattice samples 14 (pcg4d
 word 0 with the row-invariant terms hoisted: 1 + 3 multiply-adds + 3
 xorshifts (6) + 1, word->float 2, FMA 1; plus one add per sample for the
@@ -160,13 +162,23 @@ def lane_ops_3d(kind: str, size, spc: int, octaves: int, f: float = 2.0) -> dict
     d = DEG[kind]
     st = _staged(spc, octaves)
     n8 = sum(1 for _, spci in st if spci >= 8)
-    lut = tiles * n8 * (4 * (d + 1) + 24) * (COORD_OPS + BASIS_OPS[kind])
+    # C1 tile octaves (cells >= 32 samples) when there are two or more
+    nt = sum(1 for _, spci in st if spci >= 32) if kind == "c1" else 0
+    nt = nt if nt >= 2 else 0
+    lut = tiles * (n8 - nt) * (4 * (d + 1) + 24) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
     evalops = threads * 4 * (7 - d) * (d + 1)
+    if nt:
+        # 64 nodes x nt octaves x (3 axes of coordinate + basis, z reduction 32,
+        # row 9, evaluation 4, accumulate 1), one shuffle-add a node; per thread
+        # 3 x 64 FMA of interpolation (z, y, x)
+        evalops += tiles * (64 * nt * (3 * (COORD_OPS + BASIS_OPS[kind]) + 32 + 9 + 4 + 1) + 64) + threads * 192
     for i, spci in st:
         k = spci.bit_length() - 1
         nc = ((31 >> min(k, 31)) + 2) * ((15 >> min(k, 31)) + 2) * ((7 >> min(k, 31)) + 2)
         corners += tiles * nc * (35 if kind.startswith("perlin") else 38)
+        if i < nt:
+            continue
         if spci >= 8:
             evalops += threads * (32 + 4 + 4 * (9 + 4 * (d + 1)))
         elif spci == 4:
