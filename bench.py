@@ -151,18 +151,33 @@ def profile_traffic():
         return None
 
 
-def oracle_sample_rate(rows: int, seed: int = 0):
+def oracle_sample_rate(rows: int, seed: int = 0, threads: int = 0):
     """Oracle throughput on `rows` distinct full rows of the workload, evenly
-    spread over the field.  Returns (samples/s, samples, seconds, threads)."""
+    spread over the field, on `threads` host threads (0 = all).  Returns
+    (samples/s, samples, seconds, threads)."""
     import numpy as np
     import oracle as O
     ys = np.unique(np.linspace(0, SIZE[1] - 1, max(1, rows)).astype(np.int64))
     idx = np.concatenate([np.stack([np.arange(SIZE[0]), np.full(SIZE[0], y)], 1) for y in ys]).astype(np.int64)
     O.lib()
     t0 = time.perf_counter()
-    O.field_samples(2, (SPC, SPC), (1, 1), idx, octaves=OCTAVES, method=O.C1, seed=seed, persistence=0.5)
+    O.field_samples(2, (SPC, SPC), (1, 1), idx, octaves=OCTAVES, method=O.C1, seed=seed, persistence=0.5,
+                    nthreads=threads)
     dt = time.perf_counter() - t0
-    return idx.shape[0] / dt, idx.shape[0], dt, O.num_threads()
+    return idx.shape[0] / dt, idx.shape[0], dt, threads if threads > 0 else O.num_threads()
+
+
+def oracle_small_fields():
+    """The oracle on the whole 256^2, 6-octave, spc-64 field (C1, Perlin S5,
+    OpenSimplex), all host threads: seconds and samples/s of each."""
+    import oracle as O
+    res = {}
+    for name, method in [("c1", O.C1), ("perlin_s5", O.PERLIN_S5), ("opensimplex", O.OPENSIMPLEX)]:
+        t0 = time.perf_counter()
+        O.field_grid(2, (256, 256), (4, 4), octaves=6, method=method, seed=0, persistence=0.5)
+        dt = time.perf_counter() - t0
+        res[name] = {"seconds": round(dt, 4), "gsamples_s": 256 * 256 / dt / 1e9}
+    return res
 
 
 def bench_3d(P, R, ctx, stream, torch, reps=10):
@@ -619,6 +634,10 @@ def main():
             line["cpu_baseline"] = {"value": rate / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
                                     "sample": "%d full rows (%d samples) of the 8192^2 field, %.1f s" % (
                                         args.cpu_rows, n, dtc)}
+            rate1, n1, dt1, _ = oracle_sample_rate(max(1, args.cpu_rows // 16), threads=1)
+            line["cpu_baseline"]["single_core"] = {"value": rate1 / 1e9, "unit": UNIT,
+                                                   "sample": "%d samples, %.1f s" % (n1, dt1)}
+            line["cpu_baseline"]["field_256_n6"] = oracle_small_fields()
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
