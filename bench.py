@@ -210,6 +210,34 @@ def bench_3d(P, R, ctx, stream, torch, reps=10):
     return res
 
 
+def bench_small_field(P, ctx, stream, torch, reps=500):
+    """The 256^2, 6-octave, spc-64 field (FP32): device time per field over
+    back-to-back launches, and the host time of one ptg_* call (argument
+    checks, plan, launch)."""
+    out = torch.empty((256, 256), dtype=torch.float32, device="cuda")
+    res = {"workload": "2D 256^2, 6 octaves, spc 64 (4x4 base cells), FP32, %d launches back to back" % reps}
+    for name, fn, kw in [("c1", P.ptg_field, dict(smoothness=P.PTG_C1)),
+                         ("perlin_s5", P.ptg_perlin, dict()),
+                         ("opensimplex", P.ptg_opensimplex, dict())]:
+        d = P.make_desc(dims=2, size=(256, 256), spc=64, octaves=6, seed=0, **kw)
+        for _ in range(10):
+            fn(ctx, d, out, stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record(stream)
+        for _ in range(reps):
+            fn(ctx, d, out, stream)
+        b.record(stream)
+        host_us = (time.perf_counter() - t0) / reps * 1e6
+        torch.cuda.synchronize()
+        us = a.elapsed_time(b) / reps * 1e3
+        res[name] = {"us_per_field": round(us, 2), "host_us_per_call": round(host_us, 2),
+                     "gsamples_s": 256 * 256 / us / 1e3}
+    del out
+    return res
+
+
 def bench_octave_sweep(P, ctx, stream, torch, octaves=(1, 2, 4, 6, 8, 10, 12), reps=5):
     """Time per 8192^2 field against the octave count N (spc 1024: octaves
     10 and 11 sit on lattice points), per method -- the GPU counterpart of the
@@ -610,6 +638,7 @@ def main():
         line["ridged"] = ridged
         if rank == 0:
             line["volume3d_512_n8"] = bench_3d(P, R, ctx, stream, torch)
+            line["field_256_n6"] = bench_small_field(P, ctx, stream, torch)
             line["octave_sweep"] = bench_octave_sweep(P, ctx, stream, torch)
             line["batched"] = bench_batched(P, ctx, stream, torch)
             line["serving"] = bench_serving(P, torch, duration_s=args.serve_seconds)
