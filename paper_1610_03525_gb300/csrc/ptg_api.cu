@@ -378,6 +378,7 @@ int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, voi
         P->ampw[i] = P->ridged ? (float)w : (float)(amp * w);
         P->wgt[i] = (float)amp;
         P->key[i] = (d->seed << 8) | (uint32_t)i;
+        if (f == 2.0 && s >= 0 && i >= s) P->lattice_mask |= 1u << i;  // integer lattice coordinates
         // stage the corners of the cells a tile spans while cells cover two or
         // more samples: one cell before the base cell, floor(63 scale) + 1
         // after it, one more for rounding, and the corner past the last cell
@@ -419,6 +420,7 @@ int ptg_make_general3_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, vo
     const double spc = (double)d->spc, f = (double)d->lacunarity;
     const double p = (double)d->persistence, w = (double)d->grad_weight;
     const int ext[3] = {kTile3dX - 1, kTile3dY - 1, kTile3dZ - 1};
+    const int spc_log2 = log2_exact(d->spc);
     double amp = 1.0;
     int box = 0;
     for (int i = 0; i < d->octaves; ++i) {
@@ -432,6 +434,7 @@ int ptg_make_general3_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, vo
         P->ampw[i] = P->ridged ? (float)w : (float)(amp * w);
         P->wgt[i] = (float)amp;
         P->key[i] = (d->seed << 8) | (uint32_t)i;
+        if (f == 2.0 && spc_log2 >= 0 && i >= spc_log2) P->lattice_mask |= 1u << i;  // integer lattice coordinates
         if (scale <= 0.5) {  // one cell before the base cell, ext * scale + 1 after it, one for rounding, +1 corner
             int bw[3];
             for (int a = 0; a < 3; ++a) bw[a] = (int)std::floor(ext[a] * scale) + 5;

@@ -51,6 +51,19 @@ __device__ __forceinline__ Cell hashed_cell(uint32_t cx, uint32_t cy, uint32_t k
 // kRidged: each octave adds wgt_i r with r = (1 - |h|)^2 w, w the clamped
 // doubled ridge of the octave before (1 at octave 0); otherwise the octave
 // value (its amplitude already in the corner data).
+template <bool kRidged>
+__device__ __forceinline__ void add_octave(float& acc, float& wt, float h, float wgt)
+{
+    if (kRidged) {
+        const float a = 1.0f - fabsf(h);
+        const float ridge = a * a * wt;
+        acc = fmaf(wgt, ridge, acc);
+        wt = __saturatef(2.0f * ridge);
+    } else {
+        acc += h;
+    }
+}
+
 template <int METHOD, bool kRidged>
 __global__ void __launch_bounds__(kThreads) general2d_kernel(const __grid_constant__ GeneralPlan P)
 {
@@ -104,6 +117,34 @@ __global__ void __launch_bounds__(kThreads) general2d_kernel(const __grid_consta
     for (int i = 0; i < N; ++i) {
         const float shi = P.scale_hi[i], slo = P.scale_lo[i];
         const int w = P.box_w[i];
+        if ((P.lattice_mask >> i) & 1u) {
+            // every sample sits on a lattice point (ridged fields with spc a power
+            // of two): the octave is the corner value, one hash word a sample
+            // (Perlin: zero)
+            int nx[kCols];
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) {
+                float t;
+                lattice_split(kx0 + (float)c, shi, slo, s_fx[i], nx[c], t);
+            }
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                int ny;
+                float t;
+                lattice_split(ky0 + (float)r, shi, slo, s_fy[i], ny, t);
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) {
+                    float h = 0.0f;
+                    if (METHOD != kPerlinS5 && METHOD != kPerlinS3) {
+                        uint32_t x = s_cx[i] + (uint32_t)nx[c], y = s_cy[i] + (uint32_t)ny, z = P.key[i];
+                        pcg3d(x, y, z);
+                        h = corner_data<METHOD>(x, y, z, P.amp[i], P.ampw[i]).x;
+                    }
+                    add_octave<kRidged>(acc[r][c], wt[r][c], h, P.wgt[i]);
+                }
+            }
+            continue;
+        }
         const float4* box = sm + P.box_off[i];
         int nx[kCols];
         float4 xb[kCols];
@@ -133,15 +174,8 @@ __global__ void __launch_bounds__(kThreads) general2d_kernel(const __grid_consta
                     cell = hashed_cell<METHOD>(s_cx[i] + (uint32_t)nx[c], s_cy[i] + (uint32_t)ny, P.key[i], P.amp[i],
                                                P.ampw[i]);
                 }
-                const float h = Model<METHOD>::eval(Model<METHOD>::row(cell, yb), xb[c]);
-                if (kRidged) {
-                    const float a = 1.0f - fabsf(h);
-                    const float ridge = a * a * wt[r][c];
-                    acc[r][c] = fmaf(P.wgt[i], ridge, acc[r][c]);
-                    wt[r][c] = __saturatef(2.0f * ridge);
-                } else {
-                    acc[r][c] += h;
-                }
+                add_octave<kRidged>(acc[r][c], wt[r][c], Model<METHOD>::eval(Model<METHOD>::row(cell, yb), xb[c]),
+                                    P.wgt[i]);
             }
         }
     }

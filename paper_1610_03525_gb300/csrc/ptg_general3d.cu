@@ -28,6 +28,21 @@ __device__ __forceinline__ float4 corner3(uint32_t cx, uint32_t cy, uint32_t cz,
                        unit_scaled(w, ampw, m3w));
 }
 
+// Adds one octave's value h to a sample's sum: plain, or (kRidged) the ridge
+// (1 - |h|)^2 w weighted by wgt, w then the clamped doubled ridge.
+template <bool kRidged>
+__device__ __forceinline__ void add_octave3(float& acc, float& wt, float h, float wgt)
+{
+    if (kRidged) {
+        const float a = 1.0f - fabsf(h);
+        const float ridge = a * a * wt;
+        acc = fmaf(wgt, ridge, acc);
+        wt = __saturatef(2.0f * ridge);
+    } else {
+        acc += h;
+    }
+}
+
 // kRidged: ridged noise, as in the 2D per-sample generator.
 template <int METHOD, bool kRidged>
 __global__ void __launch_bounds__(kThreads) general3d_kernel(const __grid_constant__ General3Plan P)
@@ -81,6 +96,28 @@ __global__ void __launch_bounds__(kThreads) general3d_kernel(const __grid_consta
     for (int i = 0; i < N; ++i) {
         const float shi = P.scale_hi[i], slo = P.scale_lo[i];
         const int wx = P.box_w[0][i], wy = P.box_w[1][i], wz = P.box_w[2][i];
+        if ((P.lattice_mask >> i) & 1u) {
+            // every sample sits on a lattice point: the corner value (Perlin: zero)
+            int nx[kCols], nz;
+            float t;
+            lattice_split(kz, shi, slo, s_f[2][i], nz, t);
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) lattice_split(kx0 + (float)c, shi, slo, s_f[0][i], nx[c], t);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                int ny;
+                lattice_split(ky0 + (float)r, shi, slo, s_f[1][i], ny, t);
+#pragma unroll
+                for (int c = 0; c < kCols; ++c) {
+                    float h = 0.0f;
+                    if (METHOD != kPerlinS5 && METHOD != kPerlinS3)
+                        h = corner3<METHOD>(s_c[0][i] + (uint32_t)nx[c], s_c[1][i] + (uint32_t)ny,
+                                            s_c[2][i] + (uint32_t)nz, P.key[i], P.amp[i], P.ampw[i]).x;
+                    add_octave3<kRidged>(acc[r][c], wt[r][c], h, P.wgt[i]);
+                }
+            }
+            continue;
+        }
         const float4* box = sm + P.box_off[i];
         int nx[kCols], nz;
         float4 xb[kCols], zb;
@@ -130,15 +167,7 @@ __global__ void __launch_bounds__(kThreads) general3d_kernel(const __grid_consta
                 cell.c01 = zreduce(lo[2], hi[2], zb);
                 cell.c11 = zreduce(lo[3], hi[3], zb);
                 const Row R = row_of(cell, yb.x, yb.y, yb.z);
-                const float h = eval_row(R, xb[c].x, xb[c].y, xb[c].z);
-                if (kRidged) {
-                    const float a = 1.0f - fabsf(h);
-                    const float ridge = a * a * wt[r][c];
-                    acc[r][c] = fmaf(P.wgt[i], ridge, acc[r][c]);
-                    wt[r][c] = __saturatef(2.0f * ridge);
-                } else {
-                    acc[r][c] += h;
-                }
+                add_octave3<kRidged>(acc[r][c], wt[r][c], eval_row(R, xb[c].x, xb[c].y, xb[c].z), P.wgt[i]);
             }
         }
     }

@@ -80,7 +80,8 @@ struct GeneralPlan {
     int32_t W, H, dtype, N, vec_ok, tiles_x, tiles_y, method;
     int32_t box_words;  // float4 words of shared memory for all staged corner boxes
     int32_t ridged;
-    int32_t pad[2];
+    uint32_t lattice_mask;  // bit i: every sample of octave i is a lattice point (integer coordinates)
+    int32_t pad;
     double base_x[kMaxOctaves], base_y[kMaxOctaves];
     double scale[kMaxOctaves];
     float scale_hi[kMaxOctaves], scale_lo[kMaxOctaves];
@@ -99,6 +100,8 @@ struct General3Plan {
     int32_t W, H, D, dtype, N, vec_ok, tiles_x, tiles_y, tiles_z, method;
     int32_t box_words;  // float4 words of shared memory for all staged corner boxes
     int32_t ridged;     // as in GeneralPlan
+    uint32_t lattice_mask;  // as in GeneralPlan
+    int32_t pad;
     double base[3][kMaxOctaves];  // lattice coordinate of output sample (0, 0, 0) at octave i
     double scale[kMaxOctaves];
     float scale_hi[kMaxOctaves], scale_lo[kMaxOctaves];
