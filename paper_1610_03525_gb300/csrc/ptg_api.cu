@@ -258,10 +258,10 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
     for (int i = 0; i < d->octaves; ++i) {
         const double scale = f == 2.0 ? std::ldexp(1.0, i) : std::pow(f, (double)i);
         const double step = scale / spc;
-        // stage the tile's vertex gradients while the lattice is coarser than
+        // stage the tile's vertex gradients while the lattice is no finer than
         // the samples; the box side is bounded by 64 step + 7 vertices
         P->box_wb[i] = 0;
-        if (step < 1.0) {
+        if (step <= 1.0) {
             const int wb = (int)std::floor(64.0 * step * 1.0001) + 8;
             if ((size_t)(box + wb * wb) * 8 <= (size_t)96 * 1024) {
                 P->box_off[i] = box;

@@ -40,6 +40,10 @@
 namespace ptg {
 namespace {
 
+// Thread layout: the 32 lanes of a warp cover an 8 x 4 block of samples at a
+// time (lane = x + 8 y), so that the gradients they gather from a staged box at
+// one instruction lie close together.  A thread takes the columns lx + 8 c
+// (c < 8) and the rows 16 w + ly + 4 r (r < 4) of warp w's 16 rows.
 constexpr int kTW = 64, kTH = 64, kThreads = 128, kCols = 8, kRows = 4;
 constexpr float kSquish = 0.36602540378443865f;   // (sqrt(3) - 1) / 2
 constexpr double kStretchD = -0.21132486540518713; // (1/sqrt(3) - 1) / 2
@@ -125,7 +129,7 @@ __device__ __forceinline__ float sample_noise(const Grad<kStaged>& G, int32_t a,
 // two, so the offsets k * step and their sums are exact floats.
 template <bool kStaged, bool kExact>
 __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const SimplexPlan& P, const TileOctave T,
-                                               const float2* boxes, int i, int tx, int ty)
+                                               const float2* boxes, int i, int lx, int ly0)
 {
     const float step = P.step[i], step_lo = P.step_lo[i], amp = P.amp[i] * kScale;
     Grad<kStaged> G;
@@ -147,7 +151,7 @@ __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const
     int32_t icx[kCols];
 #pragma unroll
     for (int c = 0; c < kCols; ++c) {
-        const float k = (float)(tx * kCols + c);
+        const float k = (float)(lx + 8 * c);
         cs[c] = __fmul_rn(k, step);  // rounded and never contracted: cse carries its rounding error
         const float fl = floorf(cs[c]);
         icx[c] = (int32_t)fl;
@@ -157,7 +161,7 @@ __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const
     }
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
-        const float k = (float)(ty * kRows + r);
+        const float k = (float)(ly0 + 4 * r);
         const float rs = __fmul_rn(k, step);
         const float fl = floorf(rs);
         const int32_t iry = (int32_t)fl;
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
 {
     __shared__ TileOctave tile[kMaxOctaves];
     extern __shared__ float2 boxes[];
-    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    const int tid = threadIdx.x, lx = tid & 7, ly0 = ((tid >> 5) << 4) | ((tid >> 3) & 3);
     const int j0x = blockIdx.x * kTW, j0y = blockIdx.y * kTH;
     if (tid < P.N) {
         const int i = tid;
@@ -255,35 +259,23 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
     for (int i = 0; i < P.N; ++i) {
         const bool exact = kAllExact || ((P.exact_mask >> i) & 1u);
         if (P.box_wb[i] > 0) {
-            if (exact) simplex_octave<true, true>(acc, P, tile[i], boxes, i, tx, ty);
-            else simplex_octave<true, kAllExact>(acc, P, tile[i], boxes, i, tx, ty);
+            if (exact) simplex_octave<true, true>(acc, P, tile[i], boxes, i, lx, ly0);
+            else simplex_octave<true, kAllExact>(acc, P, tile[i], boxes, i, lx, ly0);
         } else {
-            if (exact) simplex_octave<false, true>(acc, P, tile[i], boxes, i, tx, ty);
-            else simplex_octave<false, kAllExact>(acc, P, tile[i], boxes, i, tx, ty);
+            if (exact) simplex_octave<false, true>(acc, P, tile[i], boxes, i, lx, ly0);
+            else simplex_octave<false, kAllExact>(acc, P, tile[i], boxes, i, lx, ly0);
         }
     }
     OutT* out = reinterpret_cast<OutT*>(P.out);
-    const int x0 = j0x + tx * kCols, y0 = j0y + ty * kRows;
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
-        const int y = y0 + r;
+        const int y = j0y + ly0 + 4 * r;
         if (y >= P.H) break;
         OutT* row = out + (size_t)y * (size_t)P.W;
-        if (P.vec_ok && x0 + kCols <= P.W) {
-            if (sizeof(OutT) == 4) {
-                float4* p = reinterpret_cast<float4*>(row + x0);
-                p[0] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-                p[1] = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
-            } else {
-                __half2 hh[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) hh[q] = __floats2half2_rn(acc[r][2 * q], acc[r][2 * q + 1]);
-                *reinterpret_cast<uint4*>(row + x0) = *reinterpret_cast<const uint4*>(hh);
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < kCols; ++c)
-                if (x0 + c < P.W) store1(row + x0 + c, acc[r][c]);
+        for (int c = 0; c < kCols; ++c) {
+            const int x = j0x + lx + 8 * c;
+            if (x < P.W) store1(row + x, acc[r][c]);
         }
     }
 }
