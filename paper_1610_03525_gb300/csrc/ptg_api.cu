@@ -379,11 +379,11 @@ int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, voi
         P->wgt[i] = (float)amp;
         P->key[i] = (d->seed << 8) | (uint32_t)i;
         if (f == 2.0 && s >= 0 && i >= s) P->lattice_mask |= 1u << i;  // integer lattice coordinates
-        // stage the corners of the cells a tile spans while cells cover two or
-        // more samples: one cell before the base cell, floor(63 scale) + 1
+        // stage the corners of the cells a tile spans while cells cover at
+        // least one sample: one cell before the base cell, floor(63 scale) + 1
         // after it, one more for rounding, and the corner past the last cell
         P->box_w[i] = 0;
-        if (scale <= 0.5) {
+        if (scale <= 1.0 && !((P->lattice_mask >> i) & 1u)) {  // lattice octaves read one corner a sample
             const int bw = (int)std::floor(63.0 * scale) + 5;
             if ((size_t)(box + bw * bw) * sizeof(float4) <= (size_t)96 * 1024) {
                 P->box_off[i] = box;
