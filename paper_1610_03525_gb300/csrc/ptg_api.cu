@@ -242,8 +242,6 @@ int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int 
     P->tiles_x = (P->W + kTile2dX - 1) / kTile2dX;
     P->tiles_y = (P->H + kTile2dY - 1) / kTile2dY;
     if (P->tiles_y > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall for one launch");
-    const int esz = d->dtype == PTG_F16 ? 2 : 4;
-    P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
     (void)s;
     const double spc = (double)d->spc, f = (double)d->lacunarity;
     double lim = 0.0;
@@ -299,8 +297,6 @@ int ptg_make_simplex3_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int
     P->tiles_y = (P->H + kTile3dY - 1) / kTile3dY;
     P->tiles_z = (P->D + kTile3dZ - 1) / kTile3dZ;
     if (P->tiles_y > 65535 || P->tiles_z > 65535) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall");
-    const int esz = d->dtype == PTG_F16 ? 2 : 4;
-    P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
     const double spc = (double)d->spc, f = (double)d->lacunarity;
     double lim = 0.0;
     for (int k = 0; k < 3; ++k) {

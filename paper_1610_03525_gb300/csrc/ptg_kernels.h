@@ -36,7 +36,7 @@ cudaError_t launch_fbm3d(const FieldPlan& P, int method, int s, cudaStream_t str
 // (step_lo = 0 when the step is a power of two).
 struct SimplexPlan {
     void* out;
-    int32_t W, H, dtype, N, vec_ok, tiles_x, tiles_y;
+    int32_t W, H, dtype, N, tiles_x, tiles_y;
     double base_x[kMaxOctaves], base_y[kMaxOctaves];
     double step_d[kMaxOctaves];
     float step[kMaxOctaves];
@@ -57,10 +57,9 @@ cudaError_t launch_opensimplex2d(const SimplexPlan& P, cudaStream_t stream);
 // float4; box_w[k][i] bounds the box extent along axis k (0 = hash per sample).
 struct Simplex3Plan {
     void* out;
-    int32_t W, H, D, dtype, N, vec_ok, tiles_x, tiles_y, tiles_z;
+    int32_t W, H, D, dtype, N, tiles_x, tiles_y, tiles_z;
     int32_t box_words;
     uint32_t exact_mask;  // bit i: step[i] is a power of two (products k * step exact)
-    int32_t pad;
     double base[3][kMaxOctaves];
     double step_d[kMaxOctaves];
     float step[kMaxOctaves], step_lo[kMaxOctaves], amp[kMaxOctaves];
