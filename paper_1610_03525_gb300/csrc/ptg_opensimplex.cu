@@ -16,10 +16,11 @@
 // branch-free (max(0, 2 - r^2)).
 //
 // Gradient staging: for octaves whose lattice spacing is at least a sample
-// (2^i < spc), the CTA hashes every vertex of the stretched-plane box that its
-// 64 x 64 tile can touch into shared memory once; samples then read their four
-// gradients.  Finer octaves hash the four vertices per sample directly.  The
-// tile spans L = 64 2^i / spc lattice units in real space, i.e.
+// (up to one lattice unit a sample, while the boxes fit in 96 KB), the CTA
+// hashes every vertex of the stretched-plane box that its 64 x 64 tile can
+// touch into shared memory once; samples then read their four gradients.
+// Finer octaves hash the four vertices per sample directly.  The tile spans
+// L = 64 x (lattice units a sample) in real space, i.e.
 // [s0 + r L, s0 + (1 + r) L] in each stretched coordinate (s0 the tile's first
 // sample); two vertices of margin below and three above cover the extra
 // vertices (offsets -1..2) and rounding.
