@@ -123,3 +123,32 @@ def test_unknown_request():
         assert e.value.code == P.PTG_ERR_INVALID
     finally:
         ctx.close()
+
+
+def test_per_sample_requests_in_the_mix():
+    """Ridged fields, other frequency ratios and spc that are not powers of
+    two go through the request loop too (the per-sample generators), with the
+    same values as a direct call."""
+    ctx = _ctx(budget=256 << 20)
+    try:
+        descs = [P.make_desc(dims=2, size=(300, 200), spc=100, octaves=7, seed=1),
+                 P.make_desc(dims=2, size=(256, 256), spc=64, octaves=9, seed=2, variant=P.PTG_RIDGED),
+                 P.make_desc(dims=2, size=(128, 96), spc=1024, octaves=12, seed=3, lacunarity=1.9),
+                 P.make_desc(dims=3, size=(40, 24, 16), spc=16, octaves=6, seed=4, lacunarity=1.7),
+                 P.make_desc(dims=3, size=(64, 32, 16), spc=16, octaves=6, seed=5, smoothness=P.PTG_C2,
+                             variant=P.PTG_RIDGED)]
+        alone = []
+        for d in descs:
+            o = _buf(d)
+            P.ptg_field(ctx, d, o)
+            alone.append(o)
+        torch.cuda.synchronize()
+        outs = [_buf(d) for d in descs]
+        ids = [P.ptg_submit(ctx, d, o) for d, o in zip(descs, outs)]
+        for i in ids:
+            assert P.ptg_wait(ctx, i, 30_000_000_000) == P.PTG_OK
+            assert P.ptg_poll(ctx, i)[0] == P.PTG_OK
+        for o, a in zip(outs, alone):
+            assert torch.equal(o, a)
+    finally:
+        ctx.close()
