@@ -528,3 +528,24 @@ def test_invalid_arguments_write_nothing(ctx, kw, code):
     assert e.value.code == code
     torch.cuda.synchronize()
     assert bool((out == 7.0).all())
+
+
+@pytest.mark.parametrize("dims,size", [(2, (65536, 34000)), (3, (1024, 1024, 2100))])
+def test_beyond_2g_elements(ctx, dims, size):
+    """Fields of more than 2^31 elements (FP16, about 4.4 GB): 64-bit output
+    offsets; samples from the first and last rows / planes against the oracle."""
+    n = int(np.prod(size))
+    assert n > 2**31
+    out = gpu_field(ctx, "c1", dims=dims, size=size, spc=1024 if dims == 2 else 128, octaves=8, seed=3,
+                    dtype=P.PTG_F16)
+    rng = np.random.default_rng(dims)
+    k = 4096
+    idx = np.stack([rng.integers(0, s, k) for s in size[:-1]] +
+                   [np.concatenate([rng.integers(0, 8, k // 2), size[-1] - 1 - rng.integers(0, 8, k // 2)])], 1)
+    ti = torch.from_numpy(idx.astype(np.int64)).cuda()
+    sel = out[ti[:, 1], ti[:, 0]] if dims == 2 else out[ti[:, 2], ti[:, 1], ti[:, 0]]  # gathered on the device
+    got = sel.float().cpu().numpy().astype(np.float64)
+    ref = oracle_at("c1", idx, dims=dims, spc=1024 if dims == 2 else 128, octaves=8, seed=3)
+    assert np.all(np.abs(got - ref) <= tol32(8) + half_ulp16(ref))
+    del out
+    torch.cuda.empty_cache()
