@@ -154,6 +154,29 @@ __global__ void __launch_bounds__(kThreads) general2d_kernel(const __grid_consta
             lattice_split(kx0 + (float)c, shi, slo, s_fx[i], nx[c], t);
             xb[c] = axis_basis<METHOD>(t);
         }
+        if (w > 0 && nx[0] == nx[kCols - 1]) {
+            // the thread's run lies in one cell: collapse each row once (per
+            // thread, so warps diverge only where a run crosses a cell edge)
+            const int lx = min(max(nx[0] + 1, 0), w - 2);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                int ny;
+                float t;
+                lattice_split(ky0 + (float)r, shi, slo, s_fy[i], ny, t);
+                const int ly = min(max(ny + 1, 0), w - 2);
+                const float4* p = box + ly * w + lx;
+                Cell cell;
+                cell.c00 = p[0];
+                cell.c10 = p[1];
+                cell.c01 = p[w];
+                cell.c11 = p[w + 1];
+                const Row R = Model<METHOD>::row(cell, axis_basis<METHOD>(t));
+#pragma unroll
+                for (int c = 0; c < kCols; ++c)
+                    add_octave<kRidged>(acc[r][c], wt[r][c], Model<METHOD>::eval(R, xb[c]), P.wgt[i]);
+            }
+            continue;
+        }
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
             int ny;

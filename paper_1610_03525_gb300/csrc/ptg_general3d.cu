@@ -132,6 +132,31 @@ __global__ void __launch_bounds__(kThreads) general3d_kernel(const __grid_consta
             lattice_split(kx0 + (float)c, shi, slo, s_f[0][i], nx[c], t);
             xb[c] = axis_basis<METHOD>(t);
         }
+        if (wx > 0 && nx[0] == nx[kCols - 1]) {
+            // the thread's run lies in one cell: reduce it along z and collapse
+            // each row once (per thread: warps diverge only at cell edges)
+            const int lx = min(max(nx[0] + 1, 0), wx - 2), lz = min(max(nz + 1, 0), wz - 2);
+            const int plane = wx * wy;
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                int ny;
+                float t;
+                lattice_split(ky0 + (float)r, shi, slo, s_f[1][i], ny, t);
+                const float4 yb = axis_basis<METHOD>(t);
+                const int ly = min(max(ny + 1, 0), wy - 2);
+                const float4* p = box + (lz * wy + ly) * wx + lx;
+                Cell cell;
+                cell.c00 = zreduce(p[0], p[plane], zb);
+                cell.c10 = zreduce(p[1], p[plane + 1], zb);
+                cell.c01 = zreduce(p[wx], p[plane + wx], zb);
+                cell.c11 = zreduce(p[wx + 1], p[plane + wx + 1], zb);
+                const Row R = row_of(cell, yb.x, yb.y, yb.z);
+#pragma unroll
+                for (int c = 0; c < kCols; ++c)
+                    add_octave3<kRidged>(acc[r][c], wt[r][c], eval_row(R, xb[c].x, xb[c].y, xb[c].z), P.wgt[i]);
+            }
+            continue;
+        }
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
             int ny;
