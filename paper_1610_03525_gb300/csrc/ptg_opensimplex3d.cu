@@ -15,9 +15,10 @@
 // (sum u)^2.  Where sum xi <= 3/2, the vertices that can be within sqrt(2)
 // are the nineteen offsets delta with entries in -1..2 listed in kCand (the
 // cube corner 0, the three unit steps, the three pairs, the three double
-// steps, and the nine mixed ones); they were found by minimising r^2 over
-// that half of the cube for every delta in -2..3 and keeping those with a
-// minimum below 2.  The other half maps onto this one by the point
+// steps, and the nine mixed ones); they were found by minimising r^2 exactly
+// over that half of the cube (a convex quadratic on a polytope, solved over
+// every set of active faces) for every delta in -3..4 and keeping those with
+// a minimum below 2; the list is the same for sum xi <= 1.6.  The other half maps onto this one by the point
 // reflection xi -> 1 - xi, delta -> 1 - delta, which flips the sign of every
 // displacement and so of every term.  Nineteen vertices per sample and
 // octave, all evaluated (max(0, 2 - r^2) is zero out of range), with no
