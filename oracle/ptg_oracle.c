@@ -10,7 +10,9 @@
  * What it computes (each function cites the passage it follows):
  *   - a counter-based lattice hash (pcg3d / pcg4d, Jarzynski & Olano,
  *     "Hash Functions for GPU Rendering", JCGT 9(3), 2020) giving each lattice
- *     corner a value and a gradient in [-1, 1);
+ *     corner a value and a gradient in [-1, 1).  The paper fixes no hash and no
+ *     published test vectors are at hand: parity unpinned for the hash's exact
+ *     words (its pins are statistical: uniform, uncorrelated, avalanche);
  *   - the fixed-point sample -> (cell, fraction) map of every octave (Sec. 2.1
  *     unit cell, Sec. 4 octave frequencies);
  *   - the corner constraint system of Eq. (mixedderiv) / Eq. (polynomial),
