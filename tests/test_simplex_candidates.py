@@ -72,3 +72,56 @@ def test_reflection_covers_the_upper_half():
         inr = (u * u).sum(1) + u.sum(1) ** 2 < 2.0
         if inr.any():
             assert any(np.array_equal(1 - np.array(d), c) for c in cand), d
+
+
+def _min_r2_2d(d, A, b):
+    """Exact minimum of |x - d|^2 + (sum(x - d))^2 over {x : A x <= b} in 2D
+    (the 2D squish (sqrt(3) - 1)/2 makes 2q + 2q^2 = 1)."""
+    H = 2.0 * (np.eye(2) + np.ones((2, 2)))
+    best = np.inf
+    for n in range(3):
+        for act in itertools.combinations(range(len(b)), n):
+            Aa, ba = A[list(act)], b[list(act)]
+            K = np.block([[H, Aa.T], [Aa, np.zeros((n, n))]]) if n else H
+            rhs = np.concatenate([H @ d, ba]) if n else H @ d
+            try:
+                x = np.linalg.solve(K, rhs)[:2]
+            except np.linalg.LinAlgError:
+                continue
+            if np.all(A @ x <= b + 1e-12):
+                u = x - d
+                best = min(best, u @ u + u.sum() ** 2)
+    return best
+
+
+def test_2d_vertex_choice_is_complete():
+    """The 2D kernel takes the three vertices of the point's triangle and one
+    more: across the edge opposite the vertex of smallest barycentric weight.
+    Over each of the six regions (two triangles x three smallest weights) every
+    vertex that can come within sqrt(2) must be among those four."""
+    sq = np.sqrt(3.0)
+    assert abs(2 * ((sq - 1) / 2) + 2 * ((sq - 1) / 2) ** 2 - 1.0) < 1e-15
+    # lower triangle xi + yi <= 1: weights (wc, wx, wy) = (1 - x - y, x, y); upper: (x + y - 1, 1 - y, 1 - x)
+    tri = {
+        "lower": (np.array([[-1.0, 0.0], [0.0, -1.0], [1.0, 1.0]]), np.array([0.0, 0.0, 1.0]),
+                  lambda x, y: (1 - x - y, x, y), [(1, 0), (0, 1), (0, 0)],
+                  {0: (1, 1), 1: (-1, 1), 2: (1, -1)}),
+        "upper": (np.array([[1.0, 0.0], [0.0, 1.0], [-1.0, -1.0]]), np.array([1.0, 1.0, -1.0]),
+                  lambda x, y: (x + y - 1, 1 - y, 1 - x), [(1, 0), (0, 1), (1, 1)],
+                  {0: (0, 0), 1: (0, 2), 2: (2, 0)}),
+    }
+    # weights as affine functions w = g . (x, y) + h, to write "w_m <= w_n" as a face
+    lin = {"lower": [(np.array([-1.0, -1.0]), 1.0), (np.array([1.0, 0.0]), 0.0), (np.array([0.0, 1.0]), 0.0)],
+           "upper": [(np.array([1.0, 1.0]), -1.0), (np.array([0.0, -1.0]), 1.0), (np.array([-1.0, 0.0]), 1.0)]}
+    for name, (A0, b0, _, verts, extra) in tri.items():
+        for m in range(3):  # region where weight m is the smallest
+            A, b = [*A0], [*b0]
+            for n in range(3):
+                if n != m:  # w_m - w_n <= 0
+                    A.append(lin[name][m][0] - lin[name][n][0])
+                    b.append(lin[name][n][1] - lin[name][m][1])
+            A, b = np.array(A), np.array(b)
+            chosen = set(verts) | {extra[m]}
+            for d in itertools.product(range(-3, 5), repeat=2):
+                if _min_r2_2d(np.array(d, float), A, b) < 2.0 - 1e-9:
+                    assert d in chosen, (name, m, d)
