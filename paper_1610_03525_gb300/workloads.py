@@ -43,9 +43,12 @@ def grid_indices_3d(w: int, h: int, d: int) -> np.ndarray:
     return np.stack([xs.ravel(), ys.ravel(), zs.ravel()], 1)
 
 
-def subsample(size, every: int, n_random: int, seed: int = 12345) -> np.ndarray:
+def subsample(size, every: int, n_random: int, seed: int = 12345, lattice_spc: int = 0) -> np.ndarray:
     """Deterministic parity subset of a large field: every `every`-th row
-    (2D) or plane (3D) in full, plus n_random uniformly drawn samples."""
+    (2D) or plane (3D) in full, plus n_random uniformly drawn samples, plus
+    (lattice_spc > 0) the samples on the base lattice's lines: every column
+    x = 0 mod lattice_spc in 2D, every line along z at x, y = 0 mod
+    lattice_spc in 3D."""
     dims = len(size)
     rng = np.random.default_rng(seed)
     parts = []
@@ -53,11 +56,19 @@ def subsample(size, every: int, n_random: int, seed: int = 12345) -> np.ndarray:
         w, h = size
         for y in range(0, h, every):
             parts.append(np.stack([np.arange(w, dtype=np.int64), np.full(w, y, np.int64)], 1))
+        if lattice_spc > 0:
+            for x in range(0, w, lattice_spc):
+                parts.append(np.stack([np.full(h, x, np.int64), np.arange(h, dtype=np.int64)], 1))
     else:
         w, h, d = size
         for z in range(0, d, every):
             ys, xs = np.meshgrid(np.arange(h, dtype=np.int64), np.arange(w, dtype=np.int64), indexing="ij")
             parts.append(np.stack([xs.ravel(), ys.ravel(), np.full(xs.size, z, np.int64)], 1))
+        if lattice_spc > 0:
+            for y in range(0, h, lattice_spc):
+                for x in range(0, w, lattice_spc):
+                    parts.append(np.stack([np.full(d, x, np.int64), np.full(d, y, np.int64),
+                                           np.arange(d, dtype=np.int64)], 1))
     rnd = np.stack([rng.integers(0, size[k], n_random, dtype=np.int64) for k in range(dims)], 1)
     parts.append(rnd)
     return np.concatenate(parts, 0)

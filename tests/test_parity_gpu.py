@@ -438,7 +438,8 @@ def test_any_lacunarity_fp16_host_and_chunks(ctx, kind):
 def test_sampled_8192_n12(ctx, kind, seed, dtype):
     cfg = W.CONFIGS["2d_8192_n12"]
     out = gpu_field(ctx, kind, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"], seed=seed, dtype=dtype)
-    idx = W.subsample(cfg["size"], every=1024, n_random=1 << 15, seed=seed)
+    # every 64th row, 2^20 random samples and the base lattice's columns
+    idx = W.subsample(cfg["size"], every=64, n_random=1 << 20, seed=seed, lattice_spc=cfg["spc"])
     ref = oracle_at(kind, idx, spc=cfg["spc"], octaves=cfg["octaves"], seed=seed)
     err = np.abs(gather(out, idx) - ref)
     bound = tol32(cfg["octaves"], kind=kind) + (half_ulp16(ref) if dtype == P.PTG_F16 else 0.0)
@@ -453,7 +454,8 @@ def test_sampled_3d_512_n8(ctx, kind):
     cfg = W.CONFIGS["3d_512_n8"]
     out = gpu_field(ctx, kind, dims=3, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"],
                     origin=cfg["origin"], seed=0, dtype=P.PTG_F16)
-    idx = W.subsample(cfg["size"], every=256, n_random=1 << 15, seed=1)
+    # every 64th plane, 2^20 random samples and the base lattice's lines along z
+    idx = W.subsample(cfg["size"], every=64, n_random=1 << 20, seed=1, lattice_spc=cfg["spc"])
     ref = oracle_at(kind, idx, dims=3, spc=cfg["spc"], octaves=cfg["octaves"], origin=cfg["origin"], seed=0)
     err = np.abs(gather(out, idx) - ref)
     assert np.all(err <= tol32(cfg["octaves"], kind=kind) + half_ulp16(ref)), err.max()
