@@ -102,7 +102,7 @@ __device__ __forceinline__ float4 hashed_grad(int32_t a, int32_t b, int32_t c, u
 // Sum of the nineteen candidates' terms for a point at stretched fraction
 // (x0, x1, x2) of vertex (a, b, c); the caller multiplies by the amplitude.
 template <bool kStaged>
-__device__ __forceinline__ float sample_noise(const float4* __restrict__ box, int bsx, int bsy, int bsz, int bsize,
+__device__ __forceinline__ float sample_noise(const float4* __restrict__ box, int bsx, int bsy, int bsize,
                                               const TileOctave3& T, uint32_t key, int32_t a, int32_t b, int32_t c,
                                               float x0, float x1, float x2)
 {
@@ -144,7 +144,6 @@ __device__ __forceinline__ float sample_noise(const float4* __restrict__ box, in
         }
         sum = fmaf(k2 * k2, fmaf(g.x, d0, fmaf(g.y, d1, g.z * d2)), sum);
     }
-    (void)bsz;
     return s * sum;
 }
 
@@ -157,7 +156,7 @@ __device__ __forceinline__ void simplex3_octave(float (&acc)[kRows][kCols], cons
 {
     const float step = P.step[i], step_lo = P.step_lo[i], amp = P.amp[i] * kScale;
     const uint32_t key = P.key[i];
-    const int bsx = T.bw[0], bsy = T.bw[1], bsz = T.bw[2], bsize = bsx * bsy * bsz;
+    const int bsx = T.bw[0], bsy = T.bw[1], bsize = bsx * bsy * T.bw[2];
 
     // per-axis offsets: float, integer part, fraction added to the tile base, residuals
     auto axis = [&](float k, int ax, int32_t& io, float& u, float& o, float& oe, float& be) {
@@ -210,7 +209,7 @@ __device__ __forceinline__ void simplex3_octave(float (&acc)[kRows][kCols], cons
             const int32_t a = T.a0[0] + iox + iip + (int32_t)f0;
             const int32_t b = T.a0[1] + ioy + iip + (int32_t)f1;
             const int32_t cc = T.a0[2] + ioz + iip + (int32_t)f2;
-            acc[r][c] = fmaf(amp, sample_noise<kStaged>(box, bsx, bsy, bsz, bsize, T, key, a, b, cc, s0 - f0,
+            acc[r][c] = fmaf(amp, sample_noise<kStaged>(box, bsx, bsy, bsize, T, key, a, b, cc, s0 - f0,
                                                         s1 - f1, s2 - f2),
                              acc[r][c]);
         }
