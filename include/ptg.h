@@ -135,7 +135,8 @@ typedef struct {
     float lacunarity;     /* frequency ratio f between octaves, in [1, 16]
                              (Sec. 4: frequency f^i at octave i).  f = 2 runs
                              the fused generators; any other f runs a
-                             per-sample generator (2D, or 3D C1/C2/Perlin)
+                             per-sample generator (2D, or 3D C1/C2/Perlin;
+                             OpenSimplex takes any f in 2D and 3D)
                              in which the lattice
                              coordinate (origin + (offset + j)/spc) f^i is
                              formed per tile in FP64 and must stay below 2^30
