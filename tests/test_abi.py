@@ -122,3 +122,28 @@ def test_create_without_gpu_fails_cleanly(P):
         pytest.skip("GPU present")
     with pytest.raises(P.PtgError):
         P.ptg_create(0)
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: the header compiles as strict C99 (no C++ or
+    torch types), and as C++ with C linkage."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "ptg.h"\n'
+                   "int main(void) {\n"
+                   "    ptg_ctx* c = 0;\n"
+                   "    ptg_field_desc d;\n"
+                   "    d.struct_size = (uint32_t)sizeof d;\n"
+                   "    return ptg_create(&c, 0, 0) + (int)d.struct_size;\n"
+                   "}\n")
+    flags = ["-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only", "-I", os.path.dirname(HEADER)]
+    r = subprocess.run([cc, "-std=c99", *flags, str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    cxx = shutil.which("g++")
+    if cxx:
+        r = subprocess.run([cxx, "-std=c++17", "-x", "c++", *flags, str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
