@@ -1,4 +1,4 @@
-// ptg_opensimplex3d.cu -- OpenSimplex-style 3D gradient noise: the
+// ptg_opensimplex3d.cuh -- OpenSimplex-style 3D gradient noise: the
 // simplex-lattice comparison point of Thorimbert & Chopard (arXiv:1610.03525,
 // Sec. 1, 5.1, 5.2) carried to three dimensions, the 3D baseline their
 // conclusion asks for, with the same fractal sum (Sec. 4).
@@ -37,6 +37,8 @@
 // of K r_hi recovered by an FMA, and integer parts are removed before
 // fractions are summed.  Steps that are not powers of two also carry the
 // rounding residuals of every offset and sum (two-sums), as in 2D.
+#pragma once
+
 #include <cstdint>
 
 #include "ptg_device.cuh"
@@ -301,28 +303,26 @@ __global__ void __launch_bounds__(kThreads, 4) opensimplex3d_kernel(const __grid
     }
 }
 
-}  // namespace
-
-cudaError_t launch_opensimplex3d(const Simplex3Plan& P, cudaStream_t stream)
+// One kernel instance: OutT is float or __half; kAllExact as above.  Each
+// instance is compiled in a translation unit of its own
+// (ptg_opensimplex3d_{f32,f16}[_dyadic].cu), which keeps the build parallel.
+template <typename OutT, bool kAllExact>
+cudaError_t launch_instance(const Simplex3Plan& P, cudaStream_t stream)
 {
     const dim3 grid(P.tiles_x, P.tiles_y, P.tiles_z);
     const size_t smem = sizeof(float4) * (size_t)P.box_words;
-    const bool all_exact = P.exact_mask == (P.N >= 32 ? 0xffffffffu : (1u << P.N) - 1u);
-#define PTG_LAUNCHOS3(T, X)                                                                          \
-    do {                                                                                             \
-        auto kfn = opensimplex3d_kernel<T, X>;                                                       \
-        cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
-        if (e != cudaSuccess) return e;                                                              \
-        kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
-        return cudaGetLastError();                                                                   \
-    } while (0)
-    if (P.dtype == 1) {
-        if (all_exact) PTG_LAUNCHOS3(__half, true);
-        PTG_LAUNCHOS3(__half, false);
-    }
-    if (all_exact) PTG_LAUNCHOS3(float, true);
-    PTG_LAUNCHOS3(float, false);
-#undef PTG_LAUNCHOS3
+    auto kfn = opensimplex3d_kernel<OutT, kAllExact>;
+    const cudaError_t e = set_kernel_smem((const void*)kfn, smem);
+    if (e != cudaSuccess) return e;
+    kfn<<<grid, kThreads, smem, stream>>>(P);
+    return cudaGetLastError();
 }
+
+}  // namespace
+
+cudaError_t launch_opensimplex3d_f32(const Simplex3Plan& P, cudaStream_t stream);
+cudaError_t launch_opensimplex3d_f32_dyadic(const Simplex3Plan& P, cudaStream_t stream);
+cudaError_t launch_opensimplex3d_f16(const Simplex3Plan& P, cudaStream_t stream);
+cudaError_t launch_opensimplex3d_f16_dyadic(const Simplex3Plan& P, cudaStream_t stream);
 
 }  // namespace ptg

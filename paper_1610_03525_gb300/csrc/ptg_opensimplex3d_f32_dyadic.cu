@@ -1,0 +1,12 @@
+// ptg_opensimplex3d_f32_dyadic.cu -- the FP32 instance of the 3D OpenSimplex-style
+// generator (ptg_opensimplex3d.cuh) for fields whose every octave step is a power of two.
+#include "ptg_opensimplex3d.cuh"
+
+namespace ptg {
+
+cudaError_t launch_opensimplex3d_f32_dyadic(const Simplex3Plan& P, cudaStream_t stream)
+{
+    return launch_instance<float, true>(P, stream);
+}
+
+}  // namespace ptg

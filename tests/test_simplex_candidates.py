@@ -14,7 +14,7 @@ import re
 
 import numpy as np
 
-SRC = os.path.join(os.path.dirname(__file__), "..", "paper_1610_03525_gb300", "csrc", "ptg_opensimplex3d.cu")
+SRC = os.path.join(os.path.dirname(__file__), "..", "paper_1610_03525_gb300", "csrc", "ptg_opensimplex3d.cuh")
 
 
 def kernel_candidates():
