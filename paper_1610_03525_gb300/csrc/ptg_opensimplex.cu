@@ -44,7 +44,9 @@ namespace {
 // Thread layout: the 32 lanes of a warp cover an 8 x 4 block of samples at a
 // time (lane = x + 8 y), so that the gradients they gather from a staged box at
 // one instruction lie close together.  A thread takes the columns lx + 8 c
-// (c < 8) and the rows 16 w + ly + 4 r (r < 4) of warp w's 16 rows.
+// (c < 8) and the rows 16 w + ly + 4 r (r < 4) of warp w's 16 rows, one row at
+// a time through all octaves: the row loop stays rolled, so that the octave
+// bodies (8 samples x 4 vertices each) fit the instruction cache.
 constexpr int kTW = 64, kTH = 64, kThreads = 128, kCols = 8, kRows = 4;
 constexpr float kSquish = 0.36602540378443865f;   // (sqrt(3) - 1) / 2
 constexpr double kStretchD = -0.21132486540518713; // (1/sqrt(3) - 1) / 2
@@ -126,11 +128,11 @@ __device__ __forceinline__ float sample_noise(const Grad<kStaged>& G, int32_t a,
            vertex_at(G, a, b, d3, d3, xi, yi) + vertex_at(G, a, b, ex, ey, xi, yi);
 }
 
-// One octave for the thread's 4 x 8 samples.  kExact: the step is a power of
-// two, so the offsets k * step and their sums are exact floats.
+// One octave for the thread's 8 samples of tile row ly.  kExact: the step is
+// a power of two, so the offsets k * step and their sums are exact floats.
 template <bool kStaged, bool kExact>
-__device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const SimplexPlan& P, const TileOctave T,
-                                               const float2* boxes, int i, int lx, int ly0)
+__device__ __forceinline__ void simplex_row(float (&acc)[kCols], const SimplexPlan& P, const TileOctave T,
+                                            const float2* boxes, int i, int lx, int ly)
 {
     const float step = P.step[i], step_lo = P.step_lo[i], amp = P.amp[i] * kScale;
     Grad<kStaged> G;
@@ -160,43 +162,40 @@ __device__ __forceinline__ void simplex_octave(float (&acc)[kRows][kCols], const
         cse[c] = kExact ? 0.0f : fmaf(k, step, -cs[c]) + k * step_lo;
         cbe[c] = kExact ? 0.0f : two_sum_err(T.fx, cs[c] - fl, fxc[c]) + T.fxl;
     }
+    const float k = (float)ly;
+    const float rs = __fmul_rn(k, step);
+    const float fl = floorf(rs);
+    const int32_t iry = (int32_t)fl;
+    const float fyr = T.fy + (rs - fl);
+    const float rse = kExact ? 0.0f : fmaf(k, step, -rs) + k * step_lo;
+    const float rbe = kExact ? 0.0f : two_sum_err(T.fy, rs - fl, fyr) + T.fyl;
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-        const float k = (float)(ly0 + 4 * r);
-        const float rs = __fmul_rn(k, step);
-        const float fl = floorf(rs);
-        const int32_t iry = (int32_t)fl;
-        const float fyr = T.fy + (rs - fl);
-        const float rse = kExact ? 0.0f : fmaf(k, step, -rs) + k * step_lo;
-        const float rbe = kExact ? 0.0f : two_sum_err(T.fy, rs - fl, fyr) + T.fyl;
-#pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-            const float K = cs[c] + rs;
-            const float p = __fmul_rn(K, kStretchHi);  // e carries its rounding error
-            const float e = fmaf(K, kStretchHi, -p);         // exact rounding error of p
-            const float ip = floorf(p);
-            float t, sx, sy;
-            if (kExact) {
-                t = (p - ip) + (e + K * kStretchLo);
-                sx = fxc[c] + t;
-                sy = fyr + t;
-            } else {
-                const float Ke = two_sum_err(cs[c], rs, K) + (cse[c] + rse);  // K's error and product residuals
-                const float small = e + fmaf(Ke, kStretchHi, K * kStretchLo);
-                const float pt = p - ip;  // exact
-                t = pt + small;
-                const float te = two_sum_err(pt, small, t);
-                const float ux = fxc[c] + t, uy = fyr + t;
-                sx = ux + (two_sum_err(fxc[c], t, ux) + (te + (cse[c] + cbe[c])));
-                sy = uy + (two_sum_err(fyr, t, uy) + (te + (rse + rbe)));
-            }
-            const float flx = floorf(sx), fly = floorf(sy);
-            const float xi = sx - flx, yi = sy - fly;
-            const int32_t iip = (int32_t)ip;
-            const int32_t a = T.a0 + icx[c] + iip + (int32_t)flx;
-            const int32_t b = T.b0 + iry + iip + (int32_t)fly;
-            acc[r][c] = fmaf(amp, sample_noise(G, a, b, xi, yi), acc[r][c]);
+    for (int c = 0; c < kCols; ++c) {
+        const float K = cs[c] + rs;
+        const float p = __fmul_rn(K, kStretchHi);  // e carries its rounding error
+        const float e = fmaf(K, kStretchHi, -p);         // exact rounding error of p
+        const float ip = floorf(p);
+        float t, sx, sy;
+        if (kExact) {
+            t = (p - ip) + (e + K * kStretchLo);
+            sx = fxc[c] + t;
+            sy = fyr + t;
+        } else {
+            const float Ke = two_sum_err(cs[c], rs, K) + (cse[c] + rse);  // K's error and product residuals
+            const float small = e + fmaf(Ke, kStretchHi, K * kStretchLo);
+            const float pt = p - ip;  // exact
+            t = pt + small;
+            const float te = two_sum_err(pt, small, t);
+            const float ux = fxc[c] + t, uy = fyr + t;
+            sx = ux + (two_sum_err(fxc[c], t, ux) + (te + (cse[c] + cbe[c])));
+            sy = uy + (two_sum_err(fyr, t, uy) + (te + (rse + rbe)));
         }
+        const float flx = floorf(sx), fly = floorf(sy);
+        const float xi = sx - flx, yi = sy - fly;
+        const int32_t iip = (int32_t)ip;
+        const int32_t a = T.a0 + icx[c] + iip + (int32_t)flx;
+        const int32_t b = T.b0 + iry + iip + (int32_t)fly;
+        acc[c] = fmaf(amp, sample_noise(G, a, b, xi, yi), acc[c]);
     }
 }
 
@@ -251,32 +250,29 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
     }
     __syncthreads();
 
-    float acc[kRows][kCols];
-#pragma unroll
-    for (int r = 0; r < kRows; ++r)
-#pragma unroll
-        for (int c = 0; c < kCols; ++c) acc[r][c] = 0.0f;
-
-    for (int i = 0; i < P.N; ++i) {
-        const bool exact = kAllExact || ((P.exact_mask >> i) & 1u);
-        if (P.box_wb[i] > 0) {
-            if (exact) simplex_octave<true, true>(acc, P, tile[i], boxes, i, lx, ly0);
-            else simplex_octave<true, kAllExact>(acc, P, tile[i], boxes, i, lx, ly0);
-        } else {
-            if (exact) simplex_octave<false, true>(acc, P, tile[i], boxes, i, lx, ly0);
-            else simplex_octave<false, kAllExact>(acc, P, tile[i], boxes, i, lx, ly0);
-        }
-    }
     OutT* out = reinterpret_cast<OutT*>(P.out);
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < kRows; ++r) {
-        const int y = j0y + ly0 + 4 * r;
-        if (y >= P.H) break;
+        const int ly = ly0 + 4 * r, y = j0y + ly;
+        if (y >= P.H) break;  // rows grow with r; no barrier follows
+        float acc[kCols];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) acc[c] = 0.0f;
+        for (int i = 0; i < P.N; ++i) {
+            const bool exact = kAllExact || ((P.exact_mask >> i) & 1u);
+            if (P.box_wb[i] > 0) {
+                if (exact) simplex_row<true, true>(acc, P, tile[i], boxes, i, lx, ly);
+                else simplex_row<true, kAllExact>(acc, P, tile[i], boxes, i, lx, ly);
+            } else {
+                if (exact) simplex_row<false, true>(acc, P, tile[i], boxes, i, lx, ly);
+                else simplex_row<false, kAllExact>(acc, P, tile[i], boxes, i, lx, ly);
+            }
+        }
         OutT* row = out + (size_t)y * (size_t)P.W;
 #pragma unroll
         for (int c = 0; c < kCols; ++c) {
             const int x = j0x + lx + 8 * c;
-            if (x < P.W) store1(row + x, acc[r][c]);
+            if (x < P.W) store1(row + x, acc[c]);
         }
     }
 }

@@ -2,8 +2,8 @@
 
     python -m paper_1610_03525_gb300.profile --kind c1 --size 8192 8192 --spc 1024 --octaves 12 --reps 3
 
-Kinds: c1, c2, perlin_s5, perlin_s3, opensimplex (2D), c1/c2 with three sizes
-for 3D.  No timing is done here; numbers come from the profiler.
+Kinds: c1, c2, perlin_s5, perlin_s3, opensimplex; three sizes make a 3D
+volume.  No timing is done here; numbers come from the profiler.
 """
 from __future__ import annotations
 
