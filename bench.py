@@ -616,6 +616,7 @@ def main():
                                                  "paper_d2m1n3_f32": "paper_gauge",
                                                  "opensimplex_f32": "opensimplex"}[k], SIZE, SPC,
                                                 OCTAVES, rw_k, nt_k)["per_sample"]
+            v["alu_frac"] = v["ops_per_sample"] * n_samples / (v["ms"] / 1e3) / peak
         line["baselines"] = extras
         # any frequency ratio between octaves (per-sample generator), same size and octave count
         general = {}
