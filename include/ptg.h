@@ -120,7 +120,12 @@ typedef enum { PTG_COARSE_AUTO = 0, PTG_COARSE_RUNS = 0x400, PTG_COARSE_TILE = 0
 typedef struct {
     uint32_t struct_size; /* sizeof(ptg_field_desc)                            */
     int32_t dims;         /* 2 or 3                                            */
-    int64_t size[3];      /* samples per axis (x, y, z), each in [1, 2^30]; unused = 1 */
+    int64_t size[3];      /* samples per axis (x, y, z), each in [1, 2^30]; unused = 1.
+                             One device launch covers at most 65535 tiles
+                             along the slowest axis: H <= 4194240 (2D, 64-row
+                             tiles), D <= 524280 (3D, 8-plane tiles), else
+                             PTG_ERR_UNSUPPORTED; ptg_generate_host has no
+                             such bound (it works in bands)                 */
     int64_t spc;          /* samples per base cell, in [1, 2^30]; a value
                              that is not a power of two runs the per-sample
                              generators (see lacunarity)                    */
