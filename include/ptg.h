@@ -258,8 +258,8 @@ int ptg_submit(ptg_ctx* ctx, const ptg_field_desc* desc, void* out, uint64_t* re
  * ts_ns (may be NULL) = submit, admit, start and end times in ns of a
  * monotonic host clock (0 where not reached yet).  End is when the request
  * loop saw the request complete; start is end minus the device time between
- * timing events recorded around the request's kernels (not before admit).  Returns PTG_OK or
- * PTG_ERR_INVALID (unknown id). */
+ * timing events recorded around the request's kernels (not before admit).
+ * Returns PTG_OK or PTG_ERR_INVALID (unknown id). */
 int ptg_poll(ptg_ctx* ctx, uint64_t req_id, ptg_status* st, uint64_t ts_ns[4]);
 
 /* Wait at most timeout_ns for a request; returns its final status or
