@@ -54,7 +54,10 @@ four words 12, index 6; Perlin three words: 35) and lattice samples 14 (pcg4d
 word 0 with the row-invariant terms hoisted: 1 + 3 multiply-adds + 3
 xorshifts (6) + 1, word->float 2, FMA 1; plus one add per sample for the
 offsets).
-OpenSimplex-style: per sample and octave 150 (4 vertices x 33 + 18).
+OpenSimplex-style: per sample and octave 150 (4 vertices x 33 + 18), a flat
+count not split into staged and hashed octaves; on the 8192^2, 12-octave field
+it exceeds the executed instruction count (1800 against 1675 a sample), so
+fractions taken from it are upper estimates.
 3D OpenSimplex-style (tiles of 32 x 16 x 8): per sample and octave 40
 (stretched position 20, reflection 12, squish 4, amplitude 4) + 19 candidate
 vertices x 14 (displacement 3, r^2 3, kernel 4, g . d 3, accumulate 1); a
