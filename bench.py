@@ -662,8 +662,9 @@ def main():
         if rank == 0 and world == 1:
             rate, n, dtc, threads = oracle_sample_rate(args.cpu_rows)
             line["cpu_baseline"] = {"value": rate / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                    "sample": "%d full rows (%d samples) of the 8192^2 field, %.1f s" % (
-                                        args.cpu_rows, n, dtc)}
+                                    "sample": "%d full rows (%d samples) of the 8192^2 field, %.1f s on %d "
+                                              "threads (%.0f core-seconds)" % (args.cpu_rows, n, dtc, threads,
+                                                                               dtc * threads)}
             rate1, n1, dt1, _ = oracle_sample_rate(max(1, args.cpu_rows // 16), threads=1)
             line["cpu_baseline"]["single_core"] = {"value": rate1 / 1e9, "unit": UNIT,
                                                    "sample": "%d samples, %.1f s" % (n1, dt1)}
