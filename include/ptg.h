@@ -236,8 +236,9 @@ int ptg_batch_free(ptg_batch_plan* plan);
  * real-time loop in which cudaMalloc's implicit device synchronisation would
  * stall every other stream.  Same fields, outputs and results as ptg_batch,
  * but the launch plans and the work counter live in one fixed device array
- * inside the library (file-scope, at most 256 fields, about 450 KB, held by
- * every device that loads the library until the process exits) instead of
+ * inside the library (file-scope, at most 256 fields; 256 x 2016-byte field
+ * plans + 257 x 8-byte tile offsets + an 8-byte counter = 518,160 bytes, held
+ * by every device that loads the library until the process exits) instead of
  * context-owned allocations; no cudaMalloc, cudaFree or other allocator is
  * called.  The caller owns every output buffer.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress); make that first
@@ -338,6 +339,16 @@ int ptg_debug_hash(ptg_ctx* ctx, int32_t dims, const uint32_t* keys, int64_t n, 
  * admitted request's stream wait on the host (never on the device) until
  * hold = 0 is set or 5 s pass, simulating a stalled device. */
 int ptg_debug_hold(ptg_ctx* ctx, int32_t hold);
+
+/* Failure-injection hook for memory exhaustion, on the host.  Of the device
+ * or pinned-host allocations the library makes next for this context (staging
+ * of ptg_generate_host, ptg_batch buffers, prepared batches, the box-count
+ * pyramid, the autotune field), the first `after` succeed and the following n
+ * fail as if memory were exhausted: the call that needed them frees what it
+ * had allocated, returns PTG_ERR_NOMEM and writes nothing.  n = 0 turns the
+ * injection off.  A failed allocation is never attempted, so no GPU fault is
+ * involved.  Negative arguments return PTG_ERR_INVALID. */
+int ptg_debug_fail_alloc(ptg_ctx* ctx, int32_t after, int32_t n);
 
 /* Cell index and in-cell position of n sample indices j (device int64) on
  * one axis at octave i, with the generators' fixed-point map:

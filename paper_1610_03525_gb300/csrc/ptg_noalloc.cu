@@ -29,6 +29,9 @@ struct NoAllocScratch {
     long long tiles[kNoAllocMaxFields + 1];
     unsigned long long counter;
 };
+// 256 x sizeof(FieldPlan) + 257 x 8 + 8 bytes: the footprint the header states.
+static_assert(sizeof(FieldPlan) == 2016, "FieldPlan changed size: update the stated footprint");
+static_assert(sizeof(NoAllocScratch) == 518160, "scratch footprint changed: update the stated size");
 
 // Host staging of the plans.  A pageable source of cudaMemcpyAsync is consumed
 // before the call returns, so it is free again right after the copies.
@@ -39,13 +42,14 @@ void* g_dev_addr[kMaxDevices];
 }  // namespace
 
 // The scratch array: 256 field plans, their tile offsets and the work counter
-// (about 450 KB on each device that loads the library).
+// (518,160 bytes, about 506 KiB, on each device that loads the library).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
 extern "C" int ptg_batch_noalloc(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n,
                                  void* stream)
 {
     if (!ctx) return PTG_ERR_INVALID;
+    ctx->err.clear();
     if (n < 0 || n > kNoAllocMaxFields)
         return ptg_fail(ctx, PTG_ERR_INVALID, "ptg_batch_noalloc takes 0 to %d fields, got %d", kNoAllocMaxFields, n);
     if (n > 0 && (!descs || !outs)) return ptg_fail(ctx, PTG_ERR_INVALID, "descs or outs is NULL");
@@ -71,14 +75,15 @@ extern "C" int ptg_batch_noalloc(ptg_ctx* ctx, const ptg_field_desc* descs, void
         const ptg_field_desc* d = descs + f;
         int s = 0;
         int rc = ptg_check_desc(ctx, d, kKindField, &s);
-        if (rc != PTG_OK) return rc;
-        if (d->dims != 2) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field %d: batches are 2D", f);
+        if (rc != PTG_OK) return ptg_fail(ctx, rc, "batch field %d: %s", f, ctx->err.c_str());
+        if (d->dims != 2) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "batch field %d: batches are 2D", f);
         if (ptg_per_sample(d, s))
-            return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field %d: batches need lacunarity 2, a power-of-two spc and no ridged noise", f);
-        if (!outs[f]) return ptg_fail(ctx, PTG_ERR_INVALID, "field %d: out is NULL", f);
+            return ptg_fail(ctx, PTG_ERR_UNSUPPORTED,
+                            "batch field %d: batches need lacunarity 2, a power-of-two spc and no ridged noise", f);
+        if (!outs[f]) return ptg_fail(ctx, PTG_ERR_INVALID, "batch field %d: out is NULL", f);
         rc = ptg_make_field_plan(ctx, d, ptg_kernel_method(kKindField, d), outs[f], s, 0, d->size[1],
                                  &g_stage.plans[f]);
-        if (rc != PTG_OK) return rc;
+        if (rc != PTG_OK) return ptg_fail(ctx, rc, "batch field %d: %s", f, ctx->err.c_str());
         const size_t sm = fbm2d_smem_bytes(g_stage.plans[f]);
         if (sm > smem) smem = sm;
         g_stage.tiles[f] = acc;
