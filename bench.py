@@ -126,28 +126,31 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def profile_traffic():
-    """DRAM bytes per launch of the timed kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def kernel_source_hash():
+    """sha256 (first 16 hex digits) of the sources of the fused 2D generator."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "fbm2d_c1_8192_n12.md")
-    if not os.path.exists(path):
-        return None
     h = hashlib.sha256()
     for f in ("ptg_fbm2d.cu", "ptg_device.cuh", "ptg_eval.cuh"):
         with open(os.path.join(ROOT, "paper_1610_03525_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    src = h.hexdigest()[:16]
-    vals = {}
-    for line in open(path):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != src:
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the timed kernel, from the machine-readable
+    sidecar of its committed ncu capture (profiles/fbm2d_c1_8192_n12.json),
+    if that capture was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "fbm2d_c1_8192_n12.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        return float(rec["dram_bytes_per_launch"])
+    except (KeyError, TypeError, ValueError):
         return None
 
 
@@ -368,7 +371,7 @@ def bench_quality(P, ctx, stream, torch):
     return res
 
 
-def bench_serving(P, torch, duration_s=2.0, warmup_s=0.5, rate_hz=20000.0, budget=40 << 30, slots=256):
+def bench_serving(P, torch, duration_s=10.0, warmup_s=1.0, rate_hz=20000.0, budget=40 << 30, slots=256):
     """Poisson request stream through ptg_submit / ptg_poll (80% 2D 128..2048,
     20% 3D 32..256, octaves 4..12, C1/C2) under a 40 GB budget."""
     from paper_1610_03525_gb300 import workloads as Wl
@@ -469,7 +472,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=32)
     ap.add_argument("--cpu-rows", type=int, default=1536, help="oracle rows for the cpu_baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip baselines, e2e and the oracle leg")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="measured seconds of the serving stream")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="measured seconds of the serving stream")
     ap.add_argument("--tune-cache", default=None,
                     help="thread-shape table: loaded if present (and written for this GPU), else timed and written")
     args = ap.parse_args()
