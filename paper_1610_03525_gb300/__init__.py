@@ -88,6 +88,7 @@ def lib():
             "ptg_wait": ([P, U64, U64], ctypes.c_int),
             "ptg_cancel": ([P, U64], ctypes.c_int),
             "ptg_debug_hold": ([P, I32], ctypes.c_int),
+            "ptg_debug_fail_alloc": ([P, I32, I32], ctypes.c_int),
             "ptg_autotune": ([P, I32, ctypes.c_char_p], ctypes.c_int),
             "ptg_box_counts": ([P, P, I64, I64, F, I32, P, P], ctypes.c_int),
             "ptg_histogram": ([P, P, I64, I64, I64, F, F, I32, I32, P, P], ctypes.c_int),
@@ -355,6 +356,10 @@ def box_dimension(counts, first: int = 1, last: int | None = None) -> float:
 
 def ptg_debug_hold(ctx: Context, hold: int) -> int:
     return _check(ctx, lib().ptg_debug_hold(ctx.handle, hold))
+
+
+def ptg_debug_fail_alloc(ctx: Context, n: int, after: int = 0) -> int:
+    return _check(ctx, lib().ptg_debug_fail_alloc(ctx.handle, after, n))
 
 
 def ptg_debug_hash(ctx: Context, dims: int, keys, out, stream=None) -> int:

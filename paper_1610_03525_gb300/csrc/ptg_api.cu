@@ -63,6 +63,43 @@ int ptg_fail(ptg_ctx* ctx, int code, const char* fmt, ...)
     return code;
 }
 
+static bool injected_alloc_failure(ptg_ctx* ctx)
+{
+    if (ctx->fail_allocs <= 0) return false;
+    if (ctx->alloc_pass > 0) {
+        --ctx->alloc_pass;
+        return false;
+    }
+    --ctx->fail_allocs;
+    return true;
+}
+
+cudaError_t ptg_dev_alloc(ptg_ctx* ctx, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (injected_alloc_failure(ctx)) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t ptg_pinned_alloc(ptg_ctx* ctx, void** p, size_t bytes)
+{
+    *p = nullptr;
+    if (injected_alloc_failure(ctx)) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocHost(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaSuccess;
+}
+
 int ptg_cuda_fail(ptg_ctx* ctx, cudaError_t e, const char* where)
 {
     return ptg_fail(ctx, PTG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
@@ -665,8 +702,8 @@ int ptg_box_counts(ptg_ctx* ctx, const float* map, int64_t W, int64_t H, float l
         if (ctx->stat_buf) cudaFree(ctx->stat_buf);
         ctx->stat_buf = nullptr;
         ctx->stat_bytes = 0;
-        e = cudaMalloc(&ctx->stat_buf, need);
-        if (e != cudaSuccess) return ptg_cuda_fail(ctx, e, "cudaMalloc (box-count pyramid)");
+        if (ptg_dev_alloc(ctx, (void**)&ctx->stat_buf, need) != cudaSuccess)
+            return ptg_fail(ctx, PTG_ERR_NOMEM, "cannot allocate %zu bytes for the box-count pyramid", need);
         ctx->stat_bytes = need;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -725,6 +762,15 @@ int ptg_debug_axis(ptg_ctx* ctx, int64_t origin, int64_t spc, int32_t octave, co
     cudaError_t e = launch_debug_axis((long long)origin, s, octave, (const long long*)j, (long long)n, cell, t,
                                       (cudaStream_t)stream);
     return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "debug_axis");
+}
+
+int ptg_debug_fail_alloc(ptg_ctx* ctx, int32_t after, int32_t n)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+    if (after < 0 || n < 0) return ptg_fail(ctx, PTG_ERR_INVALID, "after and n must be >= 0");
+    ctx->alloc_pass = after;
+    ctx->fail_allocs = n;
+    return PTG_OK;
 }
 
 }  // extern "C"

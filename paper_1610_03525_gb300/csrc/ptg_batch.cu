@@ -89,11 +89,11 @@ int ptg_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int3
     if (ctx->batch_cap < n) {
         ptg_batch_release(ctx);
         const int cap = n < 64 ? 64 : n;
-        if (cudaMalloc(&ctx->batch_dplans, sizeof(FieldPlan) * cap) != cudaSuccess ||
-            cudaMalloc(&ctx->batch_dtiles, sizeof(long long) * (cap + 1)) != cudaSuccess ||
-            cudaMalloc(&ctx->batch_dcounter, 256) != cudaSuccess ||
-            cudaMallocHost(&ctx->batch_hplans, sizeof(FieldPlan) * cap) != cudaSuccess ||
-            cudaMallocHost(&ctx->batch_htiles, sizeof(long long) * (cap + 1)) != cudaSuccess ||
+        if (ptg_dev_alloc(ctx, (void**)&ctx->batch_dplans, sizeof(FieldPlan) * cap) != cudaSuccess ||
+            ptg_dev_alloc(ctx, (void**)&ctx->batch_dtiles, sizeof(long long) * (cap + 1)) != cudaSuccess ||
+            ptg_dev_alloc(ctx, (void**)&ctx->batch_dcounter, 256) != cudaSuccess ||
+            ptg_pinned_alloc(ctx, (void**)&ctx->batch_hplans, sizeof(FieldPlan) * cap) != cudaSuccess ||
+            ptg_pinned_alloc(ctx, (void**)&ctx->batch_htiles, sizeof(long long) * (cap + 1)) != cudaSuccess ||
             cudaEventCreateWithFlags(&ctx->batch_uploaded, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             ptg_batch_release(ctx);
@@ -133,9 +133,9 @@ int ptg_batch_prepare(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* ou
     ptg_batch_plan* p = new (std::nothrow) ptg_batch_plan();
     if (!p) return ptg_fail(ctx, PTG_ERR_NOMEM, "out of host memory");
     p->ctx = ctx;
-    if (cudaMalloc(&p->dplans, sizeof(FieldPlan) * n) != cudaSuccess ||
-        cudaMalloc(&p->dtiles, sizeof(long long) * (n + 1)) != cudaSuccess ||
-        cudaMalloc(&p->dcounter, 256) != cudaSuccess) {
+    if (ptg_dev_alloc(ctx, (void**)&p->dplans, sizeof(FieldPlan) * n) != cudaSuccess ||
+        ptg_dev_alloc(ctx, (void**)&p->dtiles, sizeof(long long) * (n + 1)) != cudaSuccess ||
+        ptg_dev_alloc(ctx, (void**)&p->dcounter, 256) != cudaSuccess) {
         cudaGetLastError();
         ptg_batch_free(p);
         return ptg_fail(ctx, PTG_ERR_NOMEM, "cannot allocate batch plan for %d fields", n);

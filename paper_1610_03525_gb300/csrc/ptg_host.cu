@@ -53,10 +53,8 @@ extern "C" int ptg_generate_host(ptg_ctx* ctx, const ptg_field_desc* d, int32_t 
         if (ctx->stage) cudaFree(ctx->stage);
         ctx->stage = nullptr;
         ctx->stage_bytes = 0;
-        if (cudaMalloc(&ctx->stage, need) != cudaSuccess) {
-            cudaGetLastError();
+        if (ptg_dev_alloc(ctx, &ctx->stage, need) != cudaSuccess)
             return ptg_fail(ctx, PTG_ERR_NOMEM, "cannot allocate %zu bytes of staging", need);
-        }
         ctx->stage_bytes = need;
     }
     if (!ctx->copy_stream) {

@@ -63,7 +63,18 @@ struct ptg_ctx {
     // octaves follow]: run width (8 / 16) | 0x80 when the tile octaves are
     // summed at the tile nodes; 0 = untuned
     uint8_t tune[6][2][9][3][2] = {};
+    // test hook (ptg_debug_fail_alloc): after alloc_pass more allocations made
+    // through ptg_dev_alloc / ptg_pinned_alloc succeed, the next fail_allocs
+    // fail as if memory were exhausted
+    int alloc_pass = 0;
+    int fail_allocs = 0;
 };
+
+// Every device (cudaMalloc) and pinned host (cudaMallocHost) allocation the
+// library makes goes through these two, so that a test can make them fail on
+// the host, without touching the GPU.  cudaErrorMemoryAllocation on failure.
+cudaError_t ptg_dev_alloc(ptg_ctx* ctx, void** p, size_t bytes);
+cudaError_t ptg_pinned_alloc(ptg_ctx* ctx, void** p, size_t bytes);
 
 // Launch configuration of a 2D polynomial / Perlin field: run width (8 or 16)
 // and the number of octaves summed at the tile nodes.  The variant bits of

@@ -210,8 +210,8 @@ int ptg_autotune(ptg_ctx* ctx, int32_t effort, const char* cache_path)
     }
 
     void* out = nullptr;
-    cudaError_t e = cudaMalloc(&out, (size_t)kTuneSide * kTuneSide * sizeof(float));
-    if (e != cudaSuccess) return ptg_cuda_fail(ctx, e, "cudaMalloc (autotune field)");
+    cudaError_t e = ptg_dev_alloc(ctx, &out, (size_t)kTuneSide * kTuneSide * sizeof(float));
+    if (e != cudaSuccess) return ptg_fail(ctx, PTG_ERR_NOMEM, "cannot allocate the autotune field");
     std::vector<cudaEvent_t> ev(8 * (size_t)reps, nullptr);
     for (auto& x : ev)
         if (e == cudaSuccess) e = cudaEventCreate(&x);
