@@ -13,6 +13,15 @@
 // events enters the slot's stream (no host callbacks, which would stall it).
 // There is no background thread and no device spin: progress is made inside
 // ptg_submit / ptg_poll / ptg_wait.
+//
+// NVTX annotations (seen by any NVTX tool attached to the process, free
+// otherwise): a pushed range around each ptg_submit ("ptg_submit"), around
+// each admission ("ptg_admit") and, inside it, around the enqueue of the
+// request's kernels ("ptg_launch"); a mark when the loop sees a request
+// complete ("ptg_complete"); and one process-wide range per request from its
+// submission to its completion or cancellation ("ptg_request").
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -43,6 +52,13 @@ struct Request {
     uint64_t bytes = 0;
     int status = PTG_PENDING;
     uint64_t ts[4] = {0, 0, 0, 0};
+    nvtxRangeId_t span = 0;  // NVTX range from submission to completion
+};
+
+// A pushed NVTX range for the lifetime of a scope.
+struct NvtxScope {
+    explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
 };
 
 // Test hook: blocks a slot's stream on the host (not on the device) until
@@ -100,6 +116,8 @@ PtgServer* server(ptg_ctx* ctx)
 void finish(PtgServer* S, int slot, int status)
 {
     Request* r = S->running[slot];
+    nvtxMarkA("ptg_complete");
+    nvtxRangeEnd(r->span);
     r->status = status;
     r->ts[3] = now_ns();
     float ms = 0.0f;
@@ -134,6 +152,7 @@ void progress(ptg_ctx* ctx, PtgServer* S)
                 break;
             }
         if (slot < 0 || S->admitted + r->bytes > ctx->budget) break;
+        NvtxScope admit("ptg_admit");
         S->pending.pop_front();
         r->ts[1] = now_ns();
         cudaStream_t st = S->streams[slot];
@@ -143,10 +162,16 @@ void progress(ptg_ctx* ctx, PtgServer* S)
         }
         cudaEventRecord(S->begin[slot], st);
         const int64_t slow = r->d.dims == 3 ? r->d.size[2] : r->d.size[1];
-        const int rc = ptg_launch_plan(ctx, kKindField, &r->d, r->s, r->out, 0, slow, st);
+        int rc;
+        {
+            NvtxScope launch("ptg_launch");
+            rc = ptg_launch_plan(ctx, kKindField, &r->d, r->s, r->out, 0, slow, st);
+        }
         if (rc != PTG_OK) {
             r->status = rc;
             r->ts[2] = r->ts[3] = now_ns();
+            nvtxMarkA("ptg_complete");
+            nvtxRangeEnd(r->span);
             continue;
         }
         cudaEventRecord(S->done[slot], st);
@@ -177,6 +202,7 @@ extern "C" {
 
 int ptg_submit(ptg_ctx* ctx, const ptg_field_desc* d, void* out, uint64_t* req_id)
 {
+    NvtxScope scope("ptg_submit");
     if (!ctx) return PTG_ERR_INVALID;
     ctx->err.clear();
     if (!req_id) return ptg_fail(ctx, PTG_ERR_INVALID, "req_id is NULL");
@@ -201,6 +227,7 @@ int ptg_submit(ptg_ctx* ctx, const ptg_field_desc* d, void* out, uint64_t* req_i
     r->s = s;
     r->bytes = bytes;
     r->ts[0] = now_ns();
+    r->span = nvtxRangeStartA("ptg_request");
     S->reqs[r->id] = r;
     S->pending.push_back(r);
     *req_id = r->id;
@@ -258,6 +285,7 @@ int ptg_cancel(ptg_ctx* ctx, uint64_t req_id)
     std::lock_guard<std::mutex> lock(S->mu);
     for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
         if ((*it)->id == req_id) {
+            nvtxRangeEnd((*it)->span);
             (*it)->status = PTG_ERR_CANCELLED;
             S->pending.erase(it);
             return PTG_OK;

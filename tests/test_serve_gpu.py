@@ -152,3 +152,54 @@ def test_per_sample_requests_in_the_mix():
             assert torch.equal(o, a)
     finally:
         ctx.close()
+
+
+_NVTX_CHILD = r"""
+import sys, torch
+sys.path.insert(0, sys.argv[1])
+import paper_1610_03525_gb300 as P
+ctx = P.ptg_create(0, 64 << 20)
+descs = [P.make_desc(dims=2, size=(256, 128), spc=1024, octaves=6, seed=k) for k in range(12)]
+outs = [torch.empty((128, 256), device="cuda") for _ in descs]
+ids = [P.ptg_submit(ctx, d, o) for d, o in zip(descs, outs)]
+for i in ids:
+    assert P.ptg_wait(ctx, i, 30_000_000_000) == P.PTG_OK
+    P.ptg_poll(ctx, i)
+ctx.close()
+"""
+
+
+def test_nvtx_ranges_of_the_request_loop(tmp_path):
+    """The request loop's NVTX ranges, as an NVTX tool sees them: a minimal
+    tool (tests/nvtx_probe.c, loaded by NVTX through NVTX_INJECTION64_PATH)
+    counts the ranges and marks of a child process that serves 12 requests."""
+    import os
+    import shutil
+    import subprocess
+    import sys
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler for the NVTX probe")
+    from paper_1610_03525_gb300 import build
+    build.build()
+    here = os.path.dirname(os.path.abspath(__file__))
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    probe = str(tmp_path / "nvtx_probe.so")
+    subprocess.run([gcc, "-shared", "-fPIC", "-O2", "-I", cuda_inc, os.path.join(here, "nvtx_probe.c"), "-o", probe,
+                    "-lpthread"], check=True)
+    log = tmp_path / "nvtx.log"
+    env = dict(os.environ, NVTX_INJECTION64_PATH=probe, PTG_NVTX_LOG=str(log))
+    subprocess.run([sys.executable, "-c", _NVTX_CHILD, os.path.dirname(here)], check=True, env=env, timeout=300)
+    seen = {}
+    for line in log.read_text().splitlines():
+        key, count = line.rsplit("\t", 1)
+        seen[key] = int(count)
+    assert seen.get("push ptg_submit") == 12
+    assert seen.get("push ptg_admit") == 12
+    assert seen.get("push ptg_launch") == 12
+    assert seen.get("mark ptg_complete") == 12
+    assert seen.get("start ptg_request") == 12
+    assert seen.get("end ", 0) >= 12
+    assert seen.get("pop ", 0) >= 36
