@@ -195,6 +195,58 @@ def lane_ops_3d(kind: str, size, spc: int, octaves: int, f: float = 2.0) -> dict
                 lattice=lattice)
 
 
+# Kernel-independent lower bound ("bound" lane operations): the work any
+# implementation of the method with this corner hash must execute, whatever its
+# tiling, staging or evaluation scheme:
+#   - every distinct lattice corner of every octave whose cells span two or more
+#     samples is hashed once: pcg3d (three LCG steps, six cross multiply-adds,
+#     three xorshifts of two operations = 15; pcg4d 20) plus, per hash word the
+#     model uses, its map to a float (1) and its amplitude scaling (1): 21 for
+#     the Hermite cells and the paper's D2M1N3 (three words), 19 for Perlin
+#     (two), 14 for the zero-gradient model (word 0 alone: 3 + 3 + 6 + 1 + 2);
+#     3D: 20 + 2 per word (four words, Perlin three);
+#   - every sample of an octave whose cells are one sample wide or narrower sits
+#     on a lattice point and needs word 0 of its own corner hash: with the
+#     row-invariant words hoisted out of a run of samples, 10 operations (2D;
+#     3D 11) plus the word's map (1) and its accumulation into the sum (1);
+#     Perlin's lattice octaves are zero and cost nothing;
+#   - per sample, combining the octave sum: octaves whose cells are wider than
+#     d + 1 samples along a row add up to one polynomial of degree d there,
+#     which forward differences evaluate with d additions a sample; each octave
+#     whose cells are d + 1 samples wide or narrower (but wider than one sample)
+#     adds at least one operation a sample.
+# Loads, stores, index arithmetic, node-to-sample interpolation beyond the d
+# additions and every other part of the kernels' own design are not counted,
+# so bound / time / issue peak is the fraction of the machine that the
+# method's irreducible arithmetic would occupy at the measured speed.
+BOUND_CORNER_2D = {"c1": 21, "c2": 21, "paper_gauge": 21, "zero_grad": 14, "perlin_s5": 19, "perlin_s3": 19}
+BOUND_CORNER_3D = {"c1": 28, "c2": 28, "perlin_s5": 26, "perlin_s3": 26}
+
+
+def bound_ops(kind: str, size, spc: int, octaves: int) -> dict:
+    """Lower bound of the lane operations of one field (2D or 3D, fused
+    generators: spc a power of two, frequency ratio 2); see above."""
+    dims = len(size)
+    samples = 1
+    for v in size:
+        samples *= v
+    d = DEG[kind]
+    st = _staged(spc, octaves)
+    corners = 0
+    for i, spci in st:
+        n = 1
+        for v in size:
+            n *= (v + spci - 1) // spci + 1  # distinct corners of the field at this octave
+        corners += n * (BOUND_CORNER_2D if dims == 2 else BOUND_CORNER_3D)[kind]
+    nl = octaves - len(st)
+    lattice = 0 if kind.startswith("perlin") else samples * nl * (12 if dims == 2 else 13)
+    wide = any(spci > d + 1 for _, spci in st)
+    narrow = sum(1 for _, spci in st if spci <= d + 1)
+    combine = samples * ((d if wide else 0) + narrow)
+    tot = corners + lattice + combine
+    return dict(total=float(tot), per_sample=tot / samples, corners=corners, lattice=lattice, combine=combine)
+
+
 def alu_peak(num_sms: int, clock_mhz: float, lanes_per_sm: int = 128) -> float:
     """Issue peak in lane operations per second: SMs x 128 FP32/INT32 lanes
     x clock (one warp instruction per cycle on each of four SM partitions)."""

@@ -74,3 +74,26 @@ def test_simplex3_box_rule():
 
 def test_alu_peak():
     assert abs(R.alu_peak(152, 2070.0) - 152 * 128 * 2070e6) < 1.0
+
+
+def test_bound_counts_distinct_corners_by_brute_force():
+    """The lower bound's corner term counts each distinct lattice corner of a
+    staged octave once: compare with a brute-force set of the cell corners that
+    the samples of a small field touch."""
+    size, spc, N = (37, 21), 8, 5
+    b = R.bound_ops("c1", size, spc, N)
+    want = 0
+    for i in range(min(N, 3)):  # spc 8: octaves 0..2 staged (cells 8, 4, 2 samples)
+        cs = spc >> i
+        pts = set()
+        for y in range(size[1]):
+            for x in range(size[0]):
+                cx, cy = x // cs, y // cs
+                pts.update({(cx, cy), (cx + 1, cy), (cx, cy + 1), (cx + 1, cy + 1)})
+        want += len(pts) * R.BOUND_CORNER_2D["c1"]
+    assert b["corners"] == want
+    assert b["lattice"] == size[0] * size[1] * (N - 3) * 12
+    # cells of 8 samples are wider than d + 1 = 4: one cubic (3 additions);
+    # cells of 4 and 2 samples: one operation each
+    assert b["combine"] == size[0] * size[1] * (3 + 2)
+    assert R.bound_ops("perlin_s5", size, spc, N)["lattice"] == 0
