@@ -71,6 +71,21 @@ static_assert(sizeof(FieldPlan) % 16 == 0, "FieldPlan is copied in 16-byte words
 // Rendering", JCGT 9(3), 2020): an LCG step per word, cross-word multiply-adds,
 // a 16-bit xorshift, and a second round of cross-word multiply-adds.
 // ---------------------------------------------------------------------------
+// The steps of pcg3d after its LCG step (x, y, z already stepped), for
+// callers that take the LCG steps of row- or octave-invariant words once.
+__device__ __forceinline__ void pcg3d_post(uint32_t& x, uint32_t& y, uint32_t& z)
+{
+    x += y * z;
+    y += z * x;
+    z += x * y;
+    x ^= x >> 16;
+    y ^= y >> 16;
+    z ^= z >> 16;
+    x += y * z;
+    y += z * x;
+    z += x * y;
+}
+
 __device__ __forceinline__ void pcg3d(uint32_t& x, uint32_t& y, uint32_t& z)
 {
     x = x * 1664525u + 1013904223u;
@@ -269,4 +284,103 @@ __host__ __device__ constexpr int fine_off2(int K)
 __device__ __forceinline__ void store1(float* p, float v) { *p = v; }
 __device__ __forceinline__ void store1(__half* p, float v) { *p = __float2half_rn(v); }
 
+// ---------------------------------------------------------------------------
+// Bounds checks of the debug build (compiled with -DPTG_DEBUG_BOUNDS, the
+// library libptg_debug.so; the regular build has none of this code, and the
+// helpers below are plain loads and stores there).  Every shared-memory access
+// of the checked kernels is tested against the CTA's dynamic shared memory,
+// and every global index against the extent it belongs to.  A violation is
+// recorded -- the first one of each translation unit, as (site << 48) | index
+// -- and the access is skipped (a load returns zero); nothing traps and no
+// thread leaves early, so barriers stay matched.  ptg_debug_bounds() reads
+// and clears the records.
+// ---------------------------------------------------------------------------
+enum BoundsSite : int {
+    kSiteStage = 1,      // staging stores: tables, weights, corners
+    kSiteCorner = 2,     // corner loads of a cell
+    kSiteTable = 3,      // per-CTA basis tables, tile nodes, row table, weights
+    kSiteConst = 4,      // compile-time tables in global memory
+    kSiteStore = 5,      // output elements
+    kSitePlan = 6,       // batch plans and tile offsets
+    kSiteGradient = 7,   // OpenSimplex gradient boxes
+    kSiteSelfTest = 15   // ptg_debug_bounds_selftest
+};
+
+#ifdef PTG_DEBUG_BOUNDS
+static __device__ unsigned long long g_ptg_bounds;  // one record per translation unit
+#endif
+
+// True if 0 <= idx < n; otherwise records (site, idx) and returns false.
+__device__ __forceinline__ bool bounds_ok(int site, long long idx, long long n)
+{
+#ifdef PTG_DEBUG_BOUNDS
+    if (idx >= 0 && idx < n) return true;
+    atomicCAS(&g_ptg_bounds, 0ull,
+              ((unsigned long long)site << 48) | ((unsigned long long)idx & 0xFFFFFFFFFFFFull));
+    return false;
+#else
+    (void)site, (void)idx, (void)n;
+    return true;
+#endif
+}
+
+// True if `bytes` at p lie inside this CTA's dynamic shared memory.
+__device__ __forceinline__ bool smem_ok(int site, const void* p, int bytes)
+{
+#ifdef PTG_DEBUG_BOUNDS
+    extern __shared__ float4 ptg_dynamic_smem[];
+    unsigned size;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(size));
+    const long long off = (long long)__cvta_generic_to_shared(p) - (long long)__cvta_generic_to_shared(ptg_dynamic_smem);
+    return bounds_ok(site, off, (long long)size - bytes + 1);
+#else
+    (void)site, (void)p, (void)bytes;
+    return true;
+#endif
+}
+
+// Checked shared-memory load and store, and checked read-only global load of
+// element i of an array of n.
+template <typename T>
+__device__ __forceinline__ T sld(int site, const T* p)
+{
+    if (!smem_ok(site, p, (int)sizeof(T))) return T{};
+    return *p;
+}
+
+template <typename T>
+__device__ __forceinline__ void sst(int site, T* p, const T& v)
+{
+    if (smem_ok(site, p, (int)sizeof(T))) *p = v;
+}
+
+template <typename T, typename I>
+__device__ __forceinline__ T gld(int site, const T* p, I i, I n)
+{
+    if (!bounds_ok(site, (long long)i, (long long)n)) return T{};
+    return __ldg(p + i);
+}
+
 }  // namespace ptg
+
+#ifdef PTG_DEBUG_BOUNDS
+// Host side: each translation unit registers a reader of its record.
+#include <cuda_runtime.h>
+namespace ptg {
+using BoundsReader = cudaError_t (*)(unsigned long long* first);
+void register_bounds_reader(BoundsReader fn);
+}  // namespace ptg
+namespace {
+cudaError_t ptg_read_bounds_record(unsigned long long* first)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(first, ptg::g_ptg_bounds, sizeof(unsigned long long));
+    const unsigned long long zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(ptg::g_ptg_bounds, &zero, sizeof zero);
+    return e;
+}
+struct PtgBoundsRegistration {
+    PtgBoundsRegistration() { ptg::register_bounds_reader(&ptg_read_bounds_record); }
+};
+PtgBoundsRegistration ptg_bounds_registration;
+}  // namespace
+#endif

@@ -91,14 +91,16 @@ __host__ __device__ constexpr float tile_lagrange(int c, int q)
 }
 
 // Weights that carry the tile nodes' values to a thread: ly[y] = weights of
-// the d + 1 tile rows at tile row y; lx[tx][q'] = weights of the d + 1 tile
+// the d + 1 tile rows at tile row y; lx[q'][tx] = weights of the d + 1 tile
 // columns at the q'-th node column of the run of thread column tx.  Rows are
-// padded to a multiple of 4 floats for vector loads.
+// padded to a multiple of 4 floats for vector loads; lx is node-column major,
+// so the 8 thread columns of a load phase read consecutive 16-byte words
+// (distinct banks).
 template <int D, int RW>
 struct alignas(16) TileWeights {
     static constexpr int NN = D + 1, LW = (NN + 3) & ~3, TXN = 64 / RW;
     float ly[64][LW];
-    float lx[TXN][NN][LW];
+    float lx[NN][TXN][LW];
 };
 
 template <int D, int RW>
@@ -109,7 +111,7 @@ constexpr TileWeights<D, RW> make_tile_weights()
         for (int q = 0; q <= D; ++q) w.ly[y][q] = tile_lagrange<D>(y, q);
     for (int tx = 0; tx < 64 / RW; ++tx)
         for (int n = 0; n <= D; ++n)
-            for (int q = 0; q <= D; ++q) w.lx[tx][n][q] = tile_lagrange<D>(tx * RW + node_col<D, RW>(n), q);
+            for (int q = 0; q <= D; ++q) w.lx[n][tx][q] = tile_lagrange<D>(tx * RW + node_col<D, RW>(n), q);
     return w;
 }
 
@@ -232,11 +234,18 @@ __device__ __forceinline__ float4 zreduce(float4 lo, float4 hi, float4 zb)
 
 // Per-method cell model: the row collapse at a y-basis entry, the row at
 // t_y = 0, and the evaluation of a collapsed row at an x-basis entry.
+// eval_add(r, xb, a): the same evaluation with the row's V0 term replaced by
+// a, i.e. eval(r, xb) - V0 + a (a caller that sums V0 separately, once per
+// row, adds each node's other terms to its own accumulator).
 template <int METHOD>
 struct Model {  // tensor-product Hermite cells (C1, C2) and Perlin
     __device__ static __forceinline__ Row row(const Cell& c, float4 yb) { return row_of(c, yb.x, yb.y, yb.z); }
     __device__ static __forceinline__ Row row0(const Cell& c) { return row_at_zero(c); }
     __device__ static __forceinline__ float eval(const Row& r, float4 xb) { return eval_row(r, xb.x, xb.y, xb.z); }
+    __device__ static __forceinline__ float eval_add(const Row& r, float4 xb, float a)
+    {
+        return fmaf(xb.z, r.F1, fmaf(xb.y, r.F0, fmaf(xb.x, r.dV, a)));
+    }
 };
 
 // Zero-gradient D2M1N3 (Eq. zg with -xy): for a row at height y,
@@ -266,6 +275,10 @@ struct Model<kZeroGrad> {
         return r;
     }
     __device__ static __forceinline__ float eval(const Row& r, float4 xb) { return fmaf(xb.y, r.F0, fmaf(xb.x, r.dV, r.V0)); }
+    __device__ static __forceinline__ float eval_add(const Row& r, float4 xb, float a)
+    {
+        return fmaf(xb.y, r.F0, fmaf(xb.x, r.dV, a));
+    }
 };
 
 // The D2M1N3 polynomial with the coefficients printed in Sec. 3.1
@@ -323,6 +336,11 @@ struct Model<kPaperGauge> {
     {
         const float t = xb.x;
         return fmaf(t, fmaf(t, fmaf(t, r.F1, r.F0), r.dV), r.V0);
+    }
+    __device__ static __forceinline__ float eval_add(const Row& r, float4 xb, float a)
+    {
+        const float t = xb.x;
+        return fmaf(t, fmaf(t, fmaf(t, r.F1, r.F0), r.dV), a);
     }
 };
 

@@ -64,15 +64,21 @@ static_assert(Shape<8>::TXN * Shape<8>::TYN == kThreads && Shape<16>::TXN * Shap
 //   a copy of the constant basis tables of the finer run octaves (Perlin, if any),
 //   staged corners of every staged octave (rows swizzled by corner_slot),
 //   with tile octaves: the tile nodes' values [D+1][LW], then a copy of the
-//   interpolation weights (TileWeights) made while the corners are hashed.
+//   interpolation weights (TileWeights) made while the corners are hashed,
+//   then (degree 3) the tile polynomial at every tile row and node column.
 template <int METHOD, int RW>
 __host__ __device__ constexpr int xnode_words(int ng) { return ng * (Deg<METHOD>::value + 1) * Shape<RW>::TXN; }
 
+// The tile polynomial at every tile row and each of the d + 1 tile-node
+// columns, Tt[q][64] (degree 3: built by the warps that hold the node values).
+template <int METHOD>
+__host__ __device__ constexpr int row_table_words() { return Deg<METHOD>::value == 3 ? 4 * 64 / 4 : 0; }
+
 template <int METHOD, int RW>
-__host__ __device__ constexpr int grid_words()  // float4 words: tile nodes' values, then their weights
+__host__ __device__ constexpr int grid_words()  // float4 words: tile nodes' values, their weights, the row table
 {
     return ((Deg<METHOD>::value + 1) * TileWeights<Deg<METHOD>::value, RW>::LW +
-            (int)sizeof(TileWeights<Deg<METHOD>::value, RW>) / 4) / 4;
+            (int)sizeof(TileWeights<Deg<METHOD>::value, RW>) / 4) / 4 + row_table_words<METHOD>();
 }
 
 // Tile octaves: octaves with cells >= 64 samples that the host chose to sum
@@ -131,6 +137,103 @@ __device__ const RunBasis<METHOD, RW> kRunBasis = make_run_basis<METHOD, RW>();
 template <int D, int RW>
 __device__ const TileWeights<D, RW> kTileWeights = make_tile_weights<D, RW>();
 
+// Corners of every staged octave of a 64 x 64 tile, hashed once each (Sec. 4.1's
+// C_init), pre-scaled by the octave amplitude.  The layout fixes each fine
+// octave's corner grid, so the work is split into four passes with that
+// geometry known at compile time:
+//   1. octaves with cells of 64 samples or more: 2 x 2 corners each, at 4 i,
+//      all of them at once, a lane a corner (from the last thread down);
+//   2. cells of 32, 16 and 8 samples (3 x 3, 5 x 5 and 9 x 9 corners): their
+//      115 corners in one flat pass, a thread a corner;
+//   3. cells of 4 samples (17 x 17 corners): a flat loop of constant shape;
+//   4. cells of 2 samples (33 x 33 corners): a warp a corner row, a lane a
+//      column (column 32 by the lanes of warps 1 to 3), with x's LCG step
+//      taken once per lane and y's once per row.
+template <int METHOD>
+__device__ __forceinline__ void stage_corners(const FieldPlan& P, float4* __restrict__ corners, int j0x, int j0y)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s = P.s, N = P.N;
+    {  // 1. octaves i <= s - 6
+        int n6 = s - 5;
+        n6 = n6 < 0 ? 0 : (n6 < P.nst ? n6 : P.nst);
+        const int e = kThreads - 1 - tid;
+        if (e < 4 * n6) {
+            const int i = e >> 2, c = e & 3;
+            const OctPlan& op = P.oct[i];
+            uint32_t x = op.ox + ((uint32_t)j0x >> op.k) + (uint32_t)(c & 1);
+            uint32_t y = op.oy + ((uint32_t)j0y >> op.k) + (uint32_t)(c >> 1);
+            uint32_t z = op.key;
+            pcg3d(x, y, z);
+            sst(kSiteStage, &corners[4 * i + c], corner_data<METHOD>(x, y, z, op.amp, op.ampw));
+        }
+    }
+    {  // 2. cells of 32, 16 and 8 samples
+        const int n5 = (s >= 5 && s - 5 < N) ? corner_ncx2(5) * corner_ncx2(5) : 0;
+        const int n4 = (s >= 4 && s - 4 < N) ? corner_ncx2(4) * corner_ncx2(4) : 0;
+        const int n3 = (s >= 3 && s - 3 < N) ? corner_ncx2(3) * corner_ncx2(3) : 0;
+        static_assert(corner_ncx2(5) * corner_ncx2(5) + corner_ncx2(4) * corner_ncx2(4) +
+                          corner_ncx2(3) * corner_ncx2(3) <= kThreads, "one corner a thread");
+        int e = tid, K = 5;
+        if (e >= n5) {
+            e -= n5;
+            K = 4;
+            if (e >= n4) {
+                e -= n4;
+                K = 3;
+            }
+        }
+        if (K > 3 || e < n3) {
+            const OctPlan& op = P.oct[s - K];
+            const int cy = (int)__umulhi((uint32_t)e, op.magic);
+            const int cx = e - cy * op.ncx;
+            uint32_t x = op.ox + ((uint32_t)j0x >> K) + (uint32_t)cx;
+            uint32_t y = op.oy + ((uint32_t)j0y >> K) + (uint32_t)cy;
+            uint32_t z = op.key;
+            pcg3d(x, y, z);
+            if (bounds_ok(kSiteStage, cy * op.rowlen + corner_slot(cx), op.rowlen * op.ncy))
+                sst(kSiteStage, &corners[op.coff + cy * op.rowlen + corner_slot(cx)],
+                    corner_data<METHOD>(x, y, z, op.amp, op.ampw));
+        }
+    }
+    if (s >= 2 && s - 2 < N) {  // 3. cells of 4 samples
+        const OctPlan& op = P.oct[s - 2];
+        constexpr int NC = corner_ncx2(2), RL = corner_rowlen2(2);
+        const uint32_t bx = op.ox + ((uint32_t)j0x >> 2), by = op.oy + ((uint32_t)j0y >> 2);
+        float4* cg = corners + op.coff;
+        const float amp = op.amp, ampw = op.ampw;
+        const uint32_t key = op.key;
+        for (int e = tid; e < NC * NC; e += kThreads) {
+            const int cy = e / NC, cx = e - cy * NC;
+            uint32_t x = bx + (uint32_t)cx, y = by + (uint32_t)cy, z = key;
+            pcg3d(x, y, z);
+            sst(kSiteStage, &cg[cy * RL + corner_slot(cx)], corner_data<METHOD>(x, y, z, amp, ampw));
+        }
+    }
+    if (s >= 1 && s - 1 < N) {  // 4. cells of 2 samples
+        const OctPlan& op = P.oct[s - 1];
+        constexpr int NC = corner_ncx2(1), RL = corner_rowlen2(1);
+        static_assert(NC == 33, "33 corners a row: 32 lanes and one extra column");
+        const uint32_t bx = op.ox + ((uint32_t)j0x >> 1), by = op.oy + ((uint32_t)j0y >> 1);
+        float4* cg = corners + op.coff;
+        const float amp = op.amp, ampw = op.ampw;
+        const uint32_t z1 = pcg_lcg(op.key), x1 = pcg_lcg(bx + (uint32_t)lane);
+        float4* dst = cg + corner_slot(lane);
+#pragma unroll 3
+        for (int cy = warp; cy < NC; cy += kThreads / 32) {
+            uint32_t x = x1, y = pcg_lcg(by + (uint32_t)cy), z = z1;
+            pcg3d_post(x, y, z);
+            sst(kSiteStage, &dst[cy * RL], corner_data<METHOD>(x, y, z, amp, ampw));
+        }
+        if (warp > 0 && lane < 11) {  // column 32: rows 11 (warp - 1) + lane
+            const int cy = 11 * (warp - 1) + lane;
+            uint32_t x = bx + 32u, y = by + (uint32_t)cy, z = op.key;
+            pcg3d(x, y, z);
+            sst(kSiteStage, &cg[cy * RL + corner_slot(NC - 1)], corner_data<METHOD>(x, y, z, amp, ampw));
+        }
+    }
+}
+
 template <int METHOD, int RW>
 __device__ __forceinline__ void stage_tile(const FieldPlan& P, float4* sm, int j0x, int j0y)
 {
@@ -144,68 +247,56 @@ __device__ __forceinline__ void stage_tile(const FieldPlan& P, float4* sm, int j
     float4* corners = rbase + nrb;
     {  // constant tables, global -> shared (latency hidden by the hashing below)
         const float4* src = reinterpret_cast<const float4*>(&kRunBasis<METHOD, RW>);
-        for (int e = tid; e < nrb; e += kThreads) rbase[e] = __ldg(src + e);
+        for (int e = tid; e < nrb; e += kThreads)
+            sst(kSiteStage, &rbase[e], gld(kSiteConst, src, e, (int)sizeof(RunBasis<METHOD, RW>) / 16));
     }
     for (int e = tid; e < ng * NN * SH::TXN; e += kThreads) {
         const int i = e / (NN * SH::TXN), rem = e - i * (NN * SH::TXN);
         const int q = rem / SH::TXN, tx = rem % SH::TXN;
         const int col = tx * RW + node_col<D, RW>(q);
-        xnode[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0x + col), nt + i, s));
+        sst(kSiteStage, &xnode[e], axis_basis<METHOD>(axis_t((uint32_t)(j0x + col), nt + i, s)));
     }
     for (int e = tid; e < ng * 64; e += kThreads) {  // stored in table order: conflict-free
         const int i = e >> 6, slot = e & 63;
         const int row = (slot % SH::TYN) * SH::RR + slot / SH::TYN;
-        ylut[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0y + row), nt + i, s));
+        sst(kSiteStage, &ylut[e], axis_basis<METHOD>(axis_t((uint32_t)(j0y + row), nt + i, s)));
     }
     if (D <= 4 && nt > 0) {  // weights of the tile nodes, global -> shared (latency hidden by the hashing below)
         constexpr int NW = (int)sizeof(TileWeights<D, RW>) / 16;
         const float4* src = reinterpret_cast<const float4*>(&kTileWeights<D, RW>);
         float4* dst = corners + P.ncorner + NN * TileWeights<D, RW>::LW / 4;
-        for (int e = tid; e < NW; e += kThreads) dst[e] = __ldg(src + e);
+        for (int e = tid; e < NW; e += kThreads) sst(kSiteStage, &dst[e], gld(kSiteConst, src, e, NW));
     }
-    // Corners, octave by octave (uniform loops: every lane of a warp reads the
-    // same octave parameters).  Octaves with at most 32 corners go to one warp
-    // each, in turn, so that no warp carries all the small octaves.
-    const int warp = tid >> 5, lane = tid & 31;
-    int small = 0;
-    for (int i = 0; i < P.nst; ++i) {
-        const OctPlan& op = P.oct[i];
-        const int n = op.ncx * op.ncy;
-        int e0 = tid, step = kThreads;
-        if (n <= 32) {
-            if ((small++ & 3) != warp) continue;
-            e0 = lane;
-            step = 32;
-        }
-        const uint32_t bx = op.ox + ((uint32_t)j0x >> op.k), by = op.oy + ((uint32_t)j0y >> op.k);
-        float4* cg = corners + op.coff;
-        for (int e = e0; e < n; e += step) {
-            const int cy = (int)__umulhi((uint32_t)e, op.magic);
-            const int cx = e - cy * op.ncx;
-            uint32_t x = bx + (uint32_t)cx, y = by + (uint32_t)cy, z = op.key;
-            pcg3d(x, y, z);
-            cg[cy * op.rowlen + corner_slot(cx)] = corner_data<METHOD>(x, y, z, op.amp, op.ampw);
-        }
-    }
+    stage_corners<METHOD>(P, corners, j0x, j0y);
 }
 
-__device__ __forceinline__ Cell load_cell(const float4* __restrict__ cg, int rowlen, int lcx, int lcy)
+// Corner s of a row of a staged octave's block (slot `at` of the block's
+// nslots slots, checked in the debug build).
+__device__ __forceinline__ float4 corner_at(const float4* __restrict__ row, int s, int at, int nslots)
+{
+    if (!bounds_ok(kSiteCorner, at, nslots)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    return sld(kSiteCorner, &row[s]);
+}
+
+__device__ __forceinline__ Cell load_cell(const float4* __restrict__ cg, int rowlen, int lcx, int lcy, int nslots)
 {
     const float4* row0 = cg + lcy * rowlen;
     const float4* row1 = row0 + rowlen;
     const int s0 = corner_slot(lcx), s1 = corner_slot(lcx + 1);
     Cell c;
-    c.c00 = row0[s0];
-    c.c10 = row0[s1];
-    c.c01 = row1[s0];
-    c.c11 = row1[s1];
+    c.c00 = corner_at(row0, s0, lcy * rowlen + s0, nslots);
+    c.c10 = corner_at(row0, s1, lcy * rowlen + s1, nslots);
+    c.c01 = corner_at(row1, s0, (lcy + 1) * rowlen + s0, nslots);
+    c.c11 = corner_at(row1, s1, (lcy + 1) * rowlen + s1, nslots);
     return c;
 }
 
-// A run octave: node columns only.
+// A run octave: node columns only.  A collapsed row's V0 term is the same at
+// every node, so it is summed once per row (vacc) and the nodes take the rest.
 // i = octave, ti = its slot in the basis tables (i minus the tile octaves).
 template <int METHOD, int RW>
 __device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
+                                           float (&vacc)[Shape<RW>::RR],
                                            const float4* __restrict__ sm, const float4* __restrict__ corners,
                                            const FieldPlan& P, int i, int ti, int tx, int ty, int ng)
 {
@@ -214,16 +305,17 @@ __device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METH
     const OctPlan& op = P.oct[i];
     const float4* ylut = sm + xnode_words<METHOD, RW>(ng);
     const float4* cg = corners + op.coff;
-    const Cell c = load_cell(cg, op.rowlen, (tx * RW) >> op.k, (ty * SH::RR) >> op.k);
+    const Cell c = load_cell(cg, op.rowlen, (tx * RW) >> op.k, (ty * SH::RR) >> op.k, op.rowlen * op.ncy);
     float4 xb[NN];
 #pragma unroll
-    for (int q = 0; q < NN; ++q) xb[q] = sm[(ti * NN + q) * SH::TXN + tx];
+    for (int q = 0; q < NN; ++q) xb[q] = sld(kSiteTable, &sm[(ti * NN + q) * SH::TXN + tx]);
 #pragma unroll
     for (int r = 0; r < SH::RR; ++r) {
-        const float4 yb = ylut[ti * 64 + r * SH::TYN + ty];
+        const float4 yb = sld(kSiteTable, &ylut[ti * 64 + r * SH::TYN + ty]);
         const Row R = Model<METHOD>::row(c, yb);
+        vacc[r] += R.V0;
 #pragma unroll
-        for (int q = 0; q < NN; ++q) nacc[r][q] += Model<METHOD>::eval(R, xb[q]);
+        for (int q = 0; q < NN; ++q) nacc[r][q] = Model<METHOD>::eval_add(R, xb[q], nacc[r][q]);
     }
 }
 
@@ -232,37 +324,42 @@ __device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METH
 // shifts known at compile time and the bases read from the constant tables.
 template <int METHOD, int RW, int K>
 __device__ __forceinline__ void run_octave_k(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
+                                             float (&vacc)[Shape<RW>::RR],
                                              const float4* __restrict__ fine, const float4* __restrict__ rb,
                                              int tx, int ty)
 {
     using SH = Shape<RW>;
     using RB = RunBasis<METHOD, RW>;
     constexpr int NN = Deg<METHOD>::value + 1, NXK = (1 << K) / RW;
-    const Cell c = load_cell(fine + fine_off2(K), corner_rowlen2(K), (tx * RW) >> K, (ty * SH::RR) >> K);
+    const Cell c = load_cell(fine + fine_off2(K), corner_rowlen2(K), (tx * RW) >> K, (ty * SH::RR) >> K, corner_size2(K));
     const float4* tb = shared_run_basis<METHOD>() ? rb : reinterpret_cast<const float4*>(&kRunBasis<METHOD, RW>);
     const float4* xt = tb + RB::xoff(K) + (tx & (NXK - 1));
     const float4* yt = tb + RB::NX + RB::yoff(K);
     float4 xb[NN];
 #pragma unroll
-    for (int q = 0; q < NN; ++q) xb[q] = shared_run_basis<METHOD>() ? xt[q * NXK] : __ldg(xt + q * NXK);
+    for (int q = 0; q < NN; ++q)
+        xb[q] = !bounds_ok(kSiteConst, RB::xoff(K) + (tx & (NXK - 1)) + q * NXK, RB::NX) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                : shared_run_basis<METHOD>() ? sld(kSiteTable, &xt[q * NXK]) : __ldg(xt + q * NXK);
 #pragma unroll
     for (int r = 0; r < SH::RR; ++r) {
         const float4* yp = yt + ((ty * SH::RR + r) & ((1 << K) - 1));
-        const float4 yb = shared_run_basis<METHOD>() ? *yp : __ldg(yp);
+        const float4 yb = !bounds_ok(kSiteConst, (int)(yp - tb), RB::NX + RB::NY) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                          : shared_run_basis<METHOD>() ? sld(kSiteTable, yp) : __ldg(yp);
         const Row R = Model<METHOD>::row(c, yb);
+        vacc[r] += R.V0;
 #pragma unroll
-        for (int q = 0; q < NN; ++q) nacc[r][q] += Model<METHOD>::eval(R, xb[q]);
+        for (int q = 0; q < NN; ++q) nacc[r][q] = Model<METHOD>::eval_add(R, xb[q], nacc[r][q]);
     }
 }
 
 template <int METHOD, int RW, int K>
 __device__ __forceinline__ void run_fine(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
-                                         const float4* __restrict__ fine, const float4* __restrict__ rb, int s,
-                                         int N, int nt, int tx, int ty)
+                                         float (&vacc)[Shape<RW>::RR], const float4* __restrict__ fine,
+                                         const float4* __restrict__ rb, int s, int N, int nt, int tx, int ty)
 {
     if constexpr (K >= Shape<RW>::LOG) {
         const int i = s - K;  // the octave with cells of 2^K samples, if it is a run octave of this field
-        if (i >= nt && i >= 0 && i < N) run_octave_k<METHOD, RW, K>(nacc, fine, rb, tx, ty);
+        if (i >= nt && i >= 0 && i < N) run_octave_k<METHOD, RW, K>(nacc, vacc, fine, rb, tx, ty);
     }
 }
 
@@ -290,7 +387,7 @@ __device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], co
 #pragma unroll
         for (int xq = 0; xq < NXC; ++xq) {
             const int lcx = (tx * RW + xq * CW) / CW;
-            const Cell c = load_cell(cg, corner_rowlen2(K), lcx, lcy);
+            const Cell c = load_cell(cg, corner_rowlen2(K), lcx, lcy, corner_size2(K));
 #pragma unroll
             for (int rr = 0; rr < RPC; ++rr) {
                 const Row R = (kConstRows && rr == 0) ? Model<METHOD>::row0(c) : Model<METHOD>::row(c, yb[rr]);
@@ -305,35 +402,65 @@ __device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], co
 }
 
 // Tile octaves, CTA part: the sum of octaves 0 .. nt-1 at the (d+1)^2 tile
-// nodes, into G[q][r] (row stride LW).  Each node is summed by PARTS
-// consecutive lanes, octaves dealt round-robin, then added across the lanes
-// with a fixed butterfly (the same bits in every lane and on every run).
-template <int METHOD>
+// nodes, into G[q][r] (row stride LW).  Each node is summed by PARTS lanes,
+// octaves dealt round-robin, then added across the lanes with a fixed
+// butterfly (the same bits in every lane and on every run).  Degree 3: warp w
+// takes tile-node column q = w, lane 4 part + r, so that the 8 lanes of a
+// shared-memory load phase read the corners of two octaves (distinct banks);
+// otherwise a node's PARTS lanes are consecutive.
+template <int METHOD, int RW>
 __device__ __forceinline__ void tile_grid(const FieldPlan& P, const float4* __restrict__ corners, float* G,
                                           int j0x, int j0y, int nt)
 {
     constexpr int D = Deg<METHOD>::value, NN = D + 1, NG = NN * NN, LW = TileWeights<D, 8>::LW;
     constexpr int PARTS = NG <= 16 ? 8 : (NG <= 32 ? 4 : 2);
     static_assert(NG <= kThreads / PARTS, "one lane group per node");
-    const int tid = threadIdx.x, node = tid / PARTS, part = tid % PARTS;
+    const int tid = threadIdx.x;
+    const int node = D == 3 ? (tid >> 5) * NN + (tid & 3) : tid / PARTS;
+    const int part = D == 3 ? (tid & 31) >> 2 : tid % PARTS;
     const int q = node / NN, r = node - q * NN;
     float v = 0.0f;
     if (node < NG) {
         const uint32_t jx = (uint32_t)(j0x + tile_node<D>(q)), jy = (uint32_t)(j0y + tile_node<D>(r));
         for (int i = part; i < nt; i += PARTS) {
             const OctPlan& op = P.oct[i];
-            const Cell c = load_cell(corners + op.coff, op.rowlen, 0, 0);
+            const Cell c = load_cell(corners + op.coff, op.rowlen, 0, 0, 4);
             const Row R = Model<METHOD>::row(c, axis_basis<METHOD>(axis_t(jy, i, P.s)));
             v += Model<METHOD>::eval(R, axis_basis<METHOD>(axis_t(jx, i, P.s)));
         }
     }
+    if constexpr (D == 3) {
 #pragma unroll
-    for (int o = PARTS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (node < NG && part == 0) G[q * LW + r] = v;
+        for (int o = 16; o >= 4; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    } else {
+#pragma unroll
+        for (int o = PARTS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    if constexpr (D == 3) {
+        // Warp w holds the tile-node column q = w (node row r = lane mod 4):
+        // its lanes carry that column to every tile row y,
+        // Tt[q][y] = sum_m ly[y][m] G[q][m], in the order add_tile_grid used
+        static_assert(NN * PARTS == 32, "one tile-node column a warp");
+        float g[NN];
+#pragma unroll
+        for (int m = 0; m < NN; ++m) g[m] = __shfl_sync(0xffffffffu, v, m);
+        const TileWeights<D, RW>& W = *reinterpret_cast<const TileWeights<D, RW>*>(G + NN * LW);
+        float* Tt = G + NN * LW + (int)sizeof(TileWeights<D, RW>) / 4;
+        const int lane = tid & 31;
+#pragma unroll
+        for (int h = 0; h < 64 / 32; ++h) {
+            const int y = lane + 32 * h;
+            const float4 l = sld(kSiteTable, reinterpret_cast<const float4*>(W.ly[y]));
+            sst(kSiteTable, &Tt[q * 64 + y], fmaf(l.w, g[3], fmaf(l.z, g[2], fmaf(l.y, g[1], l.x * g[0]))));
+        }
+    } else if (node < NG && part == 0) {
+        sst(kSiteTable, &G[q * LW + r], v);
+    }
 }
 
 // Tile octaves, thread part: the tile polynomial at the thread's rows and
-// node columns, added to the node accumulators.
+// node columns, added to the node accumulators.  Degree 3 reads its rows from
+// the row table; otherwise each thread carries the tile nodes to its rows.
 template <int METHOD, int RW>
 __device__ __forceinline__ void add_tile_grid(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
                                               const float* __restrict__ G, int tx, int ty)
@@ -342,26 +469,44 @@ __device__ __forceinline__ void add_tile_grid(float (&nacc)[Shape<RW>::RR][Deg<M
     constexpr int D = Deg<METHOD>::value, NN = D + 1, LW = TileWeights<D, RW>::LW;
     const TileWeights<D, RW>& W = *reinterpret_cast<const TileWeights<D, RW>*>(G + NN * LW);
     float Rq[SH::RR][NN];  // tile polynomial at the thread's rows, tile columns q
-#pragma unroll
-    for (int r = 0; r < SH::RR; ++r) {
-        const float* ly = W.ly[ty * SH::RR + r];
-        float w[NN];
-#pragma unroll
-        for (int m = 0; m < NN; ++m) w[m] = ly[m];
+    if constexpr (D == 3) {
+        const float* Tt = G + NN * LW + (int)sizeof(TileWeights<D, RW>) / 4;
 #pragma unroll
         for (int q = 0; q < NN; ++q) {
-            float a = 0.0f;
+            if constexpr (SH::RR == 4) {
+                const float4 t = sld(kSiteTable, reinterpret_cast<const float4*>(Tt + q * 64 + ty * 4));
+                Rq[0][q] = t.x;
+                Rq[1][q] = t.y;
+                Rq[2][q] = t.z;
+                Rq[3][q] = t.w;
+            } else {
+                const float2 t = sld(kSiteTable, reinterpret_cast<const float2*>(Tt + q * 64 + ty * 2));
+                Rq[0][q] = t.x;
+                Rq[1][q] = t.y;
+            }
+        }
+    } else {
 #pragma unroll
-            for (int m = 0; m < NN; ++m) a = fmaf(w[m], G[q * LW + m], a);
-            Rq[r][q] = a;
+        for (int r = 0; r < SH::RR; ++r) {
+            const float* ly = W.ly[ty * SH::RR + r];
+            float w[NN];
+#pragma unroll
+            for (int m = 0; m < NN; ++m) w[m] = sld(kSiteTable, &ly[m]);
+#pragma unroll
+            for (int q = 0; q < NN; ++q) {
+                float a = 0.0f;
+#pragma unroll
+                for (int m = 0; m < NN; ++m) a = fmaf(w[m], sld(kSiteTable, &G[q * LW + m]), a);
+                Rq[r][q] = a;
+            }
         }
     }
 #pragma unroll
     for (int n = 0; n < NN; ++n) {
-        const float* lx = W.lx[tx][n];
+        const float* lx = W.lx[n][tx];
         float w[NN];
 #pragma unroll
-        for (int q = 0; q < NN; ++q) w[q] = lx[q];
+        for (int q = 0; q < NN; ++q) w[q] = sld(kSiteTable, &lx[q]);
 #pragma unroll
         for (int r = 0; r < SH::RR; ++r)
 #pragma unroll
@@ -371,7 +516,7 @@ __device__ __forceinline__ void add_tile_grid(float (&nacc)[Shape<RW>::RR][Deg<M
 
 // One lattice octave: every sample sits on a lattice point.  Each adds
 // amp unit_mant(h) = amp (unit_value(h) + 3): the -3 amp terms of all lattice
-// octaves are added once, at the store (FieldPlan::lat_bias).
+// octaves (FieldPlan::lat_bias) start the rows' sums in fbm2d_tile instead.
 template <int RW>
 __device__ __forceinline__ void lattice_octave(float (&acc)[Shape<RW>::RR][RW], const OctPlan& op, uint32_t jx,
                                                uint32_t jy)
@@ -391,6 +536,13 @@ __device__ __forceinline__ void lattice_octave(float (&acc)[Shape<RW>::RR][RW], 
     }
 }
 
+// Elements [x, x + n) of row y lie inside the W x H output (checked in the
+// debug build only).
+__device__ __forceinline__ bool out_ok(const FieldPlan& P, int x, int y, int n)
+{
+    return bounds_ok(kSiteStore, x + n - 1, P.W) && bounds_ok(kSiteStore, (long long)y * P.W + x, (long long)P.W * P.H);
+}
+
 template <typename OutT, int RW>
 __device__ __forceinline__ void store_tile_as(const FieldPlan& P, const float (&acc)[Shape<RW>::RR][RW], int x0, int y0)
 {
@@ -403,7 +555,8 @@ __device__ __forceinline__ void store_tile_as(const FieldPlan& P, const float (&
                 float4* p = reinterpret_cast<float4*>(row);
 #pragma unroll
                 for (int v = 0; v < RW / 4; ++v)
-                    p[v] = make_float4(acc[r][4 * v], acc[r][4 * v + 1], acc[r][4 * v + 2], acc[r][4 * v + 3]);
+                    if (out_ok(P, x0 + 4 * v, y0 + r, 4))
+                        p[v] = make_float4(acc[r][4 * v], acc[r][4 * v + 1], acc[r][4 * v + 2], acc[r][4 * v + 3]);
             } else {
                 uint4* p = reinterpret_cast<uint4*>(row);
 #pragma unroll
@@ -412,7 +565,7 @@ __device__ __forceinline__ void store_tile_as(const FieldPlan& P, const float (&
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         h[q] = __floats2half2_rn(acc[r][8 * v + 2 * q], acc[r][8 * v + 2 * q + 1]);
-                    p[v] = *reinterpret_cast<const uint4*>(h);
+                    if (out_ok(P, x0 + 8 * v, y0 + r, 8)) p[v] = *reinterpret_cast<const uint4*>(h);
                 }
             }
         }
@@ -428,7 +581,8 @@ __device__ __forceinline__ void store_tile_as(const FieldPlan& P, const float (&
                 float4* p = reinterpret_cast<float4*>(row + x0);
 #pragma unroll
                 for (int v = 0; v < RW / 4; ++v)
-                    p[v] = make_float4(acc[r][4 * v], acc[r][4 * v + 1], acc[r][4 * v + 2], acc[r][4 * v + 3]);
+                    if (out_ok(P, x0 + 4 * v, y, 4))
+                        p[v] = make_float4(acc[r][4 * v], acc[r][4 * v + 1], acc[r][4 * v + 2], acc[r][4 * v + 3]);
             } else {
                 uint4* p = reinterpret_cast<uint4*>(row + x0);
 #pragma unroll
@@ -437,13 +591,13 @@ __device__ __forceinline__ void store_tile_as(const FieldPlan& P, const float (&
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         h[q] = __floats2half2_rn(acc[r][8 * v + 2 * q], acc[r][8 * v + 2 * q + 1]);
-                    p[v] = *reinterpret_cast<const uint4*>(h);
+                    if (out_ok(P, x0 + 8 * v, y, 8)) p[v] = *reinterpret_cast<const uint4*>(h);
                 }
             }
         } else {
 #pragma unroll
             for (int c = 0; c < RW; ++c)
-                if (x0 + c < P.W) store1(row + x0 + c, acc[r][c]);
+                if (x0 + c < P.W && out_ok(P, x0 + c, y, 1)) store1(row + x0 + c, acc[r][c]);
         }
     }
 }
@@ -473,23 +627,34 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     const float4* corners = rb + run_basis_words<METHOD, RW>(P);
     const float4* fine = corners + 4 * n_coarse(P);  // corner blocks of the octaves with cells <= 64 samples
     float* G = reinterpret_cast<float*>(const_cast<float4*>(corners) + P.ncorner);
-    if (Deg<METHOD>::value <= 4 && nt > 0) tile_grid<METHOD>(P, corners, G, j0x, j0y, nt);
+    if (Deg<METHOD>::value <= 4 && nt > 0) tile_grid<METHOD, RW>(P, corners, G, j0x, j0y, nt);
 
     // run octaves: node columns, then interpolate the other columns once
-    float nacc[RR][NN];
+    constexpr bool kPerlin = METHOD == kPerlinS5 || METHOD == kPerlinS3;
+    float nacc[RR][NN], vacc[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+        vacc[r] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
+    }
+    for (int i = 0; i < ng; ++i) run_octave<METHOD, RW>(nacc, vacc, sm, corners, P, nt + i, i, tx, ty, ng);
+    run_fine<METHOD, RW, 6>(nacc, vacc, fine, rb, s, N, nt, tx, ty);
+    run_fine<METHOD, RW, 5>(nacc, vacc, fine, rb, s, N, nt, tx, ty);
+    run_fine<METHOD, RW, 4>(nacc, vacc, fine, rb, s, N, nt, tx, ty);
+    run_fine<METHOD, RW, 3>(nacc, vacc, fine, rb, s, N, nt, tx, ty);
 #pragma unroll
     for (int r = 0; r < RR; ++r)
 #pragma unroll
-        for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
-    for (int i = 0; i < ng; ++i) run_octave<METHOD, RW>(nacc, sm, corners, P, nt + i, i, tx, ty, ng);
-    run_fine<METHOD, RW, 6>(nacc, fine, rb, s, N, nt, tx, ty);
-    run_fine<METHOD, RW, 5>(nacc, fine, rb, s, N, nt, tx, ty);
-    run_fine<METHOD, RW, 4>(nacc, fine, rb, s, N, nt, tx, ty);
-    run_fine<METHOD, RW, 3>(nacc, fine, rb, s, N, nt, tx, ty);
+        for (int q = 0; q < NN; ++q) nacc[r][q] += vacc[r];
     if (Deg<METHOD>::value <= 4 && nt > 0) {  // uniform over the CTA
         __syncthreads();
         add_tile_grid<METHOD, RW>(nacc, G, tx, ty);
     }
+    // The -3 amp offsets of all lattice octaves (FieldPlan::lat_bias) start
+    // every sample's sum: added to the node columns, and the first term of the
+    // others' interpolation (so a field of lattice octaves alone is exact).
+    const float lat = (!kPerlin && s < N) ? P.lat_bias : 0.0f;
     float acc[RR][RW];
 #pragma unroll
     for (int r = 0; r < RR; ++r)
@@ -497,9 +662,9 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
         for (int c = 0; c < RW; ++c) {
             const int q = node_of_col<D, RW>(c);
             if (q >= 0) {
-                acc[r][c] = nacc[r][q];
+                acc[r][c] = nacc[r][q] + lat;
             } else {
-                float v = 0.0f;
+                float v = lat;
 #pragma unroll
                 for (int m = 0; m < NN; ++m) v = fmaf(lagrange<D, RW>(c, m), nacc[r][m], v);
                 acc[r][c] = v;
@@ -510,13 +675,9 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     if (RW == 16 && s >= 3 && s - 3 < N) small_octave<METHOD, RW, (RW == 16 ? 8 : 4)>(acc, fine, tx, ty);
     if (s >= 2 && s - 2 < N) small_octave<METHOD, RW, 4>(acc, fine, tx, ty);
     if (s >= 1 && s - 1 < N) small_octave<METHOD, RW, 2>(acc, fine, tx, ty);
-    if (METHOD != kPerlinS5 && METHOD != kPerlinS3 && s < N) {
+    if (!kPerlin && s < N) {
         for (int i = s; i < N; ++i)
             lattice_octave<RW>(acc, P.oct[i], (uint32_t)(j0x + tx * RW), (uint32_t)(j0y + ty * RR));
-#pragma unroll
-        for (int r = 0; r < RR; ++r)
-#pragma unroll
-            for (int c = 0; c < RW; ++c) acc[r][c] += P.lat_bias;
     }
     store_tile<RW>(P, acc, x0 + tx * RW, y0 + ty * RR);
 }
@@ -555,7 +716,7 @@ __global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* 
     __shared__ FieldPlan plan;
     __shared__ long long s_tile;
     __shared__ int s_field;
-    const long long total = tile_start[n];
+    const long long total = bounds_ok(kSitePlan, n, (long long)n + 1) ? tile_start[n] : 0;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -565,7 +726,7 @@ __global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* 
                 int lo = 0, hi = n - 1;  // last field whose first tile is <= t
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (tile_start[mid] <= t) lo = mid;
+                    if (bounds_ok(kSitePlan, mid, (long long)n + 1) && tile_start[mid] <= t) lo = mid;
                     else hi = mid - 1;
                 }
                 s_field = lo;
@@ -575,14 +736,14 @@ __global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* 
         const long long t = s_tile;
         if (t >= total) break;
         const int f = s_field;
-        if (f != cur) {
+        if (f != cur && bounds_ok(kSitePlan, f, n)) {
             const int4* src = reinterpret_cast<const int4*>(plans + f);
             int4* dst = reinterpret_cast<int4*>(&plan);
             for (int q = threadIdx.x; q < (int)(sizeof(FieldPlan) / 16); q += kThreads) dst[q] = src[q];
             cur = f;
             __syncthreads();
         }
-        const long long local = t - tile_start[f];
+        const long long local = t - (bounds_ok(kSitePlan, f, (long long)n + 1) ? tile_start[f] : t);
         const int bx = (int)(local % plan.tiles_x), by = (int)(local / plan.tiles_x);
         switch (plan.method) {  // the polynomial models (batches are ptg_field calls)
         case kC1: batch_tile<kC1>(plan, sm, bx, by); break;

@@ -19,15 +19,24 @@ RW samples wide ("run" octaves):
                 and add to a float in [2, 4), one FMA for amplitude and the
                 -3 offset; three words for the Hermite cells, two for Perlin,
                 one for the zero-gradient model) and 4 for the grid index:
-                28, 25 and 22;
-  run octaves, per thread and octave: prep + RR rows x (row reduction + eval
-                at each of the d+1 node columns); once per thread, RR rows x
-                (RW - d - 1) columns x (d+1) FMA of interpolation;
+                28, 25 and 22; the corners of cells of 2 samples are hashed
+                a warp a corner row with x's LCG step taken once per lane and
+                y's once per row (pcg3d 12 + 2 for the row word, grid index 1:
+                24, 21 and 15 -- the zero-gradient model needs word 0 alone,
+                whose last cross steps of y and z are not taken);
+  run octaves, per thread and octave: prep + RR rows x (row reduction + one
+                add of the row's V0 + (eval - 1) at each of the d+1 node
+                columns); once per thread RR x (d+1) adds of the rows' V0 sums
+                to the nodes and RR rows x (RW - d - 1) columns x (d+1) FMA of
+                interpolation;
   tile octaves (cells >= 64 samples, when summed at the tile nodes): per tile
                 (d+1)^2 nodes x nt x (2 (coordinate + basis) + prep + row + eval)
-                and (lanes a node - 1) adds a node; per thread
-                RR x (d+1)^2 FMA to the thread's rows and RR x (d+1)^2 to its
-                node columns; no basis tables for these octaves;
+                and (lanes a node - 1) adds a node; degree 3: per tile the
+                tile polynomial at 64 rows x 4 node columns (4 FMA each), per
+                thread RR x (d+1)^2 FMA to its node columns; other degrees:
+                per thread RR x (d+1)^2 FMA to the thread's rows and
+                RR x (d+1)^2 to its node columns; no basis tables for these
+                octaves;
   cells of CW < RW samples (CW = 8 for RW 16; 4, 2), per thread: RW/CW cells
                 along the run, each with prep + one row reduction per row
                 (row 0 of a cell, where the row is the corner data, costs 1),
@@ -42,9 +51,9 @@ RW samples wide ("run" octaves):
                 hoisted out of the row: x's LCG step 1 (it advances by a
                 per-octave constant along the run), y and z multiply-adds 2,
                 three xorshifts 6, the final multiply-add 1; word->float 2;
-                FMA 1 (the -3 offsets of all lattice octaves are one add per
-                sample, counted once).  Perlin's lattice octaves are zero, no
-                work.
+                FMA 1 (the -3 offsets of all lattice octaves start the rows'
+                V0 sums, no work a sample).  Perlin's lattice octaves are zero,
+                no work.
 3D tiles of 32 x 16 x 8 (each thread 8 x 4 x 1): the same regimes, with a
 reduction along z of the cell's four corner columns (32 ops) before each cell
 is used; for C1 with two or more octaves of cells >= 32 samples, those are
@@ -54,10 +63,17 @@ four words 12, index 6; Perlin three words: 35) and lattice samples 14 (pcg4d
 word 0 with the row-invariant terms hoisted: 1 + 3 multiply-adds + 3
 xorshifts (6) + 1, word->float 2, FMA 1; plus one add per sample for the
 offsets).
-OpenSimplex-style: per sample and octave 150 (4 vertices x 33 + 18), a flat
-count not split into staged and hashed octaves; on the 8192^2, 12-octave field
-it exceeds the executed instruction count (1800 against 1675 a sample), so
-fractions taken from it are upper estimates.
+OpenSimplex-style (2D, dyadic steps): per sample and octave, the column's
+offset and in-cell base (product, floor, convert, two adds: 5; redone for each
+of the thread's rows), the row's share of its own (5 per 8 samples), the
+stretched position and vertex (22: sum, split product and its error, floors,
+fractions, converts and the integer vertex), the branch-free vertex choice (17)
+and 4 vertices x (displacement and squish 6, kernel (2 - r^2)^4 (g . d) 9,
+gradient: from the staged box 5 (index, clamp) or hashed 22 (vertex 2, pcg3d
+15, two word maps 5)), the sum of the four terms and the amplitude FMA (4); a
+staged octave adds 25 a box vertex a tile (index 4, pcg3d 15, word maps 4,
+address 2), with box sides 64 step + 6 vertices (step = lattice units a
+sample, staged while step <= 1).
 3D OpenSimplex-style (tiles of 32 x 16 x 8): per sample and octave 40
 (stretched position 20, reflection 12, squish 4, amplitude 4) + 19 candidate
 vertices x 14 (displacement 3, r^2 3, kernel 4, g . d 3, accumulate 1); a
@@ -106,7 +122,14 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8, nt: int = 
     threads = tiles * 128
     samples_padded = tiles * 64 * 64
     if kind == "opensimplex":
-        tot = 150 * samples_padded * octaves
+        tot = 0.0
+        for i in range(octaves):
+            step = 2.0 ** i / spc
+            staged = step <= 1.0
+            per = 5 + 5 / 8 + 22 + 17 + 4 * (6 + 9 + (5 if staged else 22)) + 4
+            tot += samples_padded * per
+            if staged:
+                tot += tiles * (64 * step + 6) ** 2 * 25
         return dict(total=float(tot), per_sample=tot / (w * h))
     rr = 32 // rw
     d = DEG[kind]
@@ -114,26 +137,33 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8, nt: int = 
     nrun = sum(1 for _, spci in st if spci >= rw) - nt
     lut = tiles * nrun * ((64 // rw) * (d + 1) + 64) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
-    evalops = threads * rr * (rw - d - 1) * (d + 1)
+    evalops = threads * rr * (rw - d - 1) * (d + 1) + threads * rr * (d + 1)
     prep, row, smp = MODEL_OPS[kind]
     if nt:
         nodes = (d + 1) ** 2
         parts = 8 if nodes <= 16 else (4 if nodes <= 32 else 2)
         evalops += tiles * nodes * nt * (2 * (COORD_OPS + BASIS_OPS[kind]) + prep + row + smp)
         evalops += tiles * nodes * (parts - 1)  # adds across the lanes of a node
-        evalops += threads * 2 * rr * (d + 1) ** 2
+        if d == 3:
+            evalops += tiles * 64 * (d + 1) * (d + 1) + threads * rr * (d + 1) ** 2
+        else:
+            evalops += threads * 2 * rr * (d + 1) ** 2
     for i, spci in st:
         k = spci.bit_length() - 1
         ncx = (63 >> min(k, 31)) + 2
-        corners += tiles * ncx * ncx * {"zero_grad": 22, "perlin_s5": 25, "perlin_s3": 25}.get(kind, 28)
+        if spci == 2:
+            per = {"zero_grad": 15, "perlin_s5": 21, "perlin_s3": 21}.get(kind, 24)
+        else:
+            per = {"zero_grad": 22, "perlin_s5": 25, "perlin_s3": 25}.get(kind, 28)
+        corners += tiles * ncx * ncx * per
         if i < nt:
             continue
         if spci >= rw:
-            evalops += threads * (prep + rr * (row + smp * (d + 1)))
+            evalops += threads * (prep + rr * (row + 1 + (smp - 1) * (d + 1)))
         else:
             evalops += threads * small_cell_ops(kind, rw, spci)
     n_lattice = octaves - len(st)
-    lattice = 0 if kind.startswith("perlin") or n_lattice == 0 else samples_padded * (n_lattice * 13 + 1)
+    lattice = 0 if kind.startswith("perlin") or n_lattice == 0 else samples_padded * n_lattice * 13
     tot = lut + corners + evalops + lattice
     return dict(total=float(tot), per_sample=tot / (w * h), lut=lut, corners=corners, eval=evalops,
                 lattice=lattice)
