@@ -350,6 +350,24 @@ int ptg_debug_hold(ptg_ctx* ctx, int32_t hold);
  * involved.  Negative arguments return PTG_ERR_INVALID. */
 int ptg_debug_fail_alloc(ptg_ctx* ctx, int32_t after, int32_t n);
 
+/* Bounds-check records of the debug build.  libptg_debug.so (the same sources
+ * compiled with -DPTG_DEBUG_BOUNDS, see paper_1610_03525_gb300/build.py)
+ * checks every shared-memory access of the fused 2D and 3D generators, the
+ * batched 2D generator and the 2D OpenSimplex generator against the CTA's
+ * shared memory, and every index of their global accesses against its
+ * extent; a violation is skipped (loads read zero) and its first occurrence
+ * recorded.  This call synchronizes the context's device, writes the first
+ * record to *first ((site << 48) | index, 0 if none; sites 1 staging stores,
+ * 2 corner loads, 3 per-tile tables, 4 constant tables, 5 output elements,
+ * 6 batch plans, 7 gradient boxes, 15 the self-test) and clears the records.
+ * The regular library returns PTG_ERR_UNSUPPORTED with *first = 0. */
+int ptg_debug_bounds(ptg_ctx* ctx, uint64_t* first);
+
+/* Debug build: evaluate one bounds check (site, idx against [0, n)) in a
+ * kernel, without touching memory at idx, to exercise the recording path.
+ * The regular library returns PTG_ERR_UNSUPPORTED. */
+int ptg_debug_bounds_selftest(ptg_ctx* ctx, int32_t site, int64_t idx, int64_t n);
+
 /* Cell index and in-cell position of n sample indices j (device int64) on
  * one axis at octave i, with the generators' fixed-point map:
  * cell (device uint32) and t (device float). */

@@ -13,7 +13,10 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libptg.so")
+# PTG_LIBRARY may name another build of the same C ABI, e.g. the bounds-checked
+# debug build libptg_debug.so; by default the regular libptg.so is loaded.
+LIB_PATH = os.environ.get("PTG_LIBRARY") or os.path.join(_PKG, "libptg.so")
+DEBUG_LIB_PATH = os.path.join(_PKG, "libptg_debug.so")
 
 PTG_OK, PTG_PENDING = 0, 1
 PTG_ERR_INVALID, PTG_ERR_UNSUPPORTED, PTG_ERR_NOMEM, PTG_ERR_BUDGET = -1, -2, -3, -4
@@ -89,6 +92,8 @@ def lib():
             "ptg_cancel": ([P, U64], ctypes.c_int),
             "ptg_debug_hold": ([P, I32], ctypes.c_int),
             "ptg_debug_fail_alloc": ([P, I32, I32], ctypes.c_int),
+            "ptg_debug_bounds": ([P, ctypes.POINTER(U64)], ctypes.c_int),
+            "ptg_debug_bounds_selftest": ([P, I32, I64, I64], ctypes.c_int),
             "ptg_autotune": ([P, I32, ctypes.c_char_p], ctypes.c_int),
             "ptg_box_counts": ([P, P, I64, I64, F, I32, P, P], ctypes.c_int),
             "ptg_histogram": ([P, P, I64, I64, I64, F, F, I32, I32, P, P], ctypes.c_int),
@@ -360,6 +365,17 @@ def ptg_debug_hold(ctx: Context, hold: int) -> int:
 
 def ptg_debug_fail_alloc(ctx: Context, n: int, after: int = 0) -> int:
     return _check(ctx, lib().ptg_debug_fail_alloc(ctx.handle, after, n))
+
+
+def ptg_debug_bounds(ctx: Context) -> int:
+    """First bounds violation recorded by the debug build ((site << 48) | index), 0 if none; clears the records."""
+    v = ctypes.c_uint64(0)
+    _check(ctx, lib().ptg_debug_bounds(ctx.handle, ctypes.byref(v)))
+    return int(v.value)
+
+
+def ptg_debug_bounds_selftest(ctx: Context, site: int, idx: int, n: int) -> int:
+    return _check(ctx, lib().ptg_debug_bounds_selftest(ctx.handle, site, idx, n))
 
 
 def ptg_debug_hash(ctx: Context, dims: int, keys, out, stream=None) -> int:

@@ -18,6 +18,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libptg.so")
+# The debug build: the same sources with every shared-memory and global index
+# of the checked kernels tested before use (-DPTG_DEBUG_BOUNDS).
+DEBUG_BUILD_DIR = os.path.join(PKG, "_build_debug")
+DEBUG_LIB = os.path.join(PKG, "libptg_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
@@ -46,16 +50,20 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every .cu under csrc/ and link libptg.so; returns its path."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), debug_bounds: bool = False) -> str:
+    """Compile every .cu under csrc/ and link libptg.so (debug_bounds: the
+    bounds-checked libptg_debug.so); returns its path."""
+    build_dir, lib_path = (DEBUG_BUILD_DIR, DEBUG_LIB) if debug_bounds else (BUILD_DIR, LIB)
+    if debug_bounds:
+        extra_flags = tuple(extra_flags) + ("-DPTG_DEBUG_BOUNDS",)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
     hdrs = _headers()
     nvcc = _nvcc()
     objs = []
     jobs = []
     for src in srcs:
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs + [__file__]):
             cmd = [nvcc, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
@@ -74,12 +82,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if jobs:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug_bounds="--debug-bounds" in sys.argv))

@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "ptg.h"
 #include "ptg_internal.h"
@@ -49,6 +50,17 @@ cudaError_t set_kernel_smem(const void* kfn, size_t smem)
 }
 
 }  // namespace ptg
+
+#ifdef PTG_DEBUG_BOUNDS
+// Readers of the bounds records of every translation unit (debug build).
+static std::vector<ptg::BoundsReader>& bounds_readers()
+{
+    static std::vector<ptg::BoundsReader> readers;
+    return readers;
+}
+
+void ptg::register_bounds_reader(ptg::BoundsReader fn) { bounds_readers().push_back(fn); }
+#endif
 
 int ptg_fail(ptg_ctx* ctx, int code, const char* fmt, ...)
 {
@@ -771,6 +783,40 @@ int ptg_debug_fail_alloc(ptg_ctx* ctx, int32_t after, int32_t n)
     ctx->alloc_pass = after;
     ctx->fail_allocs = n;
     return PTG_OK;
+}
+
+int ptg_debug_bounds(ptg_ctx* ctx, uint64_t* first)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+    if (!first) return ptg_fail(ctx, PTG_ERR_INVALID, "first is NULL");
+    *first = 0;
+#ifdef PTG_DEBUG_BOUNDS
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return ptg_cuda_fail(ctx, e, "debug_bounds");
+    for (ptg::BoundsReader fn : bounds_readers()) {
+        unsigned long long v = 0;
+        e = fn(&v);
+        if (e != cudaSuccess) return ptg_cuda_fail(ctx, e, "debug_bounds");
+        if (*first == 0) *first = v;
+    }
+    return PTG_OK;
+#else
+    return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "bounds checks exist in the debug build (libptg_debug.so) only");
+#endif
+}
+
+int ptg_debug_bounds_selftest(ptg_ctx* ctx, int32_t site, int64_t idx, int64_t n)
+{
+    if (!ctx) return PTG_ERR_INVALID;
+#ifdef PTG_DEBUG_BOUNDS
+    DeviceGuard g(ctx->device);
+    const cudaError_t e = launch_bounds_selftest(site, (long long)idx, (long long)n, nullptr);
+    return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "debug_bounds_selftest");
+#else
+    (void)site, (void)idx, (void)n;
+    return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "bounds checks exist in the debug build (libptg_debug.so) only");
+#endif
 }
 
 }  // extern "C"

@@ -39,6 +39,13 @@ __global__ void debug_axis_kernel(uint32_t origin_shifted, int s, int octave, co
     }
 }
 
+// Evaluates one bounds check without any memory access at idx: in the debug
+// build an out-of-range (idx, n) is recorded like a kernel's violation.
+__global__ void bounds_selftest_kernel(int site, long long idx, long long n)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) (void)bounds_ok(site, idx, n);
+}
+
 int grid_for(long long n)
 {
     long long b = (n + 255) / 256;
@@ -60,6 +67,12 @@ cudaError_t launch_debug_axis(long long origin, int s, int octave, const long lo
 {
     const uint32_t o = (uint32_t)((unsigned long long)origin << octave);
     debug_axis_kernel<<<grid_for(n), 256, 0, stream>>>(o, s, octave, j, n, cell, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds_selftest(int site, long long idx, long long n, cudaStream_t stream)
+{
+    bounds_selftest_kernel<<<1, 32, 0, stream>>>(site, idx, n);
     return cudaGetLastError();
 }
 

@@ -112,15 +112,15 @@ __device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int 
     for (int e = tid + nt * NN * 4; e < n8 * NN * 4; e += kThreads) {  // no tables for the tile octaves
         const int i = e / (NN * 4), rem = e - i * (NN * 4);
         const int q = rem >> 2, tx = rem & 3;
-        xnode[e] = axis_basis<METHOD>(axis_t((uint32_t)(j0x + tx * 8 + node_col<Deg<METHOD>::value>(q)), i, s));
+        sst(kSiteStage, &xnode[e], axis_basis<METHOD>(axis_t((uint32_t)(j0x + tx * 8 + node_col<Deg<METHOD>::value>(q)), i, s)));
     }
     for (int e = tid + nt * 24; e < n8 * 24; e += kThreads) {
         const int i = e / 24, slot = e - i * 24;
         if (slot < 16) {  // y: slot = r * 4 + ty, row 4 ty + r
             const int row = (slot & 3) * 4 + (slot >> 2);
-            ylut[i * 16 + slot] = axis_basis<METHOD>(axis_t((uint32_t)(j0y + row), i, s));
+            sst(kSiteStage, &ylut[i * 16 + slot], axis_basis<METHOD>(axis_t((uint32_t)(j0y + row), i, s)));
         } else {
-            zlut[i * 8 + slot - 16] = axis_basis<METHOD>(axis_t((uint32_t)(j0z + slot - 16), i, s));
+            sst(kSiteStage, &zlut[i * 8 + slot - 16], axis_basis<METHOD>(axis_t((uint32_t)(j0z + slot - 16), i, s)));
         }
     }
     // Corners, octave by octave (uniform loops); octaves with at most 32
@@ -147,12 +147,14 @@ __device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int 
             const int cx = rem - cy * op.ncx;
             uint32_t x = bx + (uint32_t)cx, y = by + (uint32_t)cy, z = bz + (uint32_t)cz, w = op.key;
             pcg4d(x, y, z, w);
-            cg[(cz * op.ncy + cy) * op.rowlen + corner_slot(cx)] =
-                (METHOD == kPerlinS5 || METHOD == kPerlinS3)  // Perlin: no value, gradient unweighted
-                    ? make_float4(0.0f, unit_scaled(y, op.amp, m3a), unit_scaled(z, op.amp, m3a),
-                                  unit_scaled(w, op.amp, m3a))
-                    : make_float4(unit_scaled(x, op.amp, m3a), unit_scaled(y, op.ampw, m3w),
-                                  unit_scaled(z, op.ampw, m3w), unit_scaled(w, op.ampw, m3w));
+            const int slot = (cz * op.ncy + cy) * op.rowlen + corner_slot(cx);
+            if (bounds_ok(kSiteStage, slot, op.rowlen * op.ncy * op.ncz))
+                sst(kSiteStage, &cg[slot],
+                    (METHOD == kPerlinS5 || METHOD == kPerlinS3)  // Perlin: no value, gradient unweighted
+                        ? make_float4(0.0f, unit_scaled(y, op.amp, m3a), unit_scaled(z, op.amp, m3a),
+                                      unit_scaled(w, op.amp, m3a))
+                        : make_float4(unit_scaled(x, op.amp, m3a), unit_scaled(y, op.ampw, m3w),
+                                      unit_scaled(z, op.ampw, m3w), unit_scaled(w, op.ampw, m3w)));
         }
     }
 }
@@ -169,7 +171,10 @@ __device__ __forceinline__ Cell zcell(const float4* __restrict__ cg, const OctPl
 #pragma unroll
     for (int q = 0; q < 4; ++q) {  // q = a + 2 b
         const float4* p = p0 + (q >> 1) * op.rowlen + ((q & 1) ? s1 : s0);
-        r[q] = zreduce(p[0], p[plane], zb);
+        const int at = (int)(p - cg), n = plane * op.ncz;  // slots of the octave's block (debug build)
+        const float4 lo = bounds_ok(kSiteCorner, at, n) ? sld(kSiteCorner, &p[0]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 hi = bounds_ok(kSiteCorner, at + plane, n) ? sld(kSiteCorner, &p[plane]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        r[q] = zreduce(lo, hi, zb);
     }
     Cell c;
     c.c00 = r[0];
@@ -198,7 +203,7 @@ __device__ __forceinline__ void tile_grid3(const FieldPlan& P, const float4* __r
         v += eval_row(R, xb.x, xb.y, xb.z);
     }
     v += __shfl_xor_sync(0xffffffffu, v, 1);
-    if (part == 0) G[node] = v;
+    if (part == 0) sst(kSiteTable, &G[node], v);
 }
 
 // Interpolate the tile nodes to the thread's plane, rows and node columns.
@@ -206,12 +211,14 @@ __device__ __forceinline__ void add_tile_grid3(float (&nacc)[kRows][4], const fl
                                                int tz)
 {
     const Tile3Weights& W = kTile3Weights;
-    const float4 wz = __ldg(reinterpret_cast<const float4*>(W.wz[tz]));
+    const float4 wz = bounds_ok(kSiteConst, tz, 8) ? __ldg(reinterpret_cast<const float4*>(W.wz[tz]))
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
     float hz[4][4];  // [y node][x node] in the thread's plane
     const float4* G4 = reinterpret_cast<const float4*>(G);
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        const float4 g0 = G4[b], g1 = G4[4 + b], g2 = G4[8 + b], g3 = G4[12 + b];
+        const float4 g0 = sld(kSiteTable, &G4[b]), g1 = sld(kSiteTable, &G4[4 + b]);
+        const float4 g2 = sld(kSiteTable, &G4[8 + b]), g3 = sld(kSiteTable, &G4[12 + b]);
         hz[b][0] = fmaf(wz.w, g3.x, fmaf(wz.z, g2.x, fmaf(wz.y, g1.x, wz.x * g0.x)));
         hz[b][1] = fmaf(wz.w, g3.y, fmaf(wz.z, g2.y, fmaf(wz.y, g1.y, wz.x * g0.y)));
         hz[b][2] = fmaf(wz.w, g3.z, fmaf(wz.z, g2.z, fmaf(wz.y, g1.z, wz.x * g0.z)));
@@ -219,10 +226,14 @@ __device__ __forceinline__ void add_tile_grid3(float (&nacc)[kRows][4], const fl
     }
     float4 wx[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) wx[q] = __ldg(reinterpret_cast<const float4*>(W.wx[tx][q]));
+    for (int q = 0; q < 4; ++q)
+        wx[q] = bounds_ok(kSiteConst, tx, 4) ? __ldg(reinterpret_cast<const float4*>(W.wx[tx][q]))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
-        const float4 wy = __ldg(reinterpret_cast<const float4*>(W.wy[ty * kRows + r]));
+        const float4 wy = bounds_ok(kSiteConst, ty * kRows + r, 16)
+                              ? __ldg(reinterpret_cast<const float4*>(W.wy[ty * kRows + r]))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
         float hy[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) hy[a] = fmaf(wy.w, hz[3][a], fmaf(wy.z, hz[2][a], fmaf(wy.y, hz[1][a], wy.x * hz[0][a])));
@@ -242,13 +253,14 @@ __device__ __forceinline__ void run8_octave3(float (&nacc)[kRows][Deg<METHOD>::v
     const float4* ylut = sm + xnode_words3<METHOD>(n8);
     const float4* zlut = ylut + n8 * 16;
     const float4* cg = sm + corner_base3<METHOD>(n8) + op.coff;
-    const Cell c = zcell(cg, op, (tx * kCols) >> op.k, (ty * kRows) >> op.k, tz >> op.k, zlut[i * 8 + tz]);
+    const Cell c = zcell(cg, op, (tx * kCols) >> op.k, (ty * kRows) >> op.k, tz >> op.k,
+                         sld(kSiteTable, &zlut[i * 8 + tz]));
     float4 xb[NN];
 #pragma unroll
-    for (int q = 0; q < NN; ++q) xb[q] = sm[(i * NN + q) * 4 + tx];
+    for (int q = 0; q < NN; ++q) xb[q] = sld(kSiteTable, &sm[(i * NN + q) * 4 + tx]);
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
-        const float4 yb = ylut[i * 16 + r * 4 + ty];
+        const float4 yb = sld(kSiteTable, &ylut[i * 16 + r * 4 + ty]);
         const Row R = row_of(c, yb.x, yb.y, yb.z);
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] += eval_row(R, xb[q].x, xb[q].y, xb[q].z);
@@ -317,6 +329,13 @@ __device__ __forceinline__ void lattice_octave3(float (&acc)[kRows][kCols], cons
     }
 }
 
+// Elements [x, x + n) of row y of plane z lie inside the output (checked in
+// the debug build only).
+__device__ __forceinline__ bool out_ok3(const FieldPlan& P, int x, int y, int z, int n)
+{
+    return bounds_ok(kSiteStore, x + n - 1, P.W) && bounds_ok(kSiteStore, y, P.H) && bounds_ok(kSiteStore, z, P.D);
+}
+
 template <typename OutT>
 __device__ __forceinline__ void store_tile3(const FieldPlan& P, const float (&acc)[kRows][kCols], int x0, int y0,
                                             int z)
@@ -329,6 +348,7 @@ __device__ __forceinline__ void store_tile3(const FieldPlan& P, const float (&ac
         if (y >= P.H) break;
         OutT* row = out + (size_t)y * (size_t)P.W;
         if (P.vec_ok && x0 + kCols <= P.W) {
+            if (!out_ok3(P, x0, y, z, kCols)) continue;
             if (sizeof(OutT) == 4) {
                 float4* p = reinterpret_cast<float4*>(row + x0);
                 p[0] = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
@@ -342,7 +362,7 @@ __device__ __forceinline__ void store_tile3(const FieldPlan& P, const float (&ac
         } else {
 #pragma unroll
             for (int c = 0; c < kCols; ++c)
-                if (x0 + c < P.W) store1(row + x0 + c, acc[r][c]);
+                if (x0 + c < P.W && out_ok3(P, x0 + c, y, z, 1)) store1(row + x0 + c, acc[r][c]);
         }
     }
 }

@@ -122,6 +122,7 @@ cudaError_t launch_histogram(const float* maps, long long W, long long H, long l
 
 // Test hooks.
 cudaError_t launch_debug_hash(int dims, const uint32_t* keys, long long n, uint32_t* out, cudaStream_t stream);
+cudaError_t launch_bounds_selftest(int site, long long idx, long long n, cudaStream_t stream);
 cudaError_t launch_debug_axis(long long origin, int s, int octave, const long long* j, long long n,
                               uint32_t* cell, float* t, cudaStream_t stream);
 

@@ -86,8 +86,11 @@ struct Grad {
     {
         if (kStaged) {
             int idx = (b - bmin) * wb + (a - amin);
-            idx = min(max(idx, 0), size - 1);  // the box covers every reachable vertex; the clamp only guards
-            return box[idx];
+            // the box covers every reachable vertex: the debug build checks the
+            // index before the clamp, which only guards
+            if (!bounds_ok(kSiteGradient, idx, size)) return make_float2(0.0f, 0.0f);
+            idx = min(max(idx, 0), size - 1);
+            return sld(kSiteGradient, &box[idx]);
         }
         uint32_t x = (uint32_t)a, y = (uint32_t)b, z = key;
         pcg3d(x, y, z);
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
             T.w = min((int32_t)(long long)floor(xs + (1.0 + kStretchD) * L) + 3 - T.amin + 1, P.box_wb[i]);
             T.h = min((int32_t)(long long)floor(ys + (1.0 + kStretchD) * L) + 3 - T.bmin + 1, P.box_wb[i]);
         }
-        tile[i] = T;
+        if (bounds_ok(kSiteTable, i, kMaxOctaves)) tile[i] = T;
     }
     __syncthreads();
     // hash the gradient boxes of the staged octaves (uniform loop per octave)
@@ -245,7 +248,8 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
             const int vx = v - vy * T.w;
             uint32_t x = (uint32_t)(T.amin + vx), y = (uint32_t)(T.bmin + vy), z = P.key[i];
             pcg3d(x, y, z);
-            box[vy * wb + vx] = make_float2(unit_value(y), unit_value(z));
+            if (bounds_ok(kSiteStage, vy * wb + vx, wb * wb) && bounds_ok(kSiteStage, vx, wb))
+                sst(kSiteStage, &box[vy * wb + vx], make_float2(unit_value(y), unit_value(z)));
         }
     }
     __syncthreads();
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) opensimplex2d_kernel(const __grid_co
 #pragma unroll
         for (int c = 0; c < kCols; ++c) {
             const int x = j0x + lx + 8 * c;
-            if (x < P.W) store1(row + x, acc[c]);
+            if (x < P.W && bounds_ok(kSiteStore, (long long)y * P.W + x, (long long)P.W * P.H)) store1(row + x, acc[c]);
         }
     }
 }
