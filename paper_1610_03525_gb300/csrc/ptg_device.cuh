@@ -146,6 +146,23 @@ __device__ __forceinline__ uint32_t pcg4d_run_value(uint32_t x2, uint32_t y1, ui
     return x3 + y3 * w3;
 }
 
+// The steps of pcg4d after its LCG step (all four words already stepped).
+__device__ __forceinline__ void pcg4d_post(uint32_t& x, uint32_t& y, uint32_t& z, uint32_t& w)
+{
+    x += y * w;
+    y += z * x;
+    z += x * y;
+    w += y * z;
+    x ^= x >> 16;
+    y ^= y >> 16;
+    z ^= z >> 16;
+    w ^= w >> 16;
+    x += y * w;
+    y += z * x;
+    z += x * y;
+    w += y * z;
+}
+
 __device__ __forceinline__ void pcg4d(uint32_t& x, uint32_t& y, uint32_t& z, uint32_t& w)
 {
     x = x * 1664525u + 1013904223u;

@@ -100,6 +100,125 @@ constexpr Tile3Weights make_tile3_weights()
 
 __device__ const Tile3Weights kTile3Weights = make_tile3_weights();
 
+// Corner grid of a 32 x 16 x 8 tile at cells of 2^K samples: corners along
+// x, y, z and float4 slots per swizzled corner row.
+__host__ __device__ constexpr int ncx3(int K) { return (kTW - 1 >> K) + 2; }
+__host__ __device__ constexpr int ncy3(int K) { return (kTH - 1 >> K) + 2; }
+__host__ __device__ constexpr int ncz3(int K) { return (kTD - 1 >> K) + 2; }
+__host__ __device__ constexpr int rowlen3(int K) { return corner_slot(ncx3(K) - 1) + 1; }
+
+// Corner data from the four pcg4d words, pre-scaled by the octave amplitude
+// (and the gradient weight): (v, f, g, e); Perlin: (0, f, g, e), unweighted.
+template <int METHOD>
+__device__ __forceinline__ float4 corner_data4(uint32_t x, uint32_t y, uint32_t z, uint32_t w, float amp, float ampw)
+{
+    const float m3a = -3.0f * amp, m3w = -3.0f * ampw;
+    if (METHOD == kPerlinS5 || METHOD == kPerlinS3)
+        return make_float4(0.0f, unit_scaled(y, amp, m3a), unit_scaled(z, amp, m3a), unit_scaled(w, amp, m3a));
+    return make_float4(unit_scaled(x, amp, m3a), unit_scaled(y, ampw, m3w), unit_scaled(z, ampw, m3w),
+                       unit_scaled(w, ampw, m3w));
+}
+
+// Corners of every staged octave of the tile, hashed once each, in four passes
+// with each fine octave's corner grid known at compile time:
+//   1. octaves with cells of 32 samples or more (2 x 2 x 2 corners each): all
+//      of them at once, a lane a corner, from the last thread down;
+//   2. cells of 16 and 8 samples (3 x 2 x 2 and 5 x 3 x 2 corners): one flat
+//      pass of 42 corners;
+//   3. cells of 4 samples (9 x 5 x 3 corners): a flat loop of constant shape;
+//   4. cells of 2 samples (17 x 9 x 5 corners): a warp two corner rows at a
+//      time (16 lanes a row), with x's LCG step taken once per lane and the
+//      others once per row; column 16 by the last threads down.
+template <int METHOD>
+__device__ __forceinline__ void stage_corners3(const FieldPlan& P, float4* __restrict__ corners, int j0x, int j0y,
+                                               int j0z)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int s = P.s, N = P.N;
+    {  // 1. octaves i <= s - 5, eight slots each from the first (rowlen 2)
+        int n5 = s - 4;
+        n5 = n5 < 0 ? 0 : (n5 < P.nst ? n5 : P.nst);
+        for (int e = kThreads - 1 - tid; e < 8 * n5; e += kThreads) {
+            const int i = e >> 3, c = e & 7;
+            const OctPlan& op = P.oct[i];
+            uint32_t x = op.ox + ((uint32_t)j0x >> op.k) + (uint32_t)(c & 1);
+            uint32_t y = op.oy + ((uint32_t)j0y >> op.k) + (uint32_t)((c >> 1) & 1);
+            uint32_t z = op.oz + ((uint32_t)j0z >> op.k) + (uint32_t)(c >> 2);
+            uint32_t w = op.key;
+            pcg4d(x, y, z, w);
+            if (bounds_ok(kSiteStage, c, op.rowlen * op.ncy * op.ncz))
+                sst(kSiteStage, &corners[op.coff + c], corner_data4<METHOD>(x, y, z, w, op.amp, op.ampw));
+        }
+    }
+    {  // 2. cells of 16 and 8 samples
+        const int n4 = (s >= 4 && s - 4 < N) ? ncx3(4) * ncy3(4) * ncz3(4) : 0;
+        const int n3 = (s >= 3 && s - 3 < N) ? ncx3(3) * ncy3(3) * ncz3(3) : 0;
+        static_assert(ncx3(4) * ncy3(4) * ncz3(4) + ncx3(3) * ncy3(3) * ncz3(3) <= kThreads, "one corner a thread");
+        int e = tid, K = 4;
+        if (e >= n4) {
+            e -= n4;
+            K = 3;
+        }
+        if (K == 4 || e < n3) {
+            const OctPlan& op = P.oct[s - K];
+            const int nxy = op.ncx * op.ncy;
+            const int cz = (int)__umulhi((uint32_t)e, op.magic2);
+            const int rem = e - cz * nxy;
+            const int cy = (int)__umulhi((uint32_t)rem, op.magic);
+            const int cx = rem - cy * op.ncx;
+            uint32_t x = op.ox + ((uint32_t)j0x >> K) + (uint32_t)cx, y = op.oy + ((uint32_t)j0y >> K) + (uint32_t)cy;
+            uint32_t z = op.oz + ((uint32_t)j0z >> K) + (uint32_t)cz, w = op.key;
+            pcg4d(x, y, z, w);
+            const int slot = (cz * op.ncy + cy) * op.rowlen + corner_slot(cx);
+            if (bounds_ok(kSiteStage, slot, op.rowlen * op.ncy * op.ncz))
+                sst(kSiteStage, &corners[op.coff + slot], corner_data4<METHOD>(x, y, z, w, op.amp, op.ampw));
+        }
+    }
+    if (s >= 2 && s - 2 < N) {  // 3. cells of 4 samples
+        const OctPlan& op = P.oct[s - 2];
+        constexpr int NX = ncx3(2), NY = ncy3(2), NZ = ncz3(2), RL = rowlen3(2);
+        const uint32_t bx = op.ox + ((uint32_t)j0x >> 2), by = op.oy + ((uint32_t)j0y >> 2);
+        const uint32_t bz = op.oz + ((uint32_t)j0z >> 2);
+        float4* cg = corners + op.coff;
+        const float amp = op.amp, ampw = op.ampw;
+        const uint32_t key = op.key;
+        for (int e = tid; e < NX * NY * NZ; e += kThreads) {
+            const int cz = e / (NX * NY), rem = e - cz * (NX * NY);
+            const int cy = rem / NX, cx = rem - cy * NX;
+            uint32_t x = bx + (uint32_t)cx, y = by + (uint32_t)cy, z = bz + (uint32_t)cz, w = key;
+            pcg4d(x, y, z, w);
+            sst(kSiteStage, &cg[(cz * NY + cy) * RL + corner_slot(cx)], corner_data4<METHOD>(x, y, z, w, amp, ampw));
+        }
+    }
+    if (s >= 1 && s - 1 < N) {  // 4. cells of 2 samples
+        const OctPlan& op = P.oct[s - 1];
+        constexpr int NX = ncx3(1), NY = ncy3(1), NZ = ncz3(1), RL = rowlen3(1);
+        static_assert(NX == 17, "17 corners a row: 16 lanes and one extra column");
+        const uint32_t bx = op.ox + ((uint32_t)j0x >> 1), by = op.oy + ((uint32_t)j0y >> 1);
+        const uint32_t bz = op.oz + ((uint32_t)j0z >> 1);
+        float4* cg = corners + op.coff;
+        const float amp = op.amp, ampw = op.ampw;
+        const int half = lane >> 4, col = lane & 15;
+        const uint32_t w1 = pcg_lcg(op.key), x1 = pcg_lcg(bx + (uint32_t)col);
+        float4* dst = cg + corner_slot(col);
+        for (int pr = warp; pr < (NY * NZ + 1) / 2; pr += kThreads / 32) {
+            const int r = 2 * pr + half;  // corner row r = cz * NY + cy
+            if (r < NY * NZ) {
+                const int cz = r / NY, cy = r - cz * NY;
+                uint32_t x = x1, y = pcg_lcg(by + (uint32_t)cy), z = pcg_lcg(bz + (uint32_t)cz), w = w1;
+                pcg4d_post(x, y, z, w);
+                sst(kSiteStage, &dst[r * RL], corner_data4<METHOD>(x, y, z, w, amp, ampw));
+            }
+        }
+        for (int r = kThreads - 1 - tid; r < NY * NZ; r += kThreads) {  // column 16
+            const int cz = r / NY, cy = r - cz * NY;
+            uint32_t x = bx + 16u, y = by + (uint32_t)cy, z = bz + (uint32_t)cz, w = op.key;
+            pcg4d(x, y, z, w);
+            sst(kSiteStage, &cg[r * RL + corner_slot(NX - 1)], corner_data4<METHOD>(x, y, z, w, amp, ampw));
+        }
+    }
+}
+
 template <int METHOD>
 __device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int j0x, int j0y, int j0z)
 {
@@ -123,40 +242,7 @@ __device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int 
             sst(kSiteStage, &zlut[i * 8 + slot - 16], axis_basis<METHOD>(axis_t((uint32_t)(j0z + slot - 16), i, s)));
         }
     }
-    // Corners, octave by octave (uniform loops); octaves with at most 32
-    // corners go to one warp each, in turn (see the 2D generator).
-    const int warp = tid >> 5, lane = tid & 31;
-    int small = 0;
-    for (int i = 0; i < P.nst; ++i) {
-        const OctPlan& op = P.oct[i];
-        const int nxy = op.ncx * op.ncy, n = nxy * op.ncz;
-        int e0 = tid, step = kThreads;
-        if (n <= 32) {
-            if ((small++ & 3) != warp) continue;
-            e0 = lane;
-            step = 32;
-        }
-        const uint32_t bx = op.ox + ((uint32_t)j0x >> op.k), by = op.oy + ((uint32_t)j0y >> op.k);
-        const uint32_t bz = op.oz + ((uint32_t)j0z >> op.k);
-        float4* cg = corners + op.coff;
-        const float m3a = -3.0f * op.amp, m3w = -3.0f * op.ampw;
-        for (int e = e0; e < n; e += step) {
-            const int cz = (int)__umulhi((uint32_t)e, op.magic2);
-            const int rem = e - cz * nxy;
-            const int cy = (int)__umulhi((uint32_t)rem, op.magic);
-            const int cx = rem - cy * op.ncx;
-            uint32_t x = bx + (uint32_t)cx, y = by + (uint32_t)cy, z = bz + (uint32_t)cz, w = op.key;
-            pcg4d(x, y, z, w);
-            const int slot = (cz * op.ncy + cy) * op.rowlen + corner_slot(cx);
-            if (bounds_ok(kSiteStage, slot, op.rowlen * op.ncy * op.ncz))
-                sst(kSiteStage, &cg[slot],
-                    (METHOD == kPerlinS5 || METHOD == kPerlinS3)  // Perlin: no value, gradient unweighted
-                        ? make_float4(0.0f, unit_scaled(y, op.amp, m3a), unit_scaled(z, op.amp, m3a),
-                                      unit_scaled(w, op.amp, m3a))
-                        : make_float4(unit_scaled(x, op.amp, m3a), unit_scaled(y, op.ampw, m3w),
-                                      unit_scaled(z, op.ampw, m3w), unit_scaled(w, op.ampw, m3w)));
-        }
-    }
+    stage_corners3<METHOD>(P, corners, j0x, j0y, j0z);
 }
 
 // The 2D cell (W, F, G per corner) of the thread's plane: reduction along z
@@ -184,15 +270,19 @@ __device__ __forceinline__ Cell zcell(const float4* __restrict__ cg, const OctPl
     return c;
 }
 
-// The tile octaves' sum at the 64 tile nodes, into G[(z * 4 + y) * 4 + x]:
-// two lanes a node, each taking every other octave, added by one shuffle.
+// The tile octaves' sum at the 64 tile nodes, two lanes a node, each taking
+// every other octave, added by one shuffle.  Warp w holds the 16 nodes of
+// tile-node row y = w (lane 8 x + 2 z + part), so it can reduce them along z
+// for every plane: Hz[(plane * 4 + y) * 4 + x] = sum_c wz[plane][c] G(x, y, c),
+// the tile polynomial at the plane and the (y, x) nodes.
 template <int METHOD>
-__device__ __forceinline__ void tile_grid3(const FieldPlan& P, const float4* __restrict__ corners, float* G, int j0x,
+__device__ __forceinline__ void tile_grid3(const FieldPlan& P, const float4* __restrict__ corners, float* Hz, int j0x,
                                            int j0y, int j0z, int nt)
 {
-    const int tid = threadIdx.x, node = tid >> 1, part = tid & 1;
-    const uint32_t jx = (uint32_t)(j0x + node3(0, node & 3)), jy = (uint32_t)(j0y + node3(1, (node >> 2) & 3));
-    const uint32_t jz = (uint32_t)(j0z + node3(2, node >> 4));
+    const int tid = threadIdx.x, lane = tid & 31, part = lane & 1;
+    const int nx = lane >> 3, ny = tid >> 5, nz = (lane >> 1) & 3;
+    const uint32_t jx = (uint32_t)(j0x + node3(0, nx)), jy = (uint32_t)(j0y + node3(1, ny));
+    const uint32_t jz = (uint32_t)(j0z + node3(2, nz));
     float v = 0.0f;
     for (int i = part; i < nt; i += 2) {
         const OctPlan& op = P.oct[i];
@@ -203,26 +293,29 @@ __device__ __forceinline__ void tile_grid3(const FieldPlan& P, const float4* __r
         v += eval_row(R, xb.x, xb.y, xb.z);
     }
     v += __shfl_xor_sync(0xffffffffu, v, 1);
-    if (part == 0) sst(kSiteTable, &G[node], v);
+    const int plane = lane >> 2, a = lane & 3;  // this lane's table entry (plane, y = w, x = a)
+    float g[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) g[c] = __shfl_sync(0xffffffffu, v, (a << 3) | (c << 1));
+    const float4 wz = __ldg(reinterpret_cast<const float4*>(kTile3Weights.wz[plane]));
+    sst(kSiteTable, &Hz[(plane * 4 + ny) * 4 + a], fmaf(wz.w, g[3], fmaf(wz.z, g[2], fmaf(wz.y, g[1], wz.x * g[0]))));
 }
 
-// Interpolate the tile nodes to the thread's plane, rows and node columns.
-__device__ __forceinline__ void add_tile_grid3(float (&nacc)[kRows][4], const float* __restrict__ G, int tx, int ty,
+// Interpolate the tile nodes to the thread's plane (from the z-reduced table),
+// rows and node columns.
+__device__ __forceinline__ void add_tile_grid3(float (&nacc)[kRows][4], const float* __restrict__ Hz, int tx, int ty,
                                                int tz)
 {
     const Tile3Weights& W = kTile3Weights;
-    const float4 wz = bounds_ok(kSiteConst, tz, 8) ? __ldg(reinterpret_cast<const float4*>(W.wz[tz]))
-                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
     float hz[4][4];  // [y node][x node] in the thread's plane
-    const float4* G4 = reinterpret_cast<const float4*>(G);
+    const float4* H4 = reinterpret_cast<const float4*>(Hz) + tz * 4;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        const float4 g0 = sld(kSiteTable, &G4[b]), g1 = sld(kSiteTable, &G4[4 + b]);
-        const float4 g2 = sld(kSiteTable, &G4[8 + b]), g3 = sld(kSiteTable, &G4[12 + b]);
-        hz[b][0] = fmaf(wz.w, g3.x, fmaf(wz.z, g2.x, fmaf(wz.y, g1.x, wz.x * g0.x)));
-        hz[b][1] = fmaf(wz.w, g3.y, fmaf(wz.z, g2.y, fmaf(wz.y, g1.y, wz.x * g0.y)));
-        hz[b][2] = fmaf(wz.w, g3.z, fmaf(wz.z, g2.z, fmaf(wz.y, g1.z, wz.x * g0.z)));
-        hz[b][3] = fmaf(wz.w, g3.w, fmaf(wz.z, g2.w, fmaf(wz.y, g1.w, wz.x * g0.w)));
+        const float4 h = sld(kSiteTable, &H4[b]);
+        hz[b][0] = h.x;
+        hz[b][1] = h.y;
+        hz[b][2] = h.z;
+        hz[b][3] = h.w;
     }
     float4 wx[4];
 #pragma unroll
@@ -244,7 +337,7 @@ __device__ __forceinline__ void add_tile_grid3(float (&nacc)[kRows][4], const fl
 }
 
 template <int METHOD>
-__device__ __forceinline__ void run8_octave3(float (&nacc)[kRows][Deg<METHOD>::value + 1],
+__device__ __forceinline__ void run8_octave3(float (&nacc)[kRows][Deg<METHOD>::value + 1], float (&vacc)[kRows],
                                              const float4* __restrict__ sm, const FieldPlan& P, int i, int tx,
                                              int ty, int tz, int n8)
 {
@@ -262,8 +355,9 @@ __device__ __forceinline__ void run8_octave3(float (&nacc)[kRows][Deg<METHOD>::v
     for (int r = 0; r < kRows; ++r) {
         const float4 yb = sld(kSiteTable, &ylut[i * 16 + r * 4 + ty]);
         const Row R = row_of(c, yb.x, yb.y, yb.z);
+        vacc[r] += R.V0;  // the same at every node: summed once per row
 #pragma unroll
-        for (int q = 0; q < NN; ++q) nacc[r][q] += eval_row(R, xb[q].x, xb[q].y, xb[q].z);
+        for (int q = 0; q < NN; ++q) nacc[r][q] = Model<METHOD>::eval_add(R, xb[q], nacc[r][q]);
     }
 }
 
@@ -309,8 +403,8 @@ __device__ __forceinline__ void small_octave3(float (&acc)[kRows][kCols], const 
     }
 }
 
-// Adds amp unit_mant(h); the -3 amp terms of all lattice octaves are added
-// once, at the store (FieldPlan::lat_bias).
+// Adds amp unit_mant(h); the -3 amp terms of all lattice octaves
+// (FieldPlan::lat_bias) start every sample's sum instead.
 __device__ __forceinline__ void lattice_octave3(float (&acc)[kRows][kCols], const OctPlan& op, uint32_t jx,
                                                 uint32_t jy, uint32_t jz)
 {
@@ -379,22 +473,32 @@ __global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__
     stage_tile3<METHOD>(P, sm, j0x, j0y, j0z);
     __syncthreads();
 
-    // tile octaves: their sum at the tile nodes (read back after the barrier below)
-    float* G = reinterpret_cast<float*>(sm + corner_base3<METHOD>(n8) + P.ncorner);
-    if (nt > 0) tile_grid3<METHOD>(P, sm + corner_base3<METHOD>(n8), G, j0x, j0y, j0z, nt);
+    // tile octaves: their sum at the tile nodes, reduced along z for every
+    // plane (read back after the barrier below)
+    float* Hz = reinterpret_cast<float*>(sm + corner_base3<METHOD>(n8) + P.ncorner);
+    if (nt > 0) tile_grid3<METHOD>(P, sm + corner_base3<METHOD>(n8), Hz, j0x, j0y, j0z, nt);
 
-    float nacc[kRows][NN];
+    float nacc[kRows][NN], vacc[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        vacc[r] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
+    }
+    for (int i = nt; i < n8; ++i) run8_octave3<METHOD>(nacc, vacc, sm, P, i, tx, ty, tz, n8);
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
 #pragma unroll
-        for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
-    for (int i = nt; i < n8; ++i) run8_octave3<METHOD>(nacc, sm, P, i, tx, ty, tz, n8);
+        for (int q = 0; q < NN; ++q) nacc[r][q] += vacc[r];
     if constexpr (NN == 4) {
         if (nt > 0) {  // uniform over the CTA
             __syncthreads();
-            add_tile_grid3(nacc, G, tx, ty, tz);
+            add_tile_grid3(nacc, Hz, tx, ty, tz);
         }
     }
+    // the -3 amp offsets of all lattice octaves start every sample's sum
+    constexpr bool kPerlin = METHOD == kPerlinS5 || METHOD == kPerlinS3;
+    const float lat = (!kPerlin && s < N) ? P.lat_bias : 0.0f;
     float acc[kRows][kCols];
 #pragma unroll
     for (int r = 0; r < kRows; ++r)
@@ -402,9 +506,9 @@ __global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__
         for (int c = 0; c < kCols; ++c) {
             const int q = node_of_col<D>(c);
             if (q >= 0) {
-                acc[r][c] = nacc[r][q];
+                acc[r][c] = nacc[r][q] + lat;
             } else {
-                float v = 0.0f;
+                float v = lat;
 #pragma unroll
                 for (int m = 0; m < NN; ++m) v = fmaf(lagrange<D>(c, m), nacc[r][m], v);
                 acc[r][c] = v;
@@ -412,13 +516,9 @@ __global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__
         }
     if (s >= 2 && s - 2 < N) small_octave3<METHOD, 4>(acc, sm, P, s - 2, tx, ty, tz, n8);
     if (s >= 1 && s - 1 < N) small_octave3<METHOD, 2>(acc, sm, P, s - 1, tx, ty, tz, n8);
-    if (METHOD != kPerlinS5 && METHOD != kPerlinS3 && s < N) {  // Perlin is zero at lattice points
+    if (!kPerlin && s < N) {  // Perlin is zero at lattice points
         const uint32_t jx = (uint32_t)(j0x + tx * kCols), jy = (uint32_t)(j0y + ty * kRows), jz = (uint32_t)(j0z + tz);
         for (int i = s; i < N; ++i) lattice_octave3(acc, P.oct[i], jx, jy, jz);
-#pragma unroll
-        for (int r = 0; r < kRows; ++r)
-#pragma unroll
-            for (int c = 0; c < kCols; ++c) acc[r][c] += P.lat_bias;
     }
     store_tile3<OutT>(P, acc, x0 + tx * kCols, y0 + ty * kRows, z0 + tz);
 }
@@ -428,7 +528,7 @@ size_t smem_words3(const FieldPlan& P)
 {
     int n8 = P.s - 2;
     n8 = n8 < 0 ? 0 : (n8 < P.N ? n8 : P.N);
-    return (size_t)corner_base3<METHOD>(n8) + (size_t)P.ncorner + (n_tile3<METHOD>(P) > 0 ? 16 : 0);
+    return (size_t)corner_base3<METHOD>(n8) + (size_t)P.ncorner + (n_tile3<METHOD>(P) > 0 ? kTD * 16 / 4 : 0);
 }
 
 }  // namespace
