@@ -27,6 +27,11 @@
 //     columns once, at the end, by exact Lagrange interpolation.  The wider
 //     run halves the per-sample cost of these octaves and adds interpolated
 //     columns; which shape is faster depends on the octave mix.
+//     With degree 3 and runs of 8 the same holds along y: the two threads
+//     that share an 8 x 8 block (one cell of the finest run octave) evaluate
+//     rows 0, 2 and 5, 7 of it only, swap them, and interpolate rows 1, 3, 4
+//     and 6 (the "node rows"; together with the tile octaves' sum, which is a
+//     cubic over the whole tile).
 //   2 <= spc_i < RW: in-cell column positions are the constants q / spc_i and
 //     positions t = 0 take the corner data directly.
 //   spc_i <= 1 ("lattice"): every sample is a lattice point, where the cell
@@ -55,6 +60,26 @@ struct Shape {
     static constexpr int LOG = RW == 8 ? 3 : 4;
 };
 static_assert(Shape<8>::TXN * Shape<8>::TYN == kThreads && Shape<16>::TXN * Shape<16>::TYN == kThreads, "");
+
+// Node rows (degree 3, runs of 8 x 4): the sum of the run and tile octaves
+// over an 8 x 8 block (the thread pair ty = 2b, 2b + 1, lanes l and l ^ 8 of
+// one warp) is one bicubic, so it is evaluated at the block's rows 0, 2, 5, 7
+// (the node columns' positions, Lebesgue constant 1.4) and interpolated at
+// the other four.  The even thread evaluates its rows 0 and 2, the odd one
+// its rows 3 and 1 (block rows 7 and 5): mirrored, so that both take the
+// same interpolation weights.  NRW = rows a thread evaluates.
+template <int METHOD, int RW>
+__host__ __device__ constexpr bool node_rows() { return Deg<METHOD>::value == 3 && RW == 8; }
+
+template <int METHOD, int RW>
+__host__ __device__ constexpr int n_rows() { return node_rows<METHOD, RW>() ? 2 : Shape<RW>::RR; }
+
+// Row (within the thread's RR rows) of its k-th evaluated row; par = ty & 1.
+template <int METHOD, int RW>
+__device__ __forceinline__ int eval_row(int k, int par)
+{
+    return node_rows<METHOD, RW>() ? (k == 0 ? 3 * par : 2 - par) : k;
+}
 
 // Shared-memory layout (float4 units), with ng = run octaves with cells of
 // 128 samples or more that are not tile octaves (their basis depends on the
@@ -295,13 +320,13 @@ __device__ __forceinline__ Cell load_cell(const float4* __restrict__ cg, int row
 // every node, so it is summed once per row (vacc) and the nodes take the rest.
 // i = octave, ti = its slot in the basis tables (i minus the tile octaves).
 template <int METHOD, int RW>
-__device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
-                                           float (&vacc)[Shape<RW>::RR],
+__device__ __forceinline__ void run_octave(float (&nacc)[n_rows<METHOD, RW>()][Deg<METHOD>::value + 1],
+                                           float (&vacc)[n_rows<METHOD, RW>()],
                                            const float4* __restrict__ sm, const float4* __restrict__ corners,
-                                           const FieldPlan& P, int i, int ti, int tx, int ty, int ng)
+                                           const FieldPlan& P, int i, int ti, int tx, int ty, int ng, int par)
 {
     using SH = Shape<RW>;
-    constexpr int NN = Deg<METHOD>::value + 1;
+    constexpr int NN = Deg<METHOD>::value + 1, NRW = n_rows<METHOD, RW>();
     const OctPlan& op = P.oct[i];
     const float4* ylut = sm + xnode_words<METHOD, RW>(ng);
     const float4* cg = corners + op.coff;
@@ -310,8 +335,8 @@ __device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METH
 #pragma unroll
     for (int q = 0; q < NN; ++q) xb[q] = sld(kSiteTable, &sm[(ti * NN + q) * SH::TXN + tx]);
 #pragma unroll
-    for (int r = 0; r < SH::RR; ++r) {
-        const float4 yb = sld(kSiteTable, &ylut[ti * 64 + r * SH::TYN + ty]);
+    for (int r = 0; r < NRW; ++r) {
+        const float4 yb = sld(kSiteTable, &ylut[ti * 64 + eval_row<METHOD, RW>(r, par) * SH::TYN + ty]);
         const Row R = Model<METHOD>::row(c, yb);
         vacc[r] += R.V0;
 #pragma unroll
@@ -323,14 +348,14 @@ __device__ __forceinline__ void run_octave(float (&nacc)[Shape<RW>::RR][Deg<METH
 // run_octave, with the corner block, its row length and the cell index
 // shifts known at compile time and the bases read from the constant tables.
 template <int METHOD, int RW, int K>
-__device__ __forceinline__ void run_octave_k(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
-                                             float (&vacc)[Shape<RW>::RR],
+__device__ __forceinline__ void run_octave_k(float (&nacc)[n_rows<METHOD, RW>()][Deg<METHOD>::value + 1],
+                                             float (&vacc)[n_rows<METHOD, RW>()],
                                              const float4* __restrict__ fine, const float4* __restrict__ rb,
-                                             int tx, int ty)
+                                             int tx, int ty, int par)
 {
     using SH = Shape<RW>;
     using RB = RunBasis<METHOD, RW>;
-    constexpr int NN = Deg<METHOD>::value + 1, NXK = (1 << K) / RW;
+    constexpr int NN = Deg<METHOD>::value + 1, NXK = (1 << K) / RW, NRW = n_rows<METHOD, RW>();
     const Cell c = load_cell(fine + fine_off2(K), corner_rowlen2(K), (tx * RW) >> K, (ty * SH::RR) >> K, corner_size2(K));
     const float4* tb = shared_run_basis<METHOD>() ? rb : reinterpret_cast<const float4*>(&kRunBasis<METHOD, RW>);
     const float4* xt = tb + RB::xoff(K) + (tx & (NXK - 1));
@@ -341,8 +366,9 @@ __device__ __forceinline__ void run_octave_k(float (&nacc)[Shape<RW>::RR][Deg<ME
         xb[q] = !bounds_ok(kSiteConst, RB::xoff(K) + (tx & (NXK - 1)) + q * NXK, RB::NX) ? make_float4(0.f, 0.f, 0.f, 0.f)
                 : shared_run_basis<METHOD>() ? sld(kSiteTable, &xt[q * NXK]) : __ldg(xt + q * NXK);
 #pragma unroll
-    for (int r = 0; r < SH::RR; ++r) {
-        const float4* yp = yt + ((ty * SH::RR + r) & ((1 << K) - 1));
+    for (int r = 0; r < NRW; ++r) {
+        // (ty RR) mod 2^K is a multiple of RR, so the row adds without a carry
+        const float4* yp = yt + ((ty * SH::RR) & ((1 << K) - 1)) + eval_row<METHOD, RW>(r, par);
         const float4 yb = !bounds_ok(kSiteConst, (int)(yp - tb), RB::NX + RB::NY) ? make_float4(0.f, 0.f, 0.f, 0.f)
                           : shared_run_basis<METHOD>() ? sld(kSiteTable, yp) : __ldg(yp);
         const Row R = Model<METHOD>::row(c, yb);
@@ -353,13 +379,13 @@ __device__ __forceinline__ void run_octave_k(float (&nacc)[Shape<RW>::RR][Deg<ME
 }
 
 template <int METHOD, int RW, int K>
-__device__ __forceinline__ void run_fine(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
-                                         float (&vacc)[Shape<RW>::RR], const float4* __restrict__ fine,
-                                         const float4* __restrict__ rb, int s, int N, int nt, int tx, int ty)
+__device__ __forceinline__ void run_fine(float (&nacc)[n_rows<METHOD, RW>()][Deg<METHOD>::value + 1],
+                                         float (&vacc)[n_rows<METHOD, RW>()], const float4* __restrict__ fine,
+                                         const float4* __restrict__ rb, int s, int N, int nt, int tx, int ty, int par)
 {
     if constexpr (K >= Shape<RW>::LOG) {
         const int i = s - K;  // the octave with cells of 2^K samples, if it is a run octave of this field
-        if (i >= nt && i >= 0 && i < N) run_octave_k<METHOD, RW, K>(nacc, vacc, fine, rb, tx, ty);
+        if (i >= nt && i >= 0 && i < N) run_octave_k<METHOD, RW, K>(nacc, vacc, fine, rb, tx, ty, par);
     }
 }
 
@@ -439,7 +465,9 @@ __device__ __forceinline__ void tile_grid(const FieldPlan& P, const float4* __re
     if constexpr (D == 3) {
         // Warp w holds the tile-node column q = w (node row r = lane mod 4):
         // its lanes carry that column to every tile row y,
-        // Tt[q][y] = sum_m ly[y][m] G[q][m], in the order add_tile_grid used
+        // Tt[q][y] = sum_m ly[y][m] G[q][m], in the order add_tile_grid reads
+        // (with node rows, rows 4b + (0, 2, 3, 1) in slots 4b + (0, 1, 2, 3):
+        // each thread's two evaluated rows side by side)
         static_assert(NN * PARTS == 32, "one tile-node column a warp");
         float g[NN];
 #pragma unroll
@@ -451,7 +479,8 @@ __device__ __forceinline__ void tile_grid(const FieldPlan& P, const float4* __re
         for (int h = 0; h < 64 / 32; ++h) {
             const int y = lane + 32 * h;
             const float4 l = sld(kSiteTable, reinterpret_cast<const float4*>(W.ly[y]));
-            sst(kSiteTable, &Tt[q * 64 + y], fmaf(l.w, g[3], fmaf(l.z, g[2], fmaf(l.y, g[1], l.x * g[0]))));
+            const int slot = node_rows<METHOD, RW>() ? (y & ~3) | ((0x2130 >> (4 * (y & 3))) & 3) : y;
+            sst(kSiteTable, &Tt[q * 64 + slot], fmaf(l.w, g[3], fmaf(l.z, g[2], fmaf(l.y, g[1], l.x * g[0]))));
         }
     } else if (node < NG && part == 0) {
         sst(kSiteTable, &G[q * LW + r], v);
@@ -462,18 +491,22 @@ __device__ __forceinline__ void tile_grid(const FieldPlan& P, const float4* __re
 // node columns, added to the node accumulators.  Degree 3 reads its rows from
 // the row table; otherwise each thread carries the tile nodes to its rows.
 template <int METHOD, int RW>
-__device__ __forceinline__ void add_tile_grid(float (&nacc)[Shape<RW>::RR][Deg<METHOD>::value + 1],
-                                              const float* __restrict__ G, int tx, int ty)
+__device__ __forceinline__ void add_tile_grid(float (&nacc)[n_rows<METHOD, RW>()][Deg<METHOD>::value + 1],
+                                              const float* __restrict__ G, int tx, int ty, int par)
 {
     using SH = Shape<RW>;
-    constexpr int D = Deg<METHOD>::value, NN = D + 1, LW = TileWeights<D, RW>::LW;
+    constexpr int D = Deg<METHOD>::value, NN = D + 1, LW = TileWeights<D, RW>::LW, NRW = n_rows<METHOD, RW>();
     const TileWeights<D, RW>& W = *reinterpret_cast<const TileWeights<D, RW>*>(G + NN * LW);
-    float Rq[SH::RR][NN];  // tile polynomial at the thread's rows, tile columns q
+    float Rq[NRW][NN];  // tile polynomial at the thread's evaluated rows, tile columns q
     if constexpr (D == 3) {
         const float* Tt = G + NN * LW + (int)sizeof(TileWeights<D, RW>) / 4;
 #pragma unroll
         for (int q = 0; q < NN; ++q) {
-            if constexpr (SH::RR == 4) {
+            if constexpr (node_rows<METHOD, RW>()) {
+                const float2 t = sld(kSiteTable, reinterpret_cast<const float2*>(Tt + q * 64 + ty * 4 + 2 * par));
+                Rq[0][q] = t.x;
+                Rq[1][q] = t.y;
+            } else if constexpr (SH::RR == 4) {
                 const float4 t = sld(kSiteTable, reinterpret_cast<const float4*>(Tt + q * 64 + ty * 4));
                 Rq[0][q] = t.x;
                 Rq[1][q] = t.y;
@@ -508,7 +541,7 @@ __device__ __forceinline__ void add_tile_grid(float (&nacc)[Shape<RW>::RR][Deg<M
 #pragma unroll
         for (int q = 0; q < NN; ++q) w[q] = sld(kSiteTable, &lx[q]);
 #pragma unroll
-        for (int r = 0; r < SH::RR; ++r)
+        for (int r = 0; r < NRW; ++r)
 #pragma unroll
             for (int q = 0; q < NN; ++q) nacc[r][n] = fmaf(w[q], Rq[r][q], nacc[r][n]);
     }
@@ -631,25 +664,55 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
 
     // run octaves: node columns, then interpolate the other columns once
     constexpr bool kPerlin = METHOD == kPerlinS5 || METHOD == kPerlinS3;
-    float nacc[RR][NN], vacc[RR];
+    constexpr int NRW = n_rows<METHOD, RW>();
+    const int par = node_rows<METHOD, RW>() ? (ty & 1) : 0;
+    float nacc[NRW][NN], vacc[NRW];
 #pragma unroll
-    for (int r = 0; r < RR; ++r) {
+    for (int r = 0; r < NRW; ++r) {
         vacc[r] = 0.0f;
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
     }
-    for (int i = 0; i < ng; ++i) run_octave<METHOD, RW>(nacc, vacc, sm, corners, P, nt + i, i, tx, ty, ng);
-    run_fine<METHOD, RW, 6>(nacc, vacc, fine, rb, s, N, nt, tx, ty);
-    run_fine<METHOD, RW, 5>(nacc, vacc, fine, rb, s, N, nt, tx, ty);
-    run_fine<METHOD, RW, 4>(nacc, vacc, fine, rb, s, N, nt, tx, ty);
-    run_fine<METHOD, RW, 3>(nacc, vacc, fine, rb, s, N, nt, tx, ty);
+    for (int i = 0; i < ng; ++i) run_octave<METHOD, RW>(nacc, vacc, sm, corners, P, nt + i, i, tx, ty, ng, par);
+    run_fine<METHOD, RW, 6>(nacc, vacc, fine, rb, s, N, nt, tx, ty, par);
+    run_fine<METHOD, RW, 5>(nacc, vacc, fine, rb, s, N, nt, tx, ty, par);
+    run_fine<METHOD, RW, 4>(nacc, vacc, fine, rb, s, N, nt, tx, ty, par);
+    run_fine<METHOD, RW, 3>(nacc, vacc, fine, rb, s, N, nt, tx, ty, par);
 #pragma unroll
-    for (int r = 0; r < RR; ++r)
+    for (int r = 0; r < NRW; ++r)
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] += vacc[r];
     if (Deg<METHOD>::value <= 4 && nt > 0) {  // uniform over the CTA
         __syncthreads();
-        add_tile_grid<METHOD, RW>(nacc, G, tx, ty);
+        add_tile_grid<METHOD, RW>(nacc, G, tx, ty, par);
+    }
+    // the run and tile octaves' sum at the node columns of all RR rows
+    float rowv[RR][NN];
+    if constexpr (!node_rows<METHOD, RW>()) {
+#pragma unroll
+        for (int r = 0; r < RR; ++r)
+#pragma unroll
+            for (int q = 0; q < NN; ++q) rowv[r][q] = nacc[r][q];
+    } else {
+        // Mirrored block rows (even thread: y; odd thread: 7 - y): own nodes
+        // at 0, 2, the partner's at 5, 7; rows 1 and 3 interpolated with the
+        // node columns' Lagrange weights (nodes at 0, 2, 5, 7).
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const float p5 = __shfl_xor_sync(0xffffffffu, nacc[1][q], 8);
+            const float p7 = __shfl_xor_sync(0xffffffffu, nacc[0][q], 8);
+            float v[4];
+            v[0] = nacc[0][q];
+            v[2] = nacc[1][q];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int y = 2 * j + 1;
+                v[y] = fmaf(lagrange<3, 8>(y, 3), p7, fmaf(lagrange<3, 8>(y, 2), p5,
+                           fmaf(lagrange<3, 8>(y, 1), v[2], lagrange<3, 8>(y, 0) * v[0])));
+            }
+#pragma unroll
+            for (int r = 0; r < RR; ++r) rowv[r][q] = par ? v[RR - 1 - r] : v[r];
+        }
     }
     // The -3 amp offsets of all lattice octaves (FieldPlan::lat_bias) start
     // every sample's sum: added to the node columns, and the first term of the
@@ -662,11 +725,11 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
         for (int c = 0; c < RW; ++c) {
             const int q = node_of_col<D, RW>(c);
             if (q >= 0) {
-                acc[r][c] = nacc[r][q] + lat;
+                acc[r][c] = rowv[r][q] + lat;
             } else {
                 float v = lat;
 #pragma unroll
-                for (int m = 0; m < NN; ++m) v = fmaf(lagrange<D, RW>(c, m), nacc[r][m], v);
+                for (int m = 0; m < NN; ++m) v = fmaf(lagrange<D, RW>(c, m), rowv[r][m], v);
                 acc[r][c] = v;
             }
         }

@@ -24,16 +24,19 @@ RW samples wide ("run" octaves):
                 y's once per row (pcg3d 12 + 2 for the row word, grid index 1:
                 24, 21 and 15 -- the zero-gradient model needs word 0 alone,
                 whose last cross steps of y and z are not taken);
-  run octaves, per thread and octave: prep + RR rows x (row reduction + one
+  run octaves, per thread and octave: prep + NR rows x (row reduction + one
                 add of the row's V0 + (eval - 1) at each of the d+1 node
-                columns); once per thread RR x (d+1) adds of the rows' V0 sums
-                to the nodes and RR rows x (RW - d - 1) columns x (d+1) FMA of
-                interpolation;
+                columns); once per thread NR x (d+1) adds of the rows' V0 sums
+                to the nodes, (RR - NR) rows x (d+1) node columns x (d+1) FMA
+                of interpolation along y and RR rows x (RW - d - 1) columns x
+                (d+1) FMA along x.  NR = rows a thread evaluates: RR, or 2 of
+                its 4 with degree 3 and runs of 8 (node rows: a thread pair's
+                8 x 8 block at rows 0, 2, 5, 7);
   tile octaves (cells >= 64 samples, when summed at the tile nodes): per tile
                 (d+1)^2 nodes x nt x (2 (coordinate + basis) + prep + row + eval)
                 and (lanes a node - 1) adds a node; degree 3: per tile the
                 tile polynomial at 64 rows x 4 node columns (4 FMA each), per
-                thread RR x (d+1)^2 FMA to its node columns; other degrees:
+                thread NR x (d+1)^2 FMA to its node columns; other degrees:
                 per thread RR x (d+1)^2 FMA to the thread's rows and
                 RR x (d+1)^2 to its node columns; no basis tables for these
                 octaves;
@@ -136,11 +139,12 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8, nt: int = 
         return dict(total=float(tot), per_sample=tot / (w * h))
     rr = 32 // rw
     d = DEG[kind]
+    nr = 2 if (d == 3 and rw == 8) else rr  # rows a thread evaluates (node rows)
     st = _staged(spc, octaves)
     nrun = sum(1 for _, spci in st if spci >= rw) - nt
     lut = tiles * nrun * ((64 // rw) * (d + 1) + 64) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
-    evalops = threads * rr * (rw - d - 1) * (d + 1) + threads * rr * (d + 1)
+    evalops = threads * rr * (rw - d - 1) * (d + 1) + threads * nr * (d + 1) + threads * (rr - nr) * (d + 1) * (d + 1)
     prep, row, smp = MODEL_OPS[kind]
     if nt:
         nodes = (d + 1) ** 2
@@ -148,7 +152,7 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8, nt: int = 
         evalops += tiles * nodes * nt * (2 * (COORD_OPS + BASIS_OPS[kind]) + prep + row + smp)
         evalops += tiles * nodes * (parts - 1)  # adds across the lanes of a node
         if d == 3:
-            evalops += tiles * 64 * (d + 1) * (d + 1) + threads * rr * (d + 1) ** 2
+            evalops += tiles * 64 * (d + 1) * (d + 1) + threads * nr * (d + 1) ** 2
         else:
             evalops += threads * 2 * rr * (d + 1) ** 2
     for i, spci in st:
@@ -162,7 +166,7 @@ def lane_ops_2d(kind: str, size, spc: int, octaves: int, rw: int = 8, nt: int = 
         if i < nt:
             continue
         if spci >= rw:
-            evalops += threads * (prep + rr * (row + 1 + (smp - 1) * (d + 1)))
+            evalops += threads * (prep + nr * (row + 1 + (smp - 1) * (d + 1)))
         else:
             evalops += threads * small_cell_ops(kind, rw, spci)
     n_lattice = octaves - len(st)
