@@ -241,9 +241,11 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
             o.coff = coff;
             o.magic = (uint32_t)(((uint64_t{1} << 32) + (uint64_t)o.ncx - 1) / (uint64_t)o.ncx);
             o.magic2 = (uint32_t)(((uint64_t{1} << 32) + (uint64_t)(o.ncx * o.ncy) - 1) / (uint64_t)(o.ncx * o.ncy));
-            o.rowlen = corner_slot(o.ncx - 1) + 1;
+            o.rowlen = is3d ? corner_rowlen3(o.ncx) : corner_slot(o.ncx - 1) + 1;
             if (is3d) {
-                coff += o.rowlen * o.ncy * o.ncz;
+                // blocks of 8 (cells that cover the tile) one slot apart, so that the
+                // two octaves a quarter warp reads in the tile-node sum use two bank groups
+                coff += o.rowlen * o.ncy * o.ncz + (o.rowlen == 2 ? 1 : 0);
                 cend = coff;
             } else {
                 o.coff = k >= 7 ? 4 * i : 4 * ncoarse + fine_off2(k);

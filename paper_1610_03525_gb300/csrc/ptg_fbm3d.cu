@@ -16,6 +16,11 @@
 // interpolate once; cells of 4 and 2 samples use constant in-cell positions
 // along x and y; lattice octaves take one pcg4d corner value per sample.
 //
+// Node rows (C1): the run and tile octaves' sum over the 8 rows of a thread
+// pair (ty = 2b, 2b + 1; lanes l and l ^ 4) lies in one cell of the finest
+// run octave, so, as in 2D, the pair evaluates rows 0, 2 and 7, 5 of its
+// block only (the odd thread mirrored) and interpolates the other four.
+//
 // Tile octaves (C1): an octave whose cells are 32 samples or more covers the
 // whole tile with one cell (tiles start at multiples of min(spc, tile)), so
 // over the tile it is one polynomial of degree 3 per axis, and so is the sum
@@ -32,6 +37,18 @@ namespace {
 
 constexpr int kTW = kTile3dX, kTH = kTile3dY, kTD = kTile3dZ, kThreads = 128;
 constexpr int kCols = 8, kRows = 4;
+
+// Rows a thread evaluates (node rows for degree 3) and the thread's row of
+// its k-th evaluated row (par = ty & 1).
+template <int METHOD>
+__host__ __device__ constexpr bool node_rows3() { return Deg<METHOD>::value == 3; }
+template <int METHOD>
+__host__ __device__ constexpr int n_rows3() { return node_rows3<METHOD>() ? 2 : kRows; }
+template <int METHOD>
+__device__ __forceinline__ int eval_row3(int k, int par)
+{
+    return node_rows3<METHOD>() ? (k == 0 ? 3 * par : 2 - par) : k;
+}
 
 // Shared memory (float4 units): x-basis at node columns [n8][D+1][4 tx],
 // y-basis [n8][4 r][4 ty], z-basis [n8][8 tz], staged corners (planes of
@@ -105,7 +122,8 @@ __device__ const Tile3Weights kTile3Weights = make_tile3_weights();
 __host__ __device__ constexpr int ncx3(int K) { return (kTW - 1 >> K) + 2; }
 __host__ __device__ constexpr int ncy3(int K) { return (kTH - 1 >> K) + 2; }
 __host__ __device__ constexpr int ncz3(int K) { return (kTD - 1 >> K) + 2; }
-__host__ __device__ constexpr int rowlen3(int K) { return corner_slot(ncx3(K) - 1) + 1; }
+__host__ __device__ constexpr int rowlen3(int K) { return corner_rowlen3(ncx3(K)); }
+static_assert(rowlen3(1) == 19 && rowlen3(2) == 11 && rowlen3(3) == 5 && rowlen3(4) == 3 && rowlen3(5) == 2, "");
 
 // Corner data from the four pcg4d words, pre-scaled by the octave amplitude
 // (and the gradient weight): (v, f, g, e); Perlin: (0, f, g, e), unweighted.
@@ -302,9 +320,9 @@ __device__ __forceinline__ void tile_grid3(const FieldPlan& P, const float4* __r
 }
 
 // Interpolate the tile nodes to the thread's plane (from the z-reduced table),
-// rows and node columns.
-__device__ __forceinline__ void add_tile_grid3(float (&nacc)[kRows][4], const float* __restrict__ Hz, int tx, int ty,
-                                               int tz)
+// evaluated rows and node columns.
+__device__ __forceinline__ void add_tile_grid3(float (&nacc)[2][4], const float* __restrict__ Hz, int tx, int ty,
+                                               int tz, int par)
 {
     const Tile3Weights& W = kTile3Weights;
     float hz[4][4];  // [y node][x node] in the thread's plane
@@ -323,10 +341,10 @@ __device__ __forceinline__ void add_tile_grid3(float (&nacc)[kRows][4], const fl
         wx[q] = bounds_ok(kSiteConst, tx, 4) ? __ldg(reinterpret_cast<const float4*>(W.wx[tx][q]))
                                              : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-        const float4 wy = bounds_ok(kSiteConst, ty * kRows + r, 16)
-                              ? __ldg(reinterpret_cast<const float4*>(W.wy[ty * kRows + r]))
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < 2; ++r) {
+        const int row = ty * kRows + eval_row3<kC1>(r, par);
+        const float4 wy = bounds_ok(kSiteConst, row, 16) ? __ldg(reinterpret_cast<const float4*>(W.wy[row]))
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
         float hy[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) hy[a] = fmaf(wy.w, hz[3][a], fmaf(wy.z, hz[2][a], fmaf(wy.y, hz[1][a], wy.x * hz[0][a])));
@@ -337,11 +355,11 @@ __device__ __forceinline__ void add_tile_grid3(float (&nacc)[kRows][4], const fl
 }
 
 template <int METHOD>
-__device__ __forceinline__ void run8_octave3(float (&nacc)[kRows][Deg<METHOD>::value + 1], float (&vacc)[kRows],
-                                             const float4* __restrict__ sm, const FieldPlan& P, int i, int tx,
-                                             int ty, int tz, int n8)
+__device__ __forceinline__ void run8_octave3(float (&nacc)[n_rows3<METHOD>()][Deg<METHOD>::value + 1],
+                                             float (&vacc)[n_rows3<METHOD>()], const float4* __restrict__ sm,
+                                             const FieldPlan& P, int i, int tx, int ty, int tz, int n8, int par)
 {
-    constexpr int NN = Deg<METHOD>::value + 1;
+    constexpr int NN = Deg<METHOD>::value + 1, NRW = n_rows3<METHOD>();
     const OctPlan& op = P.oct[i];
     const float4* ylut = sm + xnode_words3<METHOD>(n8);
     const float4* zlut = ylut + n8 * 16;
@@ -352,8 +370,8 @@ __device__ __forceinline__ void run8_octave3(float (&nacc)[kRows][Deg<METHOD>::v
 #pragma unroll
     for (int q = 0; q < NN; ++q) xb[q] = sld(kSiteTable, &sm[(i * NN + q) * 4 + tx]);
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-        const float4 yb = sld(kSiteTable, &ylut[i * 16 + r * 4 + ty]);
+    for (int r = 0; r < NRW; ++r) {
+        const float4 yb = sld(kSiteTable, &ylut[i * 16 + eval_row3<METHOD>(r, par) * 4 + ty]);
         const Row R = row_of(c, yb.x, yb.y, yb.z);
         vacc[r] += R.V0;  // the same at every node: summed once per row
 #pragma unroll
@@ -461,8 +479,13 @@ __device__ __forceinline__ void store_tile3(const FieldPlan& P, const float (&ac
     }
 }
 
+// Six CTAs a SM for C1 (at most 80 registers; the compiler's own choice is
+// 86, which leaves five); the other models keep the compiler's choice.
+template <int METHOD>
+constexpr int min_ctas3() { return METHOD == kC1 ? 6 : 0; }
+
 template <int METHOD, typename OutT>
-__global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__ FieldPlan P)
+__global__ void __launch_bounds__(kThreads, min_ctas3<METHOD>()) fbm3d_kernel(const __grid_constant__ FieldPlan P)
 {
     constexpr int D = Deg<METHOD>::value, NN = D + 1;
     extern __shared__ float4 sm[];
@@ -478,22 +501,48 @@ __global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__
     float* Hz = reinterpret_cast<float*>(sm + corner_base3<METHOD>(n8) + P.ncorner);
     if (nt > 0) tile_grid3<METHOD>(P, sm + corner_base3<METHOD>(n8), Hz, j0x, j0y, j0z, nt);
 
-    float nacc[kRows][NN], vacc[kRows];
+    constexpr int NRW = n_rows3<METHOD>();
+    const int par = node_rows3<METHOD>() ? (ty & 1) : 0;
+    float nacc[NRW][NN], vacc[NRW];
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
+    for (int r = 0; r < NRW; ++r) {
         vacc[r] = 0.0f;
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] = 0.0f;
     }
-    for (int i = nt; i < n8; ++i) run8_octave3<METHOD>(nacc, vacc, sm, P, i, tx, ty, tz, n8);
+    for (int i = nt; i < n8; ++i) run8_octave3<METHOD>(nacc, vacc, sm, P, i, tx, ty, tz, n8, par);
 #pragma unroll
-    for (int r = 0; r < kRows; ++r)
+    for (int r = 0; r < NRW; ++r)
 #pragma unroll
         for (int q = 0; q < NN; ++q) nacc[r][q] += vacc[r];
-    if constexpr (NN == 4) {
+    // the run and tile octaves' sum at the node columns of all rows
+    float rowv[kRows][NN];
+    if constexpr (!node_rows3<METHOD>()) {
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+#pragma unroll
+            for (int q = 0; q < NN; ++q) rowv[r][q] = nacc[r][q];
+    } else {
         if (nt > 0) {  // uniform over the CTA
             __syncthreads();
-            add_tile_grid3(nacc, Hz, tx, ty, tz);
+            add_tile_grid3(nacc, Hz, tx, ty, tz, par);
+        }
+        // mirrored block rows: own nodes at 0, 2, the partner's at 5, 7
+#pragma unroll
+        for (int q = 0; q < NN; ++q) {
+            const float p5 = __shfl_xor_sync(0xffffffffu, nacc[1][q], 4);
+            const float p7 = __shfl_xor_sync(0xffffffffu, nacc[0][q], 4);
+            float v[4];
+            v[0] = nacc[0][q];
+            v[2] = nacc[1][q];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int y = 2 * j + 1;
+                v[y] = fmaf(lagrange<3>(y, 3), p7, fmaf(lagrange<3>(y, 2), p5,
+                           fmaf(lagrange<3>(y, 1), v[2], lagrange<3>(y, 0) * v[0])));
+            }
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) rowv[r][q] = par ? v[kRows - 1 - r] : v[r];
         }
     }
     // the -3 amp offsets of all lattice octaves start every sample's sum
@@ -506,11 +555,11 @@ __global__ void __launch_bounds__(kThreads) fbm3d_kernel(const __grid_constant__
         for (int c = 0; c < kCols; ++c) {
             const int q = node_of_col<D>(c);
             if (q >= 0) {
-                acc[r][c] = nacc[r][q] + lat;
+                acc[r][c] = rowv[r][q] + lat;
             } else {
                 float v = lat;
 #pragma unroll
-                for (int m = 0; m < NN; ++m) v = fmaf(lagrange<D>(c, m), nacc[r][m], v);
+                for (int m = 0; m < NN; ++m) v = fmaf(lagrange<D>(c, m), rowv[r][m], v);
                 acc[r][c] = v;
             }
         }

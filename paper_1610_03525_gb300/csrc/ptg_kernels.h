@@ -18,6 +18,16 @@ cudaError_t set_kernel_smem(const void* kfn, size_t smem);
 constexpr int kTile2dX = 64, kTile2dY = 64;
 constexpr int kTile3dX = 32, kTile3dY = 16, kTile3dZ = 8;
 
+// Float4 slots per staged corner row of a 3D tile with ncx corners a row.
+// Rows longer than two slots take an odd length, so that the corner loads
+// of two neighbouring rows (threads ty and ty + 1 of a quarter warp) land
+// in different 16-byte bank groups; rows of two (cells that cover the tile)
+// keep the x + 2 y + 4 z layout the staging writes.
+__host__ __device__ constexpr int corner_rowlen3(int ncx)
+{
+    return corner_slot(ncx - 1) + 1 > 2 ? ((corner_slot(ncx - 1) + 1) | 1) : 2;
+}
+
 size_t fbm2d_smem_bytes(const FieldPlan& P);
 cudaError_t launch_fbm2d(const FieldPlan& P, int method, int s, cudaStream_t stream);
 

@@ -59,11 +59,12 @@ RW samples wide ("run" octaves):
                 no work.
 3D tiles of 32 x 16 x 8 (each thread 8 x 4 x 1): the same regimes, with a
 reduction along z of the cell's four corner columns (32 ops) before each cell
-is used, and each run octave's rows summing their V0 once; for C1 with two or
-more octaves of cells >= 32 samples, those are tile octaves: 64 nodes x nt x
-(3 x (coordinate + basis) + 32 + 9 + 4 + 1) + 64 a tile, the nodes reduced
-along z for each of the 8 planes (8 x 16 x 4 FMA a tile) and 2 x 64 FMA of
-interpolation a thread, no basis tables; basis tables of n8 x (4 (d+1) + 24)
+is used, and each run octave's rows summing their V0 once; C1 evaluates 2 of
+its 4 rows (node rows, as in 2D: 2 x 16 FMA of interpolation along y); for C1
+with two or more octaves of cells >= 32 samples, those are tile octaves: 64
+nodes x nt x (3 x (coordinate + basis) + 32 + 9 + 4 + 1) + 64 a tile, the
+nodes reduced along z for each of the 8 planes (8 x 16 x 4 FMA a tile) and
+2 x 16 FMA of interpolation a thread and evaluated row, no basis tables; basis tables of n8 x (4 (d+1) + 24)
 entries, corners 38 (pcg4d 20, four words 12, index 6; Perlin three words:
 35; cells of 2 samples, hashed two rows a warp with the LCG steps of x per
 lane and of y, z per row: 31 and 28) and lattice samples 14 (pcg4d word 0
@@ -207,14 +208,15 @@ def lane_ops_3d(kind: str, size, spc: int, octaves: int, f: float = 2.0) -> dict
     nt = nt if nt >= 2 else 0
     lut = tiles * (n8 - nt) * (4 * (d + 1) + 24) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
-    evalops = threads * 4 * (7 - d) * (d + 1) + threads * 4 * (d + 1)
+    nr = 2 if d == 3 else 4  # rows a thread evaluates (node rows), of its 4
+    evalops = threads * 4 * (7 - d) * (d + 1) + threads * nr * (d + 1) + threads * (4 - nr) * (d + 1) * (d + 1)
     if nt:
         # 64 nodes x nt octaves x (3 axes of coordinate + basis, z reduction 32,
         # row 9, evaluation 4, accumulate 1), one shuffle-add a node; the nodes
-        # reduced along z for 8 planes (8 x 16 x 4 FMA); per thread 2 x 64 FMA
-        # of interpolation (y, x)
+        # reduced along z for 8 planes (8 x 16 x 4 FMA); per thread and
+        # evaluated row 2 x 16 FMA of interpolation (y, x)
         evalops += tiles * (64 * nt * (3 * (COORD_OPS + BASIS_OPS[kind]) + 32 + 9 + 4 + 1) + 64 + 8 * 16 * 4)
-        evalops += threads * 128
+        evalops += threads * nr * 32
     for i, spci in st:
         k = spci.bit_length() - 1
         nc = ((31 >> min(k, 31)) + 2) * ((15 >> min(k, 31)) + 2) * ((7 >> min(k, 31)) + 2)
@@ -226,7 +228,7 @@ def lane_ops_3d(kind: str, size, spc: int, octaves: int, f: float = 2.0) -> dict
         if i < nt:
             continue
         if spci >= 8:
-            evalops += threads * (32 + 4 + 4 * (9 + 1 + 3 * (d + 1)))
+            evalops += threads * (32 + 4 + nr * (9 + 1 + 3 * (d + 1)))
         elif spci == 4:
             evalops += threads * (2 * (32 + 4 + 1 + 3 * 9) + 24 * 4 + 8)
         else:
