@@ -241,10 +241,9 @@ int ptg_batch_free(ptg_batch_plan* plan);
  * by every device that loads the library until the process exits) instead of
  * context-owned allocations; no cudaMalloc, cudaFree or other allocator is
  * called.  The caller owns every output buffer.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls share the array and clear its
- * counter: calls that overlap on the GPU race, so order them (one stream, or
- * events).  n > 256 returns PTG_ERR_INVALID.  The paper has no counterpart;
+ * looks up the array's device address (cudaGetSymbolAddress).  All calls
+ * share the array and clear its counter: calls that overlap on the GPU race,
+ * so order them (one stream, or events).  n > 256 returns PTG_ERR_INVALID.  The paper has no counterpart;
  * this is a deployment aid. */
 int ptg_batch_noalloc(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n, void* stream);
 
