@@ -392,7 +392,8 @@ __device__ __forceinline__ void run_fine(float (&nacc)[n_rows<METHOD, RW>()][Deg
 // Cells of CW = 8, 4 or 2 samples (CW < RW): the in-cell position of column c
 // is (c mod CW) / CW, a constant.  Row positions are constants too when a
 // thread's rows cover whole cells (RR >= CW); otherwise (RR < CW) they depend
-// on the thread's row and the row basis is evaluated once per octave.
+// on the thread's row and the row basis is evaluated once per octave.  Each
+// pair of neighbouring columns is added to the sums by one paired add.
 template <int METHOD, int RW, int CW>
 __device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], const float4* __restrict__ fine,
                                              int tx, int ty)
@@ -418,9 +419,14 @@ __device__ __forceinline__ void small_octave(float (&acc)[Shape<RW>::RR][RW], co
             for (int rr = 0; rr < RPC; ++rr) {
                 const Row R = (kConstRows && rr == 0) ? Model<METHOD>::row0(c) : Model<METHOD>::row(c, yb[rr]);
 #pragma unroll
-                for (int q = 0; q < CW; ++q) {
-                    const float h = q == 0 ? R.V0 : Model<METHOD>::eval(R, axis_basis<METHOD>(q * inv));
-                    acc[yq * RPC + rr][xq * CW + q] += h;
+                for (int q = 0; q < CW; q += 2) {
+                    const float h0 = q == 0 ? R.V0 : Model<METHOD>::eval(R, axis_basis<METHOD>(q * inv));
+                    const float h1 = Model<METHOD>::eval(R, axis_basis<METHOD>((q + 1) * inv));
+                    float& a0 = acc[yq * RPC + rr][xq * CW + q];
+                    float& a1 = acc[yq * RPC + rr][xq * CW + q + 1];
+                    const float2 a = __fadd2_rn(make_float2(a0, a1), make_float2(h0, h1));
+                    a0 = a.x;
+                    a1 = a.y;
                 }
             }
         }
@@ -550,6 +556,8 @@ __device__ __forceinline__ void add_tile_grid(float (&nacc)[n_rows<METHOD, RW>()
 // One lattice octave: every sample sits on a lattice point.  Each adds
 // amp unit_mant(h) = amp (unit_value(h) + 3): the -3 amp terms of all lattice
 // octaves (FieldPlan::lat_bias) start the rows' sums in fbm2d_tile instead.
+// Neighbouring columns share one paired FMA (two FP32 FMAs in one
+// instruction, each rounded as fmaf).
 template <int RW>
 __device__ __forceinline__ void lattice_octave(float (&acc)[Shape<RW>::RR][RW], const OctPlan& op, uint32_t jx,
                                                uint32_t jy)
@@ -557,14 +565,19 @@ __device__ __forceinline__ void lattice_octave(float (&acc)[Shape<RW>::RR][RW], 
     const int sh = op.k;
     const uint32_t z1 = pcg_lcg(op.key), dx = 1664525u << sh;  // x's LCG step advances by dx a column
     const uint32_t x0 = op.ox + (jx << sh);
+    const float2 amp2 = make_float2(op.amp, op.amp);
 #pragma unroll
     for (int r = 0; r < Shape<RW>::RR; ++r) {
         const uint32_t y1 = pcg_lcg(op.oy + ((jy + r) << sh));
         const uint32_t base = pcg3d_run_base(x0, y1, z1);
 #pragma unroll
-        for (int c = 0; c < RW; ++c) {
-            const uint32_t h = pcg3d_run_value(base + (uint32_t)c * dx, y1, z1);
-            acc[r][c] = fmaf(op.amp, unit_mant(h), acc[r][c]);
+        for (int c = 0; c < RW; c += 2) {
+            const uint32_t h0 = pcg3d_run_value(base + (uint32_t)c * dx, y1, z1);
+            const uint32_t h1 = pcg3d_run_value(base + (uint32_t)(c + 1) * dx, y1, z1);
+            const float2 a = __ffma2_rn(make_float2(unit_mant(h0), unit_mant(h1)), amp2,
+                                        make_float2(acc[r][c], acc[r][c + 1]));
+            acc[r][c] = a.x;
+            acc[r][c + 1] = a.y;
         }
     }
 }

@@ -406,37 +406,49 @@ __device__ __forceinline__ void small_octave3(float (&acc)[kRows][kCols], const 
                     R = row_of(c, yb.x, yb.y, yb.z);
                 }
 #pragma unroll
-                for (int q = 0; q < CW; ++q) {
-                    float h;
+                for (int q = 0; q < CW; q += 2) {  // neighbouring columns: one paired add
+                    float h0;
                     if (q == 0) {
-                        h = R.V0;
+                        h0 = R.V0;
                     } else {
                         const float4 xb = axis_basis<METHOD>(q * inv);
-                        h = eval_row(R, xb.x, xb.y, xb.z);
+                        h0 = eval_row(R, xb.x, xb.y, xb.z);
                     }
-                    acc[yq * CW + rr][xq * CW + q] += h;
+                    const float4 xb1 = axis_basis<METHOD>((q + 1) * inv);
+                    const float h1 = eval_row(R, xb1.x, xb1.y, xb1.z);
+                    float& a0 = acc[yq * CW + rr][xq * CW + q];
+                    float& a1 = acc[yq * CW + rr][xq * CW + q + 1];
+                    const float2 a = __fadd2_rn(make_float2(a0, a1), make_float2(h0, h1));
+                    a0 = a.x;
+                    a1 = a.y;
                 }
             }
         }
     }
 }
 
-// Adds amp unit_mant(h); the -3 amp terms of all lattice octaves
-// (FieldPlan::lat_bias) start every sample's sum instead.
+// Adds amp unit_mant(h), neighbouring columns by one paired FMA; the -3 amp
+// terms of all lattice octaves (FieldPlan::lat_bias) start every sample's sum
+// instead.
 __device__ __forceinline__ void lattice_octave3(float (&acc)[kRows][kCols], const OctPlan& op, uint32_t jx,
                                                 uint32_t jy, uint32_t jz)
 {
     const int sh = op.k;
     const uint32_t z1 = pcg_lcg(op.oz + (jz << sh)), w1 = pcg_lcg(op.key);
     const uint32_t dx = 1664525u << sh, x0 = op.ox + (jx << sh);  // x's LCG step advances by dx a column
+    const float2 amp2 = make_float2(op.amp, op.amp);
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
         const uint32_t y1 = pcg_lcg(op.oy + ((jy + r) << sh));
         const uint32_t base = pcg4d_run_base(x0, y1, w1);
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-            const uint32_t h = pcg4d_run_value(base + (uint32_t)c * dx, y1, z1, w1);
-            acc[r][c] = fmaf(op.amp, unit_mant(h), acc[r][c]);
+        for (int c = 0; c < kCols; c += 2) {
+            const uint32_t h0 = pcg4d_run_value(base + (uint32_t)c * dx, y1, z1, w1);
+            const uint32_t h1 = pcg4d_run_value(base + (uint32_t)(c + 1) * dx, y1, z1, w1);
+            const float2 a = __ffma2_rn(make_float2(unit_mant(h0), unit_mant(h1)), amp2,
+                                        make_float2(acc[r][c], acc[r][c + 1]));
+            acc[r][c] = a.x;
+            acc[r][c + 1] = a.y;
         }
     }
 }
