@@ -121,11 +121,12 @@ typedef struct {
     uint32_t struct_size; /* sizeof(ptg_field_desc)                            */
     int32_t dims;         /* 2 or 3                                            */
     int64_t size[3];      /* samples per axis (x, y, z), each in [1, 2^30]; unused = 1.
-                             One device launch covers at most 65535 tiles
-                             along the slowest axis: H <= 4194240 (2D, 64-row
-                             tiles), D <= 524280 (3D, 8-plane tiles), else
-                             PTG_ERR_UNSUPPORTED; ptg_generate_host has no
-                             such bound (it works in bands)                 */
+                             A 3D field takes at most 65535 tiles of 16
+                             rows along y (H <= 1048560), else
+                             PTG_ERR_UNSUPPORTED.  Fields taller than one
+                             launch's 65535 tiles along the slowest axis
+                             (2D H > 4194240, 3D D > 524280) run as
+                             consecutive launches on the same stream       */
     int64_t spc;          /* samples per base cell, in [1, 2^30]; a value
                              that is not a power of two runs the per-sample
                              generators (see lacunarity)                    */

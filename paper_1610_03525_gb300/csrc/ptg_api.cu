@@ -218,7 +218,7 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
     P->tiles_y = (P->H + TH - 1) / TH;
     P->tiles_z = (P->D + TD - 1) / TD;
     if (P->tiles_y > 65535 || P->tiles_z > 65535)
-        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "field too tall for one launch (%d x %d tiles along y/z)",
+        return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "%d x %d tiles along y/z: at most 65535 along y in 3D",
                         P->tiles_y, P->tiles_z);
     const int esz = d->dtype == PTG_F16 ? 2 : 4;
     P->vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((P->W * esz) % 16 == 0);
@@ -512,8 +512,17 @@ int ptg_kernel_method(int kind, const ptg_field_desc* d)
     }
 }
 
-int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void* out, int64_t band_start,
-                    int64_t band_len, cudaStream_t st)
+// Rows (2D) or planes (3D) of the slowest axis that one launch covers: a
+// grid takes at most 65535 tiles along y and z.
+int64_t ptg_launch_rows(const ptg_field_desc* d)
+{
+    return d->dims == 3 ? int64_t{65535} * kTile3dZ : int64_t{65535} * kTile2dY;
+}
+
+// One launch: rows [band_start, band_start + band_len) of the slowest axis into
+// out (the band's first row), with band_len <= ptg_launch_rows.
+static int launch_band(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void* out, int64_t band_start,
+                       int64_t band_len, cudaStream_t st)
 {
     cudaError_t e;
     if (kind == kKindSimplex && d->dims == 3) {
@@ -544,6 +553,24 @@ int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void
         e = d->dims == 3 ? launch_fbm3d(P, method, s, st) : launch_fbm2d(P, method, s, st);
     }
     if (e != cudaSuccess) return ptg_cuda_fail(ctx, e, "kernel launch");
+    return PTG_OK;
+}
+
+int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void* out, int64_t band_start,
+                    int64_t band_len, cudaStream_t st)
+{
+    // fields taller than one launch's tiles: consecutive launches of whole-tile
+    // bands on the same stream (band starts stay multiples of the tile, so the
+    // cell alignment of every band is the field's own)
+    const int64_t step = ptg_launch_rows(d);
+    const size_t esz = d->dtype == PTG_F16 ? 2 : 4;
+    const size_t slab = (size_t)d->size[0] * esz * (d->dims == 3 ? (size_t)d->size[1] : 1);
+    for (int64_t done = 0; done < band_len; done += step) {
+        const int64_t len = band_len - done < step ? band_len - done : step;
+        void* o = out ? static_cast<void*>(static_cast<char*>(out) + (size_t)done * slab) : nullptr;
+        const int rc = launch_band(ctx, kind, d, s, o, band_start + done, len, st);
+        if (rc != PTG_OK) return rc;
+    }
     return PTG_OK;
 }
 
@@ -671,7 +698,10 @@ int ptg_validate(const ptg_field_desc* d, int32_t method, char* msg, int32_t msg
     int s = 0;
     int rc = ptg_check_desc(&scratch, d, kind, &s);
     if (rc == PTG_OK) {
-        const int64_t slow = d->dims == 3 ? d->size[2] : d->size[1];
+        // the first launch's band (ptg_launch_plan splits taller fields; later bands
+        // differ only in their start)
+        int64_t slow = d->dims == 3 ? d->size[2] : d->size[1];
+        if (slow > ptg_launch_rows(d)) slow = ptg_launch_rows(d);
         if (kind == kKindSimplex && d->dims == 3) {
             Simplex3Plan P;
             rc = ptg_make_simplex3_plan(&scratch, d, nullptr, 0, slow, &P);

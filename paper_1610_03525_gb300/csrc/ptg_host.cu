@@ -46,7 +46,7 @@ extern "C" int ptg_generate_host(ptg_ctx* ctx, const ptg_field_desc* d, int32_t 
     const int64_t tile = is3d ? ptg::kTile3dZ : ptg::kTile2dY;
     int64_t band = (int64_t)(kBandBytes / slab) / tile * tile;
     if (band < tile) band = tile;
-    if (band > 65535 * tile) band = 65535 * tile;  // one launch covers at most 65535 tiles along it
+    if (band > ptg_launch_rows(d)) band = ptg_launch_rows(d);  // one launch a band
     if (band > total) band = total;
     const size_t need = 2 * (size_t)band * slab;
     if (ctx->stage_bytes < need) {

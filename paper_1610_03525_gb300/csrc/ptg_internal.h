@@ -95,8 +95,11 @@ int ptg_make_general_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, voi
                           int64_t band_len, ptg::GeneralPlan* P);
 int ptg_make_general3_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int64_t band_start,
                            int64_t band_len, ptg::General3Plan* P);
+// Rows [band_start, band_start + band_len) of the slowest axis into out (the
+// band's first row), as consecutive launches of at most ptg_launch_rows rows.
 int ptg_launch_plan(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, void* out, int64_t band_start,
                     int64_t band_len, cudaStream_t st);
+int64_t ptg_launch_rows(const ptg_field_desc* d);
 int ptg_kernel_method(int kind, const ptg_field_desc* d);
 
 void ptg_host_release(ptg_ctx* ctx);

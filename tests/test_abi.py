@@ -102,21 +102,27 @@ def test_desc_layout_matches_header(P):
     (dict(variant=1), 0, -1),                         # blend byte on a polynomial field
     (dict(variant=0x100), 2, -2),                     # no shape for OpenSimplex
     (dict(variant=0x200, dims=3, size=(32, 32, 32)), 0, -2),
-    # size limits: 2^30 samples per axis and per cell; 65535 tiles along the
-    # slowest axis of one launch (64-row tiles in 2D, 8-plane tiles in 3D)
+    # size limits: 2^30 samples per axis and per cell; fields taller than one
+    # launch (65535 tiles: 64-row tiles in 2D, 8-plane tiles in 3D) run as
+    # several; a 3D field takes at most 65535 16-row tiles along y
     (dict(size=(1 << 31, 1)), 0, -1),
     (dict(size=(5, 5), spc=1 << 31), 0, -1),
     (dict(size=(5, 5), spc=1 << 30), 0, 0),
     (dict(size=(64, 64), offset=((1 << 31) - 32, 0, 0)), 0, -1),
     (dict(size=(64, 64), offset=((1 << 31) - 64, 0, 0)), 0, 0),
     (dict(size=(64, 65535 * 64)), 0, 0),
-    (dict(size=(64, 65535 * 64 + 1)), 0, -2),
-    (dict(size=(64, 65535 * 64 + 1)), 2, -2),
-    (dict(size=(64, 65535 * 64 + 1), spc=3), 0, -2),
+    (dict(size=(64, 65535 * 64 + 1)), 0, 0),
+    (dict(size=(64, 65535 * 64 + 1)), 2, 0),
+    (dict(size=(64, 65535 * 64 + 1), spc=3), 0, 0),
+    (dict(size=(64, 1 << 30)), 0, 0),
     (dict(dims=3, size=(32, 32, 65535 * 8)), 0, 0),
-    (dict(dims=3, size=(32, 32, 65535 * 8 + 1)), 0, -2),
-    (dict(dims=3, size=(32, 32, 65535 * 8 + 1)), 2, -2),
-    (dict(dims=3, size=(32, 32, 65535 * 8 + 1), spc=3), 0, -2),
+    (dict(dims=3, size=(32, 32, 65535 * 8 + 1)), 0, 0),
+    (dict(dims=3, size=(32, 32, 65535 * 8 + 1)), 2, 0),
+    (dict(dims=3, size=(32, 32, 65535 * 8 + 1), spc=3), 0, 0),
+    (dict(dims=3, size=(32, 65535 * 16, 8)), 0, 0),
+    (dict(dims=3, size=(32, 65535 * 16 + 1, 8)), 0, -2),
+    (dict(dims=3, size=(32, 65535 * 16 + 1, 8)), 2, -2),
+    (dict(dims=3, size=(32, 65535 * 16 + 1, 8), spc=3), 0, -2),
 ])
 def test_validation_codes(P, kw, method, code):
     d = P.make_desc(**kw)

@@ -513,6 +513,36 @@ def test_sampled_3d_512_n8(ctx, kind, dtype):
 
 
 # ---------------------------------------------------------------------------
+# fields taller than one launch (65535 tiles along the slowest axis) run as
+# consecutive launches; the samples on both sides of the seam match the oracle
+# and every sample is written
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,dims,lac", [("c1", 2, 2.0), ("opensimplex", 2, 2.0), ("c1", 2, 1.9),
+                                           ("c1", 3, 2.0), ("perlin_s5", 3, 2.0)])
+def test_field_taller_than_one_launch(ctx, kind, dims, lac):
+    tile = 64 if dims == 2 else 8
+    seam = 65535 * tile
+    size = (16, seam + 3 * tile + 7) if dims == 2 else (8, 16, seam + 13)
+    spc, octaves = (64, 5) if dims == 2 else (32, 5)
+    out = gpu_field(ctx, kind, dims=dims, size=size, spc=spc, octaves=octaves, seed=5, lacunarity=lac,
+                    origin=(3, -7, 2))
+    assert not torch.isnan(out).any()
+    rng = np.random.default_rng(11)
+    slow = size[dims - 1]
+    rows = np.concatenate([np.arange(seam - 6, seam + 6), np.arange(slow - 3, slow), [0, 1]])
+    if dims == 2:
+        near = np.stack(np.meshgrid(np.arange(size[0]), rows, indexing="ij"), -1).reshape(-1, 2)
+    else:
+        near = np.stack(np.meshgrid(np.arange(size[0]), np.arange(size[1]), rows, indexing="ij"), -1).reshape(-1, 3)
+    rand = np.stack([rng.integers(0, n, 4096) for n in size[:dims]], -1)
+    idx = np.concatenate([near, rand]).astype(np.int64)
+    ref = oracle_at(kind, idx, dims=dims, spc=spc, octaves=octaves, seed=5, lacunarity=lac, origin=(3, -7, 2))
+    err = np.abs(gather(out, idx) - ref)
+    assert np.all(err <= tol32(octaves)), err.max()
+    del out
+
+
+# ---------------------------------------------------------------------------
 # locality (Sec. 1): windows tile the world exactly; determinism; host path
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5", "paper_gauge", "zero_grad"])
