@@ -643,7 +643,9 @@ def main():
             dL = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, seed=0, lacunarity=1.9, **kw)
             general[name + "_f32"] = time_fn(lambda o, fn=fn, dL=dL: fn(ctx, dL, o, stream), reps=3)
         line["lacunarity_1.9"] = general
-        # ridged noise (the paper's ridged mountains), same size and octave count, per-sample generator
+        # ridged noise (the paper's ridged mountains), same size and octave count: the fused ridged
+        # kernel (tiles aligned to cells); "per_sample" times the per-sample generator on the same
+        # field one sample off the cell grid (offset 1), where the fused kernel does not apply
         ridged = {}
         for name, fn, kw in [("zero_gradient", P.ptg_field, dict(smoothness=P.PTG_ZERO_GRADIENT)),
                              ("c1", P.ptg_field, dict(smoothness=P.PTG_C1)),
@@ -652,6 +654,9 @@ def main():
             kw["variant"] = kw.get("variant", 0) | P.PTG_RIDGED
             dR = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, seed=0, **kw)
             ridged[name + "_f32"] = time_fn(lambda o, fn=fn, dR=dR: fn(ctx, dR, o, stream), reps=3)
+            if name == "c1":
+                dU = P.make_desc(dims=2, size=SIZE, spc=SPC, octaves=OCTAVES, seed=0, offset=(1, 0, 0), **kw)
+                ridged["c1_f32_per_sample"] = time_fn(lambda o, fn=fn, dU=dU: fn(ctx, dU, o, stream), reps=3)
         line["ridged"] = ridged
         if rank == 0:
             line["volume3d_512_n8"] = bench_3d(P, R, ctx, stream, torch)

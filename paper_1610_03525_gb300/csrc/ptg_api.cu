@@ -124,6 +124,16 @@ bool ptg_per_sample(const ptg_field_desc* d, int spc_log2)
     return d->lacunarity != 2.0f || spc_log2 < 0 || (d->variant & PTG_RIDGED) != 0;
 }
 
+// Ridged 2D fields that the fused generator's ridged kernel takes instead:
+// frequency ratio 2, spc a power of two and tiles aligned to cells (offsets
+// multiples of min(spc, 64)), as for the fused fBm kernel.
+bool ptg_fused_ridged(const ptg_field_desc* d, int spc_log2)
+{
+    if (d->dims != 2 || !(d->variant & PTG_RIDGED) || d->lacunarity != 2.0f || spc_log2 < 0) return false;
+    const int64_t align = d->spc < kTile2dX ? d->spc : kTile2dX;
+    return d->offset[0] % align == 0 && d->offset[1] % align == 0;
+}
+
 // Argument checks common to every generator.  On success fills *spc_log2
 // (-1 when spc is not a power of two: 2D, per-sample generators).
 int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log2)
@@ -267,13 +277,15 @@ int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void*
         amp *= p;
     }
     P->lat_bias = (float)lat_bias;
+    P->grad_w = (float)w;
+    P->ridged = ptg_fused_ridged(d, s) ? 1 : 0;
     P->ncorner = cend;
     P->ncount = count;
     P->method = method;
     P->s = s;
     P->rw = 8;
     P->nt = 0;
-    if (!is3d) ptg_pick_config(ctx, d, method, s, &P->rw, &P->nt);
+    if (!is3d && !P->ridged) ptg_pick_config(ctx, d, method, s, &P->rw, &P->nt);  // ridged: 8 x 4
     const size_t smem = is3d ? fbm3d_smem_bytes(*P) : fbm2d_smem_bytes(*P);
     if (smem > (size_t)ctx->max_smem)
         return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "staging needs %zu bytes of shared memory (max %d)", smem,
@@ -535,12 +547,12 @@ static int launch_band(ptg_ctx* ctx, int kind, const ptg_field_desc* d, int s, v
         int rc = ptg_make_simplex_plan(ctx, d, out, s, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
         e = launch_opensimplex2d(P, st);
-    } else if (ptg_per_sample(d, s) && d->dims == 3) {  // any frequency ratio or spc, ridged: 3D
+    } else if (ptg_per_sample(d, s) && !ptg_fused_ridged(d, s) && d->dims == 3) {  // any f or spc, ridged: 3D
         General3Plan P;
         int rc = ptg_make_general3_plan(ctx, d, ptg_kernel_method(kind, d), out, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
         e = launch_general3d(P, st);
-    } else if (ptg_per_sample(d, s)) {  // any frequency ratio or spc, ridged: per-sample generator
+    } else if (ptg_per_sample(d, s) && !ptg_fused_ridged(d, s)) {  // any f or spc, unaligned ridged: per sample
         GeneralPlan P;
         int rc = ptg_make_general_plan(ctx, d, ptg_kernel_method(kind, d), out, s, band_start, band_len, &P);
         if (rc != PTG_OK) return rc;
@@ -708,10 +720,10 @@ int ptg_validate(const ptg_field_desc* d, int32_t method, char* msg, int32_t msg
         } else if (kind == kKindSimplex) {
             SimplexPlan P;
             rc = ptg_make_simplex_plan(&scratch, d, nullptr, s, 0, slow, &P);
-        } else if (ptg_per_sample(d, s) && d->dims == 3) {
+        } else if (ptg_per_sample(d, s) && !ptg_fused_ridged(d, s) && d->dims == 3) {
             General3Plan P;
             rc = ptg_make_general3_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, 0, slow, &P);
-        } else if (ptg_per_sample(d, s)) {
+        } else if (ptg_per_sample(d, s) && !ptg_fused_ridged(d, s)) {
             GeneralPlan P;
             rc = ptg_make_general_plan(&scratch, d, ptg_kernel_method(kind, d), nullptr, s, 0, slow, &P);
         } else {

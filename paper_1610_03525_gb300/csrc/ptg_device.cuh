@@ -61,7 +61,8 @@ struct FieldPlan {
     int32_t rw;             // 2D thread shape: run width 8 (8 x 4 samples a thread) or 16 (16 x 2)
     int32_t nt;             // 2D: octaves summed at the tile nodes (cells >= 64 samples), 0 = none
     float lat_bias;         // sum over the lattice octaves of -3 amp (see unit_mant)
-    int32_t pad[2];
+    float grad_w;           // gradient weight w of Sec. 4 (ridged fields stage unit-amplitude corners)
+    int32_t ridged;         // 1: ridged multifractal sum (2D), octave i weighted by oct[i].amp
     OctPlan oct[kMaxOctaves];
 };
 static_assert(sizeof(FieldPlan) % 16 == 0, "FieldPlan is copied in 16-byte words");

@@ -163,7 +163,8 @@ template <int D, int RW>
 __device__ const TileWeights<D, RW> kTileWeights = make_tile_weights<D, RW>();
 
 // Corners of every staged octave of a 64 x 64 tile, hashed once each (Sec. 4.1's
-// C_init), pre-scaled by the octave amplitude.  The layout fixes each fine
+// C_init), pre-scaled by the octave amplitude (kUnit: at unit amplitude, with
+// the gradient weight alone, for the ridged sum).  The layout fixes each fine
 // octave's corner grid, so the work is split into four passes with that
 // geometry known at compile time:
 //   1. octaves with cells of 64 samples or more: 2 x 2 corners each, at 4 i,
@@ -174,7 +175,7 @@ __device__ const TileWeights<D, RW> kTileWeights = make_tile_weights<D, RW>();
 //   4. cells of 2 samples (33 x 33 corners): a warp a corner row, a lane a
 //      column (column 32 by the lanes of warps 1 to 3), with x's LCG step
 //      taken once per lane and y's once per row.
-template <int METHOD>
+template <int METHOD, bool kUnit = false>
 __device__ __forceinline__ void stage_corners(const FieldPlan& P, float4* __restrict__ corners, int j0x, int j0y)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -190,7 +191,8 @@ __device__ __forceinline__ void stage_corners(const FieldPlan& P, float4* __rest
             uint32_t y = op.oy + ((uint32_t)j0y >> op.k) + (uint32_t)(c >> 1);
             uint32_t z = op.key;
             pcg3d(x, y, z);
-            sst(kSiteStage, &corners[4 * i + c], corner_data<METHOD>(x, y, z, op.amp, op.ampw));
+            sst(kSiteStage, &corners[4 * i + c],
+                corner_data<METHOD>(x, y, z, kUnit ? 1.0f : op.amp, kUnit ? P.grad_w : op.ampw));
         }
     }
     {  // 2. cells of 32, 16 and 8 samples
@@ -218,7 +220,7 @@ __device__ __forceinline__ void stage_corners(const FieldPlan& P, float4* __rest
             pcg3d(x, y, z);
             if (bounds_ok(kSiteStage, cy * op.rowlen + corner_slot(cx), op.rowlen * op.ncy))
                 sst(kSiteStage, &corners[op.coff + cy * op.rowlen + corner_slot(cx)],
-                    corner_data<METHOD>(x, y, z, op.amp, op.ampw));
+                    corner_data<METHOD>(x, y, z, kUnit ? 1.0f : op.amp, kUnit ? P.grad_w : op.ampw));
         }
     }
     if (s >= 2 && s - 2 < N) {  // 3. cells of 4 samples
@@ -226,7 +228,7 @@ __device__ __forceinline__ void stage_corners(const FieldPlan& P, float4* __rest
         constexpr int NC = corner_ncx2(2), RL = corner_rowlen2(2);
         const uint32_t bx = op.ox + ((uint32_t)j0x >> 2), by = op.oy + ((uint32_t)j0y >> 2);
         float4* cg = corners + op.coff;
-        const float amp = op.amp, ampw = op.ampw;
+        const float amp = kUnit ? 1.0f : op.amp, ampw = kUnit ? P.grad_w : op.ampw;
         const uint32_t key = op.key;
         for (int e = tid; e < NC * NC; e += kThreads) {
             const int cy = e / NC, cx = e - cy * NC;
@@ -241,7 +243,7 @@ __device__ __forceinline__ void stage_corners(const FieldPlan& P, float4* __rest
         static_assert(NC == 33, "33 corners a row: 32 lanes and one extra column");
         const uint32_t bx = op.ox + ((uint32_t)j0x >> 1), by = op.oy + ((uint32_t)j0y >> 1);
         float4* cg = corners + op.coff;
-        const float amp = op.amp, ampw = op.ampw;
+        const float amp = kUnit ? 1.0f : op.amp, ampw = kUnit ? P.grad_w : op.ampw;
         const uint32_t z1 = pcg_lcg(op.key), x1 = pcg_lcg(bx + (uint32_t)lane);
         float4* dst = cg + corner_slot(lane);
 #pragma unroll 3
@@ -780,6 +782,157 @@ __device__ __noinline__ void batch_tile(const FieldPlan& P, float4* sm, int bx, 
     else fbm2d_tile<METHOD, 8>(P, sm, bx, by);
 }
 
+// ---------------------------------------------------------------------------
+// Ridged multifractal (PTG_RIDGED), fused 2D form.  The octaves interact:
+// octave i adds p^i r_i with r_i = (1 - |h_i|)^2 w_i, h_i the unit-amplitude
+// octave and w_{i+1} = clamp(2 r_i, 0, 1), so every octave is evaluated at
+// every sample, in octave order, instead of being summed at nodes first.
+// The staging is the fBm kernel's corner staging at unit amplitude, plus
+// per-CTA tables of the x- and y-bases of the octaves whose cells are at
+// least 8 samples wide (one cell a thread); 4- and 2-sample cells take
+// constant in-cell positions and lattice octaves one hash word a sample.
+// Thread shape 8 x 4.
+// ---------------------------------------------------------------------------
+
+// Octaves with cells of 8 samples or more (their basis tables come first in
+// shared memory: 64 x-bases, then 64 y-bases an octave).
+__host__ __device__ __forceinline__ int n_ridge_tables(const FieldPlan& P)
+{
+    const int n = P.s - 2;
+    return n < 0 ? 0 : (n < P.N ? n : P.N);
+}
+
+// Table slot of tile column j's x-basis: groups of 8 rotated, so that the 8
+// threads of a quarter warp (runs 8 tx .. 8 tx + 7, one column each) read 8
+// bank groups.
+__device__ __forceinline__ int ridge_xslot(int j) { return j ^ ((j >> 3) & 7); }
+
+// One octave at two neighbouring samples: each sum gains wgt (1 - |h|)^2 w,
+// and each weight becomes that ridge doubled, clamped to [0, 1]; the products
+// and the sums as paired FP32 instructions (each half rounded as the scalar
+// operation).
+__device__ __forceinline__ void ridge2(float& acc0, float& acc1, float& w0, float& w1, float h0, float h1, float wgt)
+{
+    const float2 a = make_float2(1.0f - fabsf(h0), 1.0f - fabsf(h1));
+    const float2 r = __fmul2_rn(__fmul2_rn(a, a), make_float2(w0, w1));
+    const float2 ac = __ffma2_rn(make_float2(wgt, wgt), r, make_float2(acc0, acc1));
+    acc0 = ac.x;
+    acc1 = ac.y;
+    w0 = __saturatef(2.0f * r.x);
+    w1 = __saturatef(2.0f * r.y);
+}
+
+// Cells of CW = 4 or 2 samples (a thread's 4 rows cover whole cells): the
+// in-cell positions are constants, as in small_octave.
+template <int METHOD, int CW>
+__device__ __forceinline__ void small_ridged(float (&acc)[4][8], float (&w)[4][8], const float4* __restrict__ fine,
+                                             int tx, int ty, float wgt)
+{
+    constexpr int K = CW == 4 ? 2 : 1, NXC = 8 / CW, NYC = 4 / CW;
+    constexpr float inv = 1.0f / CW;
+    const float4* cg = fine + fine_off2(K);
+#pragma unroll
+    for (int yq = 0; yq < NYC; ++yq) {
+#pragma unroll
+        for (int xq = 0; xq < NXC; ++xq) {
+            const Cell c = load_cell(cg, corner_rowlen2(K), tx * NXC + xq, ty * NYC + yq, corner_size2(K));
+#pragma unroll
+            for (int rr = 0; rr < CW; ++rr) {
+                const Row R = rr == 0 ? Model<METHOD>::row0(c) : Model<METHOD>::row(c, axis_basis<METHOD>(rr * inv));
+#pragma unroll
+                for (int q = 0; q < CW; q += 2) {
+                    const float h0 = q == 0 ? R.V0 : Model<METHOD>::eval(R, axis_basis<METHOD>(q * inv));
+                    const float h1 = Model<METHOD>::eval(R, axis_basis<METHOD>((q + 1) * inv));
+                    const int y = yq * CW + rr, x = xq * CW + q;
+                    ridge2(acc[y][x], acc[y][x + 1], w[y][x], w[y][x + 1], h0, h1, wgt);
+                }
+            }
+        }
+    }
+}
+
+// A lattice octave: h is the corner value, unit_value of pcg3d word 0 (zero
+// for Perlin), with the row-invariant words hoisted as in lattice_octave.
+template <int METHOD>
+__device__ __forceinline__ void lattice_ridged(float (&acc)[4][8], float (&w)[4][8], const OctPlan& op, uint32_t jx,
+                                               uint32_t jy)
+{
+    const float wgt = op.amp;
+    if constexpr (METHOD == kPerlinS5 || METHOD == kPerlinS3) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; c += 2) ridge2(acc[r][c], acc[r][c + 1], w[r][c], w[r][c + 1], 0.0f, 0.0f, wgt);
+    } else {
+        const int sh = op.k;
+        const uint32_t z1 = pcg_lcg(op.key), dx = 1664525u << sh, x0 = op.ox + (jx << sh);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t y1 = pcg_lcg(op.oy + ((jy + r) << sh));
+            const uint32_t base = pcg3d_run_base(x0, y1, z1);
+#pragma unroll
+            for (int c = 0; c < 8; c += 2)
+                ridge2(acc[r][c], acc[r][c + 1], w[r][c], w[r][c + 1],
+                       unit_value(pcg3d_run_value(base + (uint32_t)c * dx, y1, z1)),
+                       unit_value(pcg3d_run_value(base + (uint32_t)(c + 1) * dx, y1, z1)), wgt);
+        }
+    }
+}
+
+template <int METHOD>
+__device__ __forceinline__ void ridged_tile(const FieldPlan& P, float4* sm, int bx, int by)
+{
+    using SH = Shape<8>;
+    const int tid = threadIdx.x, tx = tid % SH::TXN, ty = tid / SH::TXN;
+    const int x0 = bx * kTW, y0 = by * kTH, j0x = x0 + P.jx0, j0y = y0 + P.jy0;
+    const int s = P.s, N = P.N, nb = n_ridge_tables(P);
+    for (int e = tid; e < nb * 128; e += kThreads) {  // x- and y-bases of the octaves with cells >= 8
+        const int i = e >> 7, a = (e >> 6) & 1, j = e & 63;
+        const float4 b = axis_basis<METHOD>(axis_t((uint32_t)((a ? j0y : j0x) + j), i, s));
+        sst(kSiteStage, &sm[i * 128 + (a ? 64 + j : ridge_xslot(j))], b);
+    }
+    float4* corners = sm + nb * 128;
+    stage_corners<METHOD, true>(P, corners, j0x, j0y);
+    __syncthreads();
+
+    float acc[4][8], w[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            acc[r][c] = 0.0f;
+            w[r][c] = 1.0f;
+        }
+    for (int i = 0; i < nb; ++i) {  // one cell a thread; octaves in order (the weights chain)
+        const OctPlan& op = P.oct[i];
+        const Cell c = load_cell(corners + op.coff, op.rowlen, (tx * 8) >> op.k, (ty * 4) >> op.k,
+                                 op.rowlen * op.ncy);
+        const float4* xt = sm + i * 128;
+        const float wgt = op.amp;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const Row R = Model<METHOD>::row(c, sld(kSiteTable, &xt[64 + ty * 4 + r]));
+#pragma unroll
+            for (int q = 0; q < 8; q += 2)
+                ridge2(acc[r][q], acc[r][q + 1], w[r][q], w[r][q + 1],
+                       Model<METHOD>::eval(R, sld(kSiteTable, &xt[ridge_xslot(tx * 8 + q)])),
+                       Model<METHOD>::eval(R, sld(kSiteTable, &xt[ridge_xslot(tx * 8 + q + 1)])), wgt);
+        }
+    }
+    const float4* fine = corners + 4 * n_coarse(P);
+    if (s >= 2 && s - 2 < N) small_ridged<METHOD, 4>(acc, w, fine, tx, ty, P.oct[s - 2].amp);
+    if (s >= 1 && s - 1 < N) small_ridged<METHOD, 2>(acc, w, fine, tx, ty, P.oct[s - 1].amp);
+    for (int i = s; i < N; ++i) lattice_ridged<METHOD>(acc, w, P.oct[i], (uint32_t)(j0x + tx * 8), (uint32_t)(j0y + ty * 4));
+    store_tile<8>(P, acc, x0 + tx * 8, y0 + ty * 4);
+}
+
+template <int METHOD>
+__global__ void __launch_bounds__(kThreads) fbm2d_ridged_kernel(const __grid_constant__ FieldPlan P)
+{
+    extern __shared__ float4 sm[];
+    ridged_tile<METHOD>(P, sm, blockIdx.x, blockIdx.y);
+}
+
 // Persistent batched generator: resident CTAs pull tiles of many fields from
 // one work counter.  Field f owns tiles [tile_start[f], tile_start[f+1]); its
 // plan is copied to shared memory when a CTA moves to it.  Every tile runs the
@@ -834,6 +987,7 @@ __global__ void __launch_bounds__(kThreads) fbm2d_batch_kernel(const FieldPlan* 
 template <int METHOD>
 size_t smem_words(const FieldPlan& P)
 {
+    if (P.ridged) return (size_t)n_ridge_tables(P) * 128 + (size_t)P.ncorner;
     const int nt = n_tile<METHOD>(P), ng = n_generic<METHOD>(P);
     const size_t grid = nt > 0 ? (size_t)(P.rw == 16 ? grid_words<METHOD, 16>() : grid_words<METHOD, 8>()) : 0;
     const size_t xw = P.rw == 16 ? (size_t)xnode_words<METHOD, 16>(ng) : (size_t)xnode_words<METHOD, 8>(ng);
@@ -871,6 +1025,13 @@ cudaError_t launch_fbm2d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
     } while (0)
 #define PTG_LAUNCH2D(M)                                                                              \
     do {                                                                                             \
+        if (P.ridged) {                                                                              \
+            auto kfr = fbm2d_ridged_kernel<M>;                                                       \
+            cudaError_t e = set_kernel_smem((const void*)kfr, smem);                                 \
+            if (e != cudaSuccess) return e;                                                          \
+            kfr<<<grid, kThreads, smem, stream>>>(P);                                                \
+            return cudaGetLastError();                                                               \
+        }                                                                                            \
         if (P.rw == 16) PTG_LAUNCH2D_RW(M, 16);                                                      \
         PTG_LAUNCH2D_RW(M, 8);                                                                       \
     } while (0)

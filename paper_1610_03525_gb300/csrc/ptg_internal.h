@@ -87,6 +87,7 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
 int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int s, int64_t band_start,
                         int64_t band_len, ptg::FieldPlan* P);
 bool ptg_per_sample(const ptg_field_desc* d, int spc_log2);
+bool ptg_fused_ridged(const ptg_field_desc* d, int spc_log2);
 int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int s, int64_t band_start,
                           int64_t band_len, ptg::SimplexPlan* P);
 int ptg_make_simplex3_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int64_t band_start, int64_t band_len,

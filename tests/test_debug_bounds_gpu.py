@@ -36,9 +36,9 @@ SM = {"c2": P.PTG_C2, "paper_gauge": P.PTG_PAPER_D2M1N3, "zero_grad": P.PTG_ZERO
 ctx = P.ptg_create(0)
 res = {"cases": 0, "violations": [], "worst": 0.0}
 
-def run(kind, dims, size, spc, N, variant=0, origin=(-(1 << 20) + 3, 12345, 7), p=0.6, w=0.75):
+def run(kind, dims, size, spc, N, variant=0, origin=(-(1 << 20) + 3, 12345, 7), p=0.6, w=0.75, ridged=False):
     smooth = SM.get(kind, P.PTG_C1)
-    var = variant | (P.PTG_PERLIN_S3 if kind == "perlin_s3" else 0)
+    var = variant | (P.PTG_PERLIN_S3 if kind == "perlin_s3" else 0) | (P.PTG_RIDGED if ridged else 0)
     d = P.make_desc(dims=dims, size=size, spc=spc, origin=origin, octaves=N, smoothness=smooth, persistence=p,
                     grad_weight=w, seed=31, variant=var)
     out = torch.full(tuple(reversed(size)), float("nan"), device="cuda")
@@ -47,8 +47,7 @@ def run(kind, dims, size, spc, N, variant=0, origin=(-(1 << 20) + 3, 12345, 7), 
     first = P.ptg_debug_bounds(ctx)
     idx = W.grid_indices_2d(*size) if dims == 2 else W.grid_indices_3d(*size)
     ref = O.field_samples(dims, (spc,) * dims, (1,) * dims, idx, octaves=N, method=ORC[kind], persistence=p,
-                          grad_weight=w, seed=31,
-                          origin=origin)
+                          grad_weight=w, seed=31, origin=origin, ridged=ridged)
     a = out.cpu().numpy()
     got = a[idx[:, 1], idx[:, 0]] if dims == 2 else a[idx[:, 2], idx[:, 1], idx[:, 0]]
     err = float(np.abs(got.astype(np.float64) - ref).max()) / W.total_amplitude(N, p)
@@ -70,6 +69,10 @@ for kind in ["c1", "c2", "perlin_s5", "perlin_s3", "paper_gauge", "zero_grad"]:
 for size in [(1, 1), (17, 13), (130, 70)]:
     for spc, N in [(1, 2), (16, 5), (1024, 12)]:
         run("opensimplex", 2, size, spc, N, origin=(-3, 5, 0))
+for kind in ["c1", "zero_grad", "paper_gauge", "perlin_s5"]:  # the fused ridged kernel
+    for size in [(1, 1), (17, 13), (130, 70)]:
+        for spc, N in [(1, 2), (2, 3), (8, 6), (64, 9), (1024, 12)]:
+            run(kind, 2, size, spc, N, origin=(-(1 << 10) + 3, 345, 0), ridged=True)
 for kind in ["c1", "c2", "perlin_s5", "perlin_s3"]:
     for size in [(1, 1, 1), (5, 3, 2), (37, 19, 11)]:
         for spc, N in [(1, 2), (4, 5), (32, 8)]:

@@ -378,7 +378,8 @@ def test_3d_opensimplex_windows_and_host(ctx):
 
 
 # ---------------------------------------------------------------------------
-# ridged noise (the paper's ridged mountains, Sec. 5.1), per-sample generators
+# ridged noise (the paper's ridged mountains, Sec. 5.1): the fused ridged kernel
+# (2D, f = 2, tiles aligned to cells) and the per-sample generators
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("kind", ["c1", "c2", "zero_grad", "paper_gauge", "perlin_s5", "perlin_s3"])
 @pytest.mark.parametrize("size,spc,octaves,origin,f,dtype", [
@@ -397,6 +398,40 @@ def test_ridged_vs_oracle(ctx, kind, size, spc, octaves, origin, f, dtype):
     errlog.record("2d_ridged", kind, dtype_name(dtype), err.max(), W.total_amplitude(octaves, 0.6), err.size,
                   bound_ratio=float((err / bound).max()))
     assert np.all(err <= bound), err.max()
+
+
+@pytest.mark.parametrize("kind", ["c1", "c2", "zero_grad", "paper_gauge", "perlin_s5", "perlin_s3"])
+@pytest.mark.parametrize("dtype", [P.PTG_F32, P.PTG_F16])
+def test_ridged_8192_n12_sampled(ctx, kind, dtype):
+    """The 8192^2, 12-octave field (spc 1024) as ridged noise: the fused ridged
+    kernel (aligned tiles), sampled on every 64th row, 2^18 random samples and
+    the base lattice's columns."""
+    cfg = W.CONFIGS["2d_8192_n12"]
+    out = gpu_field(ctx, kind, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"], seed=4, persistence=0.5,
+                    dtype=dtype, ridged=True)
+    idx = W.subsample(cfg["size"], every=64, n_random=1 << 18, seed=4, lattice_spc=cfg["spc"])
+    ref = oracle_at(kind, idx, spc=cfg["spc"], octaves=cfg["octaves"], seed=4, persistence=0.5, ridged=True)
+    err = np.abs(gather(out, idx) - ref)
+    bound = tol32(cfg["octaves"]) + (half_ulp16(ref) if dtype == P.PTG_F16 else 0.0)
+    errlog.record("2d_ridged_8192_n12", kind, dtype_name(dtype), err.max(), W.total_amplitude(cfg["octaves"]),
+                  err.size, bound_ratio=float((err / bound).max()))
+    assert np.all(err <= bound), err.max()
+    del out
+
+
+@pytest.mark.parametrize("kind", ["c1", "perlin_s5"])
+@pytest.mark.parametrize("offset", [(0, 0, 0), (64, 128, 0), (3, 5, 0)])
+def test_ridged_windows(ctx, kind, offset):
+    """Windows of a ridged world: aligned offsets run the fused ridged kernel,
+    unaligned ones the per-sample generator; both match the oracle."""
+    size, spc, N = (200, 136), 32, 8
+    out = gpu_field(ctx, kind, size=size, spc=spc, octaves=N, origin=(9, -2, 0), offset=offset, seed=6,
+                    persistence=0.6, ridged=True)
+    idx = W.grid_indices_2d(*size)
+    ref = oracle_at(kind, idx, spc=spc, octaves=N, origin=(9, -2, 0), offset=offset, seed=6, persistence=0.6,
+                    ridged=True)
+    err = np.abs(gather(out, idx) - ref)
+    assert np.all(err <= tol32(N, 0.6)), err.max()
 
 
 @pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5"])
