@@ -211,6 +211,29 @@ def bench_3d(P, R, ctx, stream, torch, reps=10):
                      "alu_frac": ops["total"] / (ms / 1e3) / peak}
         if name != "opensimplex":
             res[name]["frac_vs_bound"] = R.bound_ops(name, size, 128, 8)["total"] / (ms / 1e3) / peak
+    # ridged noise on the same volume: the fused ridged kernel, and the per-sample generator
+    # on the same volume one sample off the cell grid (where the fused kernel does not apply)
+    ridged = {}
+    for name, fn, kw, off in [("c1", P.ptg_field, dict(smoothness=P.PTG_C1), 0),
+                              ("perlin_s5", P.ptg_perlin, dict(variant=P.PTG_PERLIN_S5), 0),
+                              ("c1_per_sample", P.ptg_field, dict(smoothness=P.PTG_C1), 1)]:
+        kw = dict(kw)
+        kw["variant"] = kw.get("variant", 0) | P.PTG_RIDGED
+        d = P.make_desc(dims=3, size=size, spc=128, origin=(1 << 20, 1 << 20, 0), offset=(off, 0, 0), octaves=8,
+                        seed=0, dtype=P.PTG_F16, **kw)
+        for _ in range(2):
+            fn(ctx, d, out, stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 2 if off else reps
+        a.record(stream)
+        for _ in range(n):
+            fn(ctx, d, out, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / n
+        ridged[name] = {"gsamples_s": 512 ** 3 / ms / 1e6, "ms": ms}
+    res["ridged"] = ridged
     del out
     return res
 

@@ -112,10 +112,11 @@ typedef enum { PTG_COARSE_AUTO = 0, PTG_COARSE_RUNS = 0x400, PTG_COARSE_TILE = 0
  * and Modeling", ch. 16) with offset 1 and gain 2: octave i contributes
  * p^i r_i with r_i = (1 - |h_i|)^2 w_i, h_i the unit-amplitude octave field,
  * w_0 = 1 and w_{i+1} = clamp(2 r_i, 0, 1).  The octaves interact, so every
- * octave is evaluated at every sample, in octave order: 2D fields with
- * lacunarity 2, spc a power of two and offsets multiples of min(spc, 64) run
- * a fused ridged kernel, the others the per-sample generators (thread-shape
- * and coarse-octave bits are ignored); batches (ptg_batch*) do not take them. */
+ * octave is evaluated at every sample, in octave order: fields with
+ * lacunarity 2, spc a power of two and offsets multiples of min(spc, tile
+ * side) run the fused ridged kernels (2D and 3D), the others the per-sample
+ * generators (thread-shape and coarse-octave bits are ignored); batches
+ * (ptg_batch*) do not take them. */
 #define PTG_RIDGED 0x1000
 
 /* Full description of one field (Sec. 2.1 cell lattice, Sec. 4 octaves). */

@@ -124,14 +124,18 @@ bool ptg_per_sample(const ptg_field_desc* d, int spc_log2)
     return d->lacunarity != 2.0f || spc_log2 < 0 || (d->variant & PTG_RIDGED) != 0;
 }
 
-// Ridged 2D fields that the fused generator's ridged kernel takes instead:
+// Ridged fields that the fused generators' ridged kernels take instead:
 // frequency ratio 2, spc a power of two and tiles aligned to cells (offsets
-// multiples of min(spc, 64)), as for the fused fBm kernel.
+// multiples of min(spc, tile side) on every axis), as for the fused fBm kernels.
 bool ptg_fused_ridged(const ptg_field_desc* d, int spc_log2)
 {
-    if (d->dims != 2 || !(d->variant & PTG_RIDGED) || d->lacunarity != 2.0f || spc_log2 < 0) return false;
-    const int64_t align = d->spc < kTile2dX ? d->spc : kTile2dX;
-    return d->offset[0] % align == 0 && d->offset[1] % align == 0;
+    if (!(d->variant & PTG_RIDGED) || d->lacunarity != 2.0f || spc_log2 < 0) return false;
+    static const int64_t tile2[2] = {kTile2dX, kTile2dY}, tile3[3] = {kTile3dX, kTile3dY, kTile3dZ};
+    for (int k = 0; k < d->dims; ++k) {
+        const int64_t t = d->dims == 3 ? tile3[k] : tile2[k], align = d->spc < t ? d->spc : t;
+        if (d->offset[k] % align != 0) return false;
+    }
+    return true;
 }
 
 // Argument checks common to every generator.  On success fills *spc_log2

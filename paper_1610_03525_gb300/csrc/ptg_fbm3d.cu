@@ -147,7 +147,7 @@ __device__ __forceinline__ float4 corner_data4(uint32_t x, uint32_t y, uint32_t 
 //   4. cells of 2 samples (17 x 9 x 5 corners): a warp two corner rows at a
 //      time (16 lanes a row), with x's LCG step taken once per lane and the
 //      others once per row; column 16 by the last threads down.
-template <int METHOD>
+template <int METHOD, bool kUnit = false>
 __device__ __forceinline__ void stage_corners3(const FieldPlan& P, float4* __restrict__ corners, int j0x, int j0y,
                                                int j0z)
 {
@@ -165,7 +165,7 @@ __device__ __forceinline__ void stage_corners3(const FieldPlan& P, float4* __res
             uint32_t w = op.key;
             pcg4d(x, y, z, w);
             if (bounds_ok(kSiteStage, c, op.rowlen * op.ncy * op.ncz))
-                sst(kSiteStage, &corners[op.coff + c], corner_data4<METHOD>(x, y, z, w, op.amp, op.ampw));
+                sst(kSiteStage, &corners[op.coff + c], corner_data4<METHOD>(x, y, z, w, kUnit ? 1.0f : op.amp, kUnit ? P.grad_w : op.ampw));
         }
     }
     {  // 2. cells of 16 and 8 samples
@@ -189,7 +189,7 @@ __device__ __forceinline__ void stage_corners3(const FieldPlan& P, float4* __res
             pcg4d(x, y, z, w);
             const int slot = (cz * op.ncy + cy) * op.rowlen + corner_slot(cx);
             if (bounds_ok(kSiteStage, slot, op.rowlen * op.ncy * op.ncz))
-                sst(kSiteStage, &corners[op.coff + slot], corner_data4<METHOD>(x, y, z, w, op.amp, op.ampw));
+                sst(kSiteStage, &corners[op.coff + slot], corner_data4<METHOD>(x, y, z, w, kUnit ? 1.0f : op.amp, kUnit ? P.grad_w : op.ampw));
         }
     }
     if (s >= 2 && s - 2 < N) {  // 3. cells of 4 samples
@@ -198,7 +198,7 @@ __device__ __forceinline__ void stage_corners3(const FieldPlan& P, float4* __res
         const uint32_t bx = op.ox + ((uint32_t)j0x >> 2), by = op.oy + ((uint32_t)j0y >> 2);
         const uint32_t bz = op.oz + ((uint32_t)j0z >> 2);
         float4* cg = corners + op.coff;
-        const float amp = op.amp, ampw = op.ampw;
+        const float amp = kUnit ? 1.0f : op.amp, ampw = kUnit ? P.grad_w : op.ampw;
         const uint32_t key = op.key;
         for (int e = tid; e < NX * NY * NZ; e += kThreads) {
             const int cz = e / (NX * NY), rem = e - cz * (NX * NY);
@@ -215,7 +215,7 @@ __device__ __forceinline__ void stage_corners3(const FieldPlan& P, float4* __res
         const uint32_t bx = op.ox + ((uint32_t)j0x >> 1), by = op.oy + ((uint32_t)j0y >> 1);
         const uint32_t bz = op.oz + ((uint32_t)j0z >> 1);
         float4* cg = corners + op.coff;
-        const float amp = op.amp, ampw = op.ampw;
+        const float amp = kUnit ? 1.0f : op.amp, ampw = kUnit ? P.grad_w : op.ampw;
         const int half = lane >> 4, col = lane & 15;
         const uint32_t w1 = pcg_lcg(op.key), x1 = pcg_lcg(bx + (uint32_t)col);
         float4* dst = cg + corner_slot(col);
@@ -584,11 +584,153 @@ __global__ void __launch_bounds__(kThreads, min_ctas3<METHOD>()) fbm3d_kernel(co
     store_tile3<OutT>(P, acc, x0 + tx * kCols, y0 + ty * kRows, z0 + tz);
 }
 
+// ---------------------------------------------------------------------------
+// Ridged multifractal (PTG_RIDGED), fused 3D form: as the 2D ridged kernel
+// (every octave at every sample, in octave order, r = (1 - |h|)^2 w added
+// with weight p^i and w = clamp(2 r, 0, 1)), on this kernel's tiles and
+// staging.  Per-CTA tables hold the x-, y- and z-bases of the octaves with
+// cells of 8 samples or more (32 + 16 + 8 an octave; x rotated so that a
+// quarter warp's four runs read four bank groups).
+// ---------------------------------------------------------------------------
+constexpr int kRidgeTab3 = kTW + kTH + kTD;  // basis-table entries an octave
+
+__device__ __forceinline__ int ridge_xslot3(int j) { return j ^ ((j >> 3) & 3); }
+
+__device__ __forceinline__ void ridge2_3(float& acc0, float& acc1, float& w0, float& w1, float h0, float h1, float wgt)
+{
+    const float2 a = make_float2(1.0f - fabsf(h0), 1.0f - fabsf(h1));
+    const float2 r = __fmul2_rn(__fmul2_rn(a, a), make_float2(w0, w1));
+    const float2 ac = __ffma2_rn(make_float2(wgt, wgt), r, make_float2(acc0, acc1));
+    acc0 = ac.x;
+    acc1 = ac.y;
+    w0 = __saturatef(2.0f * r.x);
+    w1 = __saturatef(2.0f * r.y);
+}
+
+// Cells of CW = 4 or 2 samples: constant in-cell positions along x and y,
+// the thread's plane at (tz mod CW) / CW along z (as small_octave3).
+template <int METHOD, int CW>
+__device__ __forceinline__ void small_ridged3(float (&acc)[kRows][kCols], float (&w)[kRows][kCols],
+                                              const float4* __restrict__ corners, const OctPlan& op, int tx, int ty,
+                                              int tz)
+{
+    const float4* cg = corners + op.coff;
+    constexpr float inv = 1.0f / CW;
+    const float4 zb = axis_basis<METHOD>((float)(tz & (CW - 1)) * inv);
+    const int lcz = tz / CW;
+    const float wgt = op.amp;
+#pragma unroll
+    for (int yq = 0; yq < kRows / CW; ++yq) {
+        const int lcy = (ty * kRows + yq * CW) / CW;
+#pragma unroll
+        for (int xq = 0; xq < kCols / CW; ++xq) {
+            const Cell c = zcell(cg, op, (tx * kCols + xq * CW) / CW, lcy, lcz, zb);
+#pragma unroll
+            for (int rr = 0; rr < CW; ++rr) {
+                Row R;
+                if (rr == 0) {
+                    R = row_at_zero(c);
+                } else {
+                    const float4 yb = axis_basis<METHOD>(rr * inv);
+                    R = row_of(c, yb.x, yb.y, yb.z);
+                }
+#pragma unroll
+                for (int q = 0; q < CW; q += 2) {
+                    const float4 xb1 = axis_basis<METHOD>((q + 1) * inv);
+                    float h0 = R.V0;
+                    if (q > 0) {
+                        const float4 xb = axis_basis<METHOD>(q * inv);
+                        h0 = eval_row(R, xb.x, xb.y, xb.z);
+                    }
+                    const float h1 = eval_row(R, xb1.x, xb1.y, xb1.z);
+                    const int y = yq * CW + rr, x = xq * CW + q;
+                    ridge2_3(acc[y][x], acc[y][x + 1], w[y][x], w[y][x + 1], h0, h1, wgt);
+                }
+            }
+        }
+    }
+}
+
+template <int METHOD, typename OutT>
+__global__ void __launch_bounds__(kThreads) fbm3d_ridged_kernel(const __grid_constant__ FieldPlan P)
+{
+    extern __shared__ float4 sm[];
+    const int tid = threadIdx.x, tx = tid & 3, ty = (tid >> 2) & 3, tz = tid >> 4;
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH, z0 = blockIdx.z * kTD;
+    const int j0x = x0 + P.jx0, j0y = y0 + P.jy0, j0z = z0 + P.jz0;
+    const int s = P.s, N = P.N, nb = n_run8(P);
+    for (int e = tid; e < nb * kRidgeTab3; e += kThreads) {  // bases of the octaves with cells >= 8
+        const int i = e / kRidgeTab3, j = e - i * kRidgeTab3;
+        const uint32_t pos = (uint32_t)(j < kTW ? j0x + j : (j < kTW + kTH ? j0y + j - kTW : j0z + j - kTW - kTH));
+        sst(kSiteStage, &sm[i * kRidgeTab3 + (j < kTW ? ridge_xslot3(j) : j)], axis_basis<METHOD>(axis_t(pos, i, s)));
+    }
+    float4* corners = sm + nb * kRidgeTab3;
+    stage_corners3<METHOD, true>(P, corners, j0x, j0y, j0z);
+    __syncthreads();
+
+    float acc[kRows][kCols], w[kRows][kCols];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+            acc[r][c] = 0.0f;
+            w[r][c] = 1.0f;
+        }
+    for (int i = 0; i < nb; ++i) {  // one cell a thread; octaves in order (the weights chain)
+        const OctPlan& op = P.oct[i];
+        const float4* tb = sm + i * kRidgeTab3;
+        const Cell c = zcell(corners + op.coff, op, (tx * kCols) >> op.k, (ty * kRows) >> op.k, tz >> op.k,
+                             sld(kSiteTable, &tb[kTW + kTH + tz]));
+        const float wgt = op.amp;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const float4 yb = sld(kSiteTable, &tb[kTW + ty * kRows + r]);
+            const Row R = row_of(c, yb.x, yb.y, yb.z);
+#pragma unroll
+            for (int q = 0; q < kCols; q += 2) {
+                const float4 xa = sld(kSiteTable, &tb[ridge_xslot3(tx * kCols + q)]);
+                const float4 xc = sld(kSiteTable, &tb[ridge_xslot3(tx * kCols + q + 1)]);
+                ridge2_3(acc[r][q], acc[r][q + 1], w[r][q], w[r][q + 1], eval_row(R, xa.x, xa.y, xa.z),
+                         eval_row(R, xc.x, xc.y, xc.z), wgt);
+            }
+        }
+    }
+    if (s >= 2 && s - 2 < N) small_ridged3<METHOD, 4>(acc, w, corners, P.oct[s - 2], tx, ty, tz);
+    if (s >= 1 && s - 1 < N) small_ridged3<METHOD, 2>(acc, w, corners, P.oct[s - 1], tx, ty, tz);
+    const uint32_t jx = (uint32_t)(j0x + tx * kCols), jy = (uint32_t)(j0y + ty * kRows), jz = (uint32_t)(j0z + tz);
+    for (int i = s; i < N; ++i) {  // lattice octaves: the corner value (zero for Perlin)
+        const OctPlan& op = P.oct[i];
+        const float wgt = op.amp;
+        if constexpr (METHOD == kPerlinS5 || METHOD == kPerlinS3) {
+#pragma unroll
+            for (int r = 0; r < kRows; ++r)
+#pragma unroll
+                for (int c = 0; c < kCols; c += 2) ridge2_3(acc[r][c], acc[r][c + 1], w[r][c], w[r][c + 1], 0.f, 0.f, wgt);
+        } else {
+            const int sh = op.k;
+            const uint32_t z1 = pcg_lcg(op.oz + (jz << sh)), w1 = pcg_lcg(op.key);
+            const uint32_t dx = 1664525u << sh, xs = op.ox + (jx << sh);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const uint32_t y1 = pcg_lcg(op.oy + ((jy + r) << sh));
+                const uint32_t base = pcg4d_run_base(xs, y1, w1);
+#pragma unroll
+                for (int c = 0; c < kCols; c += 2)
+                    ridge2_3(acc[r][c], acc[r][c + 1], w[r][c], w[r][c + 1],
+                             unit_value(pcg4d_run_value(base + (uint32_t)c * dx, y1, z1, w1)),
+                             unit_value(pcg4d_run_value(base + (uint32_t)(c + 1) * dx, y1, z1, w1)), wgt);
+            }
+        }
+    }
+    store_tile3<OutT>(P, acc, x0 + tx * kCols, y0 + ty * kRows, z0 + tz);
+}
+
 template <int METHOD>
 size_t smem_words3(const FieldPlan& P)
 {
     int n8 = P.s - 2;
     n8 = n8 < 0 ? 0 : (n8 < P.N ? n8 : P.N);
+    if (P.ridged) return (size_t)n8 * kRidgeTab3 + (size_t)P.ncorner;
     return (size_t)corner_base3<METHOD>(n8) + (size_t)P.ncorner + (n_tile3<METHOD>(P) > 0 ? kTD * 16 / 4 : 0);
 }
 
@@ -613,7 +755,7 @@ cudaError_t launch_fbm3d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
     const bool f16 = P.dtype == 1;
 #define PTG_LAUNCH3D(M, T)                                                                           \
     do {                                                                                             \
-        auto kfn = fbm3d_kernel<M, T>;                                                               \
+        auto kfn = P.ridged ? fbm3d_ridged_kernel<M, T> : fbm3d_kernel<M, T>;                        \
         cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \

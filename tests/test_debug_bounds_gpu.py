@@ -73,6 +73,10 @@ for kind in ["c1", "zero_grad", "paper_gauge", "perlin_s5"]:  # the fused ridged
     for size in [(1, 1), (17, 13), (130, 70)]:
         for spc, N in [(1, 2), (2, 3), (8, 6), (64, 9), (1024, 12)]:
             run(kind, 2, size, spc, N, origin=(-(1 << 10) + 3, 345, 0), ridged=True)
+for kind in ["c1", "c2", "perlin_s5"]:  # the fused ridged kernel, 3D
+    for size in [(1, 1, 1), (5, 3, 2), (37, 19, 11)]:
+        for spc, N in [(1, 2), (4, 5), (32, 8)]:
+            run(kind, 3, size, spc, N, origin=(-(1 << 10) + 3, 345, 7), ridged=True)
 for kind in ["c1", "c2", "perlin_s5", "perlin_s3"]:
     for size in [(1, 1, 1), (5, 3, 2), (37, 19, 11)]:
         for spc, N in [(1, 2), (4, 5), (32, 8)]:

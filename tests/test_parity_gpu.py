@@ -445,6 +445,40 @@ def test_ridged_3d_vs_oracle(ctx, kind):
     assert err <= tol32(N, kind="ridged"), err
 
 
+@pytest.mark.parametrize("kind", ["c1", "perlin_s5"])
+@pytest.mark.parametrize("offset", [(0, 0, 0), (32, 16, 8), (3, 1, 2)])
+def test_ridged_3d_windows(ctx, kind, offset):
+    """3D ridged windows: aligned offsets run the fused ridged kernel, unaligned
+    ones the per-sample generator; both match the oracle."""
+    size, spc, N, origin = (40, 20, 12), 8, 5, (77, -5, 3)
+    out = gpu_field(ctx, kind, dims=3, size=size, spc=spc, octaves=N, origin=origin, offset=offset, seed=2,
+                    persistence=0.6, ridged=True)
+    idx = W.grid_indices_3d(*size)
+    ref = oracle_at(kind, idx, dims=3, spc=spc, octaves=N, origin=origin, offset=offset, seed=2, persistence=0.6,
+                    ridged=True)
+    err = np.abs(gather(out, idx) - ref)
+    assert np.all(err <= tol32(N, 0.6)), err.max()
+
+
+@pytest.mark.parametrize("kind", ["c1", "c2", "perlin_s5"])
+def test_ridged_3d_512_n8_sampled(ctx, kind):
+    """The 512^3, 8-octave volume (spc 128, origin (2^20, 2^20, 0)) as ridged
+    noise, FP16 out, through the fused ridged kernel: every 64th plane, 2^18
+    random samples and the base lattice's lines."""
+    cfg = W.CONFIGS["3d_512_n8"]
+    origin = cfg["origin"]
+    out = gpu_field(ctx, kind, dims=3, size=cfg["size"], spc=cfg["spc"], octaves=cfg["octaves"], origin=origin,
+                    seed=3, dtype=P.PTG_F16, ridged=True)
+    idx = W.subsample(cfg["size"], every=64, n_random=1 << 18, seed=3, lattice_spc=cfg["spc"])
+    ref = oracle_at(kind, idx, dims=3, spc=cfg["spc"], octaves=cfg["octaves"], origin=origin, seed=3, ridged=True)
+    err = np.abs(gather(out, idx) - ref)
+    bound = tol32(cfg["octaves"]) + half_ulp16(ref)
+    errlog.record("3d_ridged_512_n8", kind, "f16", err.max(), W.total_amplitude(cfg["octaves"]), err.size,
+                  bound_ratio=float((err / bound).max()))
+    assert np.all(err <= bound), err.max()
+    del out
+
+
 def test_ridged_is_not_batched(ctx):
     d = P.make_desc(dims=2, size=(64, 64), spc=64, octaves=4, variant=P.PTG_RIDGED)
     out = torch.empty((64, 64), device="cuda")
