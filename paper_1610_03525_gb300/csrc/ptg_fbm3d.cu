@@ -66,14 +66,19 @@ __device__ __forceinline__ int n_run8(const FieldPlan& P)
 }
 
 // Tile octaves (cells >= 32 samples, octaves 0 .. s - 5), used for C1 when
-// there are at least two of them; else 0.
+// there are at least four of them; else 0.  With node rows a run octave
+// costs a thread about what its share of the tile-node sum does, and the
+// sum's code (a kernel of its own, so that fields without it carry none of
+// it) adds a barrier.  By measurement on GB300 (512^3, FP16, back-to-back
+// launches), against the kernel without that code: 12% faster with six such
+// octaves and 4% with four, 1.8% slower with three and 3% with two.
 template <int METHOD>
 __host__ __device__ __forceinline__ int n_tile3(const FieldPlan& P)
 {
     if (METHOD != kC1) return 0;
     int n = P.s - 4;
     n = n < 0 ? 0 : (n < P.N ? n : P.N);
-    return n >= 2 ? n : 0;
+    return n >= 4 ? n : 0;
 }
 
 // Tile node position q along axis a (x, y, z), packed one byte each.
@@ -237,11 +242,11 @@ __device__ __forceinline__ void stage_corners3(const FieldPlan& P, float4* __res
     }
 }
 
-template <int METHOD>
+template <int METHOD, bool kTile>
 __device__ __forceinline__ void stage_tile3(const FieldPlan& P, float4* sm, int j0x, int j0y, int j0z)
 {
     constexpr int NN = Deg<METHOD>::value + 1;
-    const int tid = threadIdx.x, s = P.s, n8 = n_run8(P), nt = n_tile3<METHOD>(P);
+    const int tid = threadIdx.x, s = P.s, n8 = n_run8(P), nt = kTile ? n_tile3<METHOD>(P) : 0;
     float4* xnode = sm;
     float4* ylut = sm + xnode_words3<METHOD>(n8);
     float4* zlut = ylut + n8 * 16;
@@ -496,7 +501,8 @@ __device__ __forceinline__ void store_tile3(const FieldPlan& P, const float (&ac
 template <int METHOD>
 constexpr int min_ctas3() { return METHOD == kC1 ? 6 : 0; }
 
-template <int METHOD, typename OutT>
+// kTile: the field sums its tile octaves at the tile nodes (n_tile3 > 0).
+template <int METHOD, typename OutT, bool kTile>
 __global__ void __launch_bounds__(kThreads, min_ctas3<METHOD>()) fbm3d_kernel(const __grid_constant__ FieldPlan P)
 {
     constexpr int D = Deg<METHOD>::value, NN = D + 1;
@@ -504,8 +510,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas3<METHOD>()) fbm3d_kernel(co
     const int tid = threadIdx.x, tx = tid & 3, ty = (tid >> 2) & 3, tz = tid >> 4;
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH, z0 = blockIdx.z * kTD;  // output tile
     const int j0x = x0 + P.jx0, j0y = y0 + P.jy0, j0z = z0 + P.jz0;                  // sample indices
-    const int s = P.s, N = P.N, n8 = n_run8(P), nt = n_tile3<METHOD>(P);
-    stage_tile3<METHOD>(P, sm, j0x, j0y, j0z);
+    const int s = P.s, N = P.N, n8 = n_run8(P), nt = kTile ? n_tile3<METHOD>(P) : 0;
+    stage_tile3<METHOD, kTile>(P, sm, j0x, j0y, j0z);
     __syncthreads();
 
     // tile octaves: their sum at the tile nodes, reduced along z for every
@@ -755,7 +761,8 @@ cudaError_t launch_fbm3d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
     const bool f16 = P.dtype == 1;
 #define PTG_LAUNCH3D(M, T)                                                                           \
     do {                                                                                             \
-        auto kfn = P.ridged ? fbm3d_ridged_kernel<M, T> : fbm3d_kernel<M, T>;                        \
+        auto kfn = P.ridged ? fbm3d_ridged_kernel<M, T>                                              \
+                   : (M == kC1 && n_tile3<M>(P) > 0 ? fbm3d_kernel<M, T, M == kC1> : fbm3d_kernel<M, T, false>); \
         cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \

@@ -199,6 +199,18 @@ def test_3d_world_offset(ctx, kind, dtype):
     assert np.all(err <= bound), err.max()
 
 
+@pytest.mark.parametrize("spc,N", [(1024, 10), (256, 9), (256, 3), (128, 8), (64, 7)])
+def test_3d_c1_tile_octave_counts(ctx, spc, N):
+    """3D C1 with six, four, three, three and two octaves of cells >= 32
+    samples: summed at the tile nodes from three up, else node-row octaves."""
+    size, origin = (70, 36, 20), (1 << 12, -77, 5)
+    out = gpu_field(ctx, "c1", dims=3, size=size, spc=spc, octaves=N, origin=origin, seed=8)
+    idx = W.grid_indices_3d(*size)
+    ref = oracle_at("c1", idx, dims=3, spc=spc, octaves=N, origin=origin, seed=8)
+    err = np.abs(gather(out, idx) - ref)
+    assert np.all(err <= tol32(N)), err.max()
+
+
 def test_3d_ragged(ctx):
     size, spc, N = (37, 19, 11), 4, 5
     for kind in ("c1", "c2", "perlin_s5", "perlin_s3"):
