@@ -61,7 +61,7 @@ RW samples wide ("run" octaves):
 reduction along z of the cell's four corner columns (32 ops) before each cell
 is used, and each run octave's rows summing their V0 once; C1 evaluates 2 of
 its 4 rows (node rows, as in 2D: 2 x 16 FMA of interpolation along y); for C1
-with three or more octaves of cells >= 32 samples, those are tile octaves: 64
+with four or more octaves of cells >= 32 samples, those are tile octaves: 64
 nodes x nt x (3 x (coordinate + basis) + 32 + 9 + 4 + 1) + 64 a tile, the
 nodes reduced along z for each of the 8 planes (8 x 16 x 4 FMA a tile) and
 2 x 16 FMA of interpolation a thread and evaluated row, no basis tables; basis tables of n8 x (4 (d+1) + 24)
@@ -203,9 +203,9 @@ def lane_ops_3d(kind: str, size, spc: int, octaves: int, f: float = 2.0) -> dict
     d = DEG[kind]
     st = _staged(spc, octaves)
     n8 = sum(1 for _, spci in st if spci >= 8)
-    # C1 tile octaves (cells >= 32 samples) when there are three or more
+    # C1 tile octaves (cells >= 32 samples) when there are four or more
     nt = sum(1 for _, spci in st if spci >= 32) if kind == "c1" else 0
-    nt = nt if nt >= 3 else 0
+    nt = nt if nt >= 4 else 0
     lut = tiles * (n8 - nt) * (4 * (d + 1) + 24) * (COORD_OPS + BASIS_OPS[kind])
     corners = 0
     nr = 2 if d == 3 else 4  # rows a thread evaluates (node rows), of its 4

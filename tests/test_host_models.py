@@ -61,8 +61,8 @@ def test_lane_op_model_regimes():
     # more octaves never cost less
     per = [R.lane_ops_2d("c1", size, 1024, n)["per_sample"] for n in range(1, 13)]
     assert all(b >= a for a, b in zip(per, per[1:]))
-    # 3D: C1 at spc 128 (three octaves of cells >= 32, summed at the tile nodes) and at
-    # spc 1024 (six)
+    # 3D: C1 at spc 128 (three octaves of cells >= 32, evaluated at the node rows) and at
+    # spc 1024 (six, summed at the tile nodes)
     assert R.lane_ops_3d("c1", (512, 512, 512), 128, 8)["per_sample"] < 69.1
     assert R.lane_ops_3d("c1", (512, 512, 512), 1024, 10)["per_sample"] < R.lane_ops_3d("c1", (512, 512, 512), 1024, 11)["per_sample"]
 

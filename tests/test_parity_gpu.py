@@ -202,7 +202,7 @@ def test_3d_world_offset(ctx, kind, dtype):
 @pytest.mark.parametrize("spc,N", [(1024, 10), (256, 9), (256, 3), (128, 8), (64, 7)])
 def test_3d_c1_tile_octave_counts(ctx, spc, N):
     """3D C1 with six, four, three, three and two octaves of cells >= 32
-    samples: summed at the tile nodes from three up, else node-row octaves."""
+    samples: summed at the tile nodes from four up, else node-row octaves."""
     size, origin = (70, 36, 20), (1 << 12, -77, 5)
     out = gpu_field(ctx, "c1", dims=3, size=size, spc=spc, octaves=N, origin=origin, seed=8)
     idx = W.grid_indices_3d(*size)
