@@ -261,12 +261,14 @@ __device__ __forceinline__ void stage_corners(const FieldPlan& P, float4* __rest
     }
 }
 
-template <int METHOD, int RW>
+// kGen: the field may have generic run octaves (n_generic > 0); kernels of
+// fields without them are compiled without that path.
+template <int METHOD, int RW, bool kGen = true>
 __device__ __forceinline__ void stage_tile(const FieldPlan& P, float4* sm, int j0x, int j0y)
 {
     using SH = Shape<RW>;
     constexpr int D = Deg<METHOD>::value, NN = D + 1;
-    const int tid = threadIdx.x, s = P.s, nt = n_tile<METHOD>(P), ng = n_generic<METHOD>(P);
+    const int tid = threadIdx.x, s = P.s, nt = n_tile<METHOD>(P), ng = kGen ? n_generic<METHOD>(P) : 0;
     float4* xnode = sm;
     float4* ylut = sm + xnode_words<METHOD, RW>(ng);
     float4* rbase = ylut + ng * 64;
@@ -658,7 +660,7 @@ __device__ __forceinline__ void store_tile(const FieldPlan& P, const float (&acc
 }
 
 // Whole tile: stage, evaluate all octaves, store.
-template <int METHOD, int RW>
+template <int METHOD, int RW, bool kGen = true>
 __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int bx, int by)
 {
     using SH = Shape<RW>;
@@ -666,8 +668,8 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
     const int tid = threadIdx.x, tx = tid % SH::TXN, ty = tid / SH::TXN;
     const int x0 = bx * kTW, y0 = by * kTH;        // output tile origin
     const int j0x = x0 + P.jx0, j0y = y0 + P.jy0;  // sample indices
-    const int s = P.s, N = P.N, nt = n_tile<METHOD>(P), ng = n_generic<METHOD>(P);
-    stage_tile<METHOD, RW>(P, sm, j0x, j0y);
+    const int s = P.s, N = P.N, nt = n_tile<METHOD>(P), ng = kGen ? n_generic<METHOD>(P) : 0;
+    stage_tile<METHOD, RW, kGen>(P, sm, j0x, j0y);
     __syncthreads();
 
     // tile octaves: their sum at the tile nodes (read back after the barrier below)
@@ -766,11 +768,11 @@ __device__ __forceinline__ void fbm2d_tile(const FieldPlan& P, float4* sm, int b
 template <int METHOD>
 constexpr int min_ctas() { return METHOD == kPerlinS5 ? 5 : 0; }
 
-template <int METHOD, int RW>
+template <int METHOD, int RW, bool kGen>
 __global__ void __launch_bounds__(kThreads, min_ctas<METHOD>()) fbm2d_kernel(const __grid_constant__ FieldPlan P)
 {
     extern __shared__ float4 sm[];
-    fbm2d_tile<METHOD, RW>(P, sm, blockIdx.x, blockIdx.y);
+    fbm2d_tile<METHOD, RW, kGen>(P, sm, blockIdx.x, blockIdx.y);
 }
 
 // One tile of a batch field, as a call (not inlined) so that the batch
@@ -1023,7 +1025,7 @@ cudaError_t launch_fbm2d(const FieldPlan& P, int method, int /*s*/, cudaStream_t
     const size_t smem = fbm2d_smem_bytes(P);
 #define PTG_LAUNCH2D_RW(M, RW)                                                                       \
     do {                                                                                             \
-        auto kfn = fbm2d_kernel<M, RW>;                                                              \
+        auto kfn = n_generic<M>(P) > 0 ? fbm2d_kernel<M, RW, true> : fbm2d_kernel<M, RW, false>;      \
         cudaError_t e = set_kernel_smem((const void*)kfn, smem);                                     \
         if (e != cudaSuccess) return e;                                                              \
         kfn<<<grid, kThreads, smem, stream>>>(P);                                                    \
