@@ -928,8 +928,12 @@ __device__ __forceinline__ void ridged_tile(const FieldPlan& P, float4* sm, int 
     store_tile<8>(P, acc, x0 + tx * 8, y0 + ty * 4);
 }
 
+// Bounded to four CTAs a SM (128 registers; the compiler's own choice is 139,
+// three CTAs): on the 8192^2, 12-octave field C1 0.9%, C2 1.2% and Perlin S5
+// 3.7% faster, zero-gradient unchanged, with a 4-byte spill.  Five CTAs (96
+// registers) spill 100 bytes and are 3-4% slower.
 template <int METHOD>
-__global__ void __launch_bounds__(kThreads) fbm2d_ridged_kernel(const __grid_constant__ FieldPlan P)
+__global__ void __launch_bounds__(kThreads, 4) fbm2d_ridged_kernel(const __grid_constant__ FieldPlan P)
 {
     extern __shared__ float4 sm[];
     ridged_tile<METHOD>(P, sm, blockIdx.x, blockIdx.y);
