@@ -958,20 +958,38 @@ __global__ void __launch_bounds__(kThreads, 6) fbm2d_batch_kernel(const FieldPla
     __shared__ long long s_tile;
     __shared__ int s_field;
     const long long total = bounds_ok(kSitePlan, n, (long long)n + 1) ? tile_start[n] : 0;
+    const int lane = threadIdx.x & 31;
+    // Lane 0 of warp 0 holds the tile taken for the next round: the atomic
+    // for it is issued as soon as the current tile is known, so that its
+    // latency passes while the tile is computed.
+    long long next = 0;
+    if (threadIdx.x == 0) next = (long long)atomicAdd(counter, 1ULL);
     int cur = -1;
     for (;;) {
-        if (threadIdx.x == 0) {
-            const long long t = (long long)atomicAdd(counter, 1ULL);
-            s_tile = t;
+        if (threadIdx.x < 32) {
+            const long long t = __shfl_sync(0xffffffffu, next, 0);
             if (t < total) {
-                int lo = 0, hi = n - 1;  // last field whose first tile is <= t
+                // Last field whose first tile is <= t, by warp 0 together:
+                // each round the 32 lanes test 32 evenly spaced fields of the
+                // range [lo, hi] and the range shrinks to the gap after the
+                // last field that passes (tile_start is non-decreasing and
+                // tile_start[lo] <= t throughout, so lane 0 always passes).
+                // 4096 fields take 3 rounds of loads instead of 12.
+                int lo = 0, hi = n - 1;
                 while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (bounds_ok(kSitePlan, mid, (long long)n + 1) && tile_start[mid] <= t) lo = mid;
-                    else hi = mid - 1;
+                    const int step = (hi - lo + 32) >> 5;
+                    const int idx = lo + lane * step;
+                    const bool ok = idx <= hi && bounds_ok(kSitePlan, idx, (long long)n + 1) && tile_start[idx] <= t;
+                    const unsigned m = __ballot_sync(0xffffffffu, ok);
+                    lo += (31 - __clz(m | 1u)) * step;
+                    hi = min(hi, lo + step - 1);
                 }
-                s_field = lo;
+                if (lane == 0) {
+                    s_field = lo;
+                    next = (long long)atomicAdd(counter, 1ULL);
+                }
             }
+            if (lane == 0) s_tile = t;
         }
         __syncthreads();
         const long long t = s_tile;
