@@ -87,6 +87,11 @@ int ptg_check_desc(ptg_ctx* ctx, const ptg_field_desc* d, int kind, int* spc_log
 int ptg_make_field_plan(ptg_ctx* ctx, const ptg_field_desc* d, int method, void* out, int s, int64_t band_start,
                         int64_t band_len, ptg::FieldPlan* P);
 bool ptg_per_sample(const ptg_field_desc* d, int spc_log2);
+// Validates a batch of 2D fields and fills plans[0..n) and the tile prefix
+// sums tiles[0..n] with the fields ordered by the batch kernel's code path;
+// scratch holds 3 n ints (ptg_batch.cu).
+int ptg_build_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int n, ptg::FieldPlan* plans,
+                    long long* tiles, int* scratch, size_t* smem);
 bool ptg_fused_ridged(const ptg_field_desc* d, int spc_log2);
 int ptg_make_simplex_plan(ptg_ctx* ctx, const ptg_field_desc* d, void* out, int s, int64_t band_start,
                           int64_t band_len, ptg::SimplexPlan* P);

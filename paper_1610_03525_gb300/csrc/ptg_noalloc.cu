@@ -70,26 +70,10 @@ extern "C" int ptg_batch_noalloc(ptg_ctx* ctx, const ptg_field_desc* descs, void
     NoAllocScratch* dev = static_cast<NoAllocScratch*>(g_dev_addr[ctx->device]);
 
     size_t smem = 0;
-    long long acc = 0;
-    for (int f = 0; f < n; ++f) {
-        const ptg_field_desc* d = descs + f;
-        int s = 0;
-        int rc = ptg_check_desc(ctx, d, kKindField, &s);
-        if (rc != PTG_OK) return ptg_fail(ctx, rc, "batch field %d: %s", f, ctx->err.c_str());
-        if (d->dims != 2) return ptg_fail(ctx, PTG_ERR_UNSUPPORTED, "batch field %d: batches are 2D", f);
-        if (ptg_per_sample(d, s))
-            return ptg_fail(ctx, PTG_ERR_UNSUPPORTED,
-                            "batch field %d: batches need lacunarity 2, a power-of-two spc and no ridged noise", f);
-        if (!outs[f]) return ptg_fail(ctx, PTG_ERR_INVALID, "batch field %d: out is NULL", f);
-        rc = ptg_make_field_plan(ctx, d, ptg_kernel_method(kKindField, d), outs[f], s, 0, d->size[1],
-                                 &g_stage.plans[f]);
-        if (rc != PTG_OK) return ptg_fail(ctx, rc, "batch field %d: %s", f, ctx->err.c_str());
-        const size_t sm = fbm2d_smem_bytes(g_stage.plans[f]);
-        if (sm > smem) smem = sm;
-        g_stage.tiles[f] = acc;
-        acc += (long long)g_stage.plans[f].tiles_x * g_stage.plans[f].tiles_y;
-    }
-    g_stage.tiles[n] = acc;
+    int scratch[3 * kNoAllocMaxFields];
+    const int rc = ptg_build_batch(ctx, descs, outs, n, g_stage.plans, g_stage.tiles, scratch, &smem);
+    if (rc != PTG_OK) return rc;
+    const long long acc = g_stage.tiles[n];
 
     cudaStream_t st = (cudaStream_t)stream;
     e = cudaMemcpyAsync(dev->plans, g_stage.plans, sizeof(FieldPlan) * n, cudaMemcpyHostToDevice, st);
