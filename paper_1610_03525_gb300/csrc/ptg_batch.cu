@@ -140,7 +140,7 @@ int ptg_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int3
     cudaMemsetAsync(ctx->batch_dcounter, 0, sizeof(unsigned long long), st);
     const long long total = ctx->batch_htiles[n];
     if (total == 0) return PTG_OK;
-    e = launch_fbm2d_batch(ctx->batch_dplans, ctx->batch_dtiles, n, ctx->batch_dcounter, smem,
+    e = launch_fbm2d_batch(ctx->batch_dplans, ctx->batch_dtiles, n, ctx->batch_dcounter, total, smem,
                            batch_grid(ctx, smem, total), st);
     return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "batch launch");
 }
@@ -182,7 +182,7 @@ int ptg_batch_prepare(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* ou
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaMemsetAsync(p->dcounter, 0, sizeof(unsigned long long), cs);
-            if (tiles[n] > 0) launch_fbm2d_batch(p->dplans, p->dtiles, n, p->dcounter, smem, blocks, cs);
+            if (tiles[n] > 0) launch_fbm2d_batch(p->dplans, p->dtiles, n, p->dcounter, tiles[n], smem, blocks, cs);
             e = cudaStreamEndCapture(cs, &p->graph);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);

@@ -32,9 +32,11 @@ size_t fbm2d_smem_bytes(const FieldPlan& P);
 cudaError_t launch_fbm2d(const FieldPlan& P, int method, int s, cudaStream_t stream);
 
 // Persistent batched 2D generator over many fields (plans, tile_start and
-// counter in device memory; counter must be zero at launch).
+// counter in device memory; counter must be zero at launch; total_tiles =
+// tile_start[n], which sets how many tiles a CTA takes at a time).
 cudaError_t launch_fbm2d_batch(const FieldPlan* plans, const long long* tile_start, int n,
-                               unsigned long long* counter, size_t smem, int blocks, cudaStream_t stream);
+                               unsigned long long* counter, long long total_tiles, size_t smem, int blocks,
+                               cudaStream_t stream);
 int fbm2d_batch_blocks_per_sm(size_t smem);
 
 size_t fbm3d_smem_bytes(const FieldPlan& P);

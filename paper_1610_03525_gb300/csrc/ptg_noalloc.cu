@@ -84,6 +84,6 @@ extern "C" int ptg_batch_noalloc(ptg_ctx* ctx, const ptg_field_desc* descs, void
     if (acc == 0) return PTG_OK;
     const long long resident = (long long)ctx->num_sms * fbm2d_batch_blocks_per_sm(smem);
     const int blocks = (int)(acc < resident ? acc : resident);
-    e = launch_fbm2d_batch(dev->plans, dev->tiles, n, &dev->counter, smem, blocks, st);
+    e = launch_fbm2d_batch(dev->plans, dev->tiles, n, &dev->counter, acc, smem, blocks, st);
     return e == cudaSuccess ? PTG_OK : ptg_cuda_fail(ctx, e, "ptg_batch_noalloc launch");
 }

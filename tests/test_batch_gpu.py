@@ -57,6 +57,28 @@ def test_batch_equals_single_launches(ctx):
         assert torch.equal(o, r), k
 
 
+@pytest.mark.parametrize("n", [128, 400, 1024])
+def test_batch_tile_groups(ctx, n):
+    """Batches large enough that each CTA takes 2 or 4 consecutive tiles at a
+    time (on a 152-SM GB300: about 6, 20 and 52 tiles per resident CTA, so
+    groups of 1, 2 and 4), and groups that span several fields: every field
+    equals its own single launch bit for bit, the prepared graph too."""
+    descs, outs = _chunks(n, seed=77)
+    ref = _singles(ctx, descs, outs)
+    P.ptg_batch(ctx, descs, outs)
+    torch.cuda.synchronize()
+    for k, (o, r) in enumerate(zip(outs, ref)):
+        assert torch.equal(o, r), k
+    for o in outs:
+        o.fill_(float("nan"))
+    plan = P.ptg_batch_prepare(ctx, descs, outs)
+    P.ptg_batch_launch(plan)
+    torch.cuda.synchronize()
+    P.ptg_batch_free(plan)
+    for k, (o, r) in enumerate(zip(outs, ref)):
+        assert torch.equal(o, r), k
+
+
 def test_batch_mixed_launch_configs(ctx):
     """Fields pinned to every 2D launch configuration in one batch: each
     equals its own single launch with the same configuration."""
