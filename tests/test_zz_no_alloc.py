@@ -93,3 +93,26 @@ def test_noalloc_rejects_more_than_256_fields(ctx):
     bad = P.make_desc(dims=2, size=(64, 64), spc=64, octaves=0)
     assert _call_noalloc(ctx, [d, bad], [out, out]) == P.PTG_ERR_INVALID
     assert "batch field 1" in P.ptg_last_error(ctx)
+
+
+def test_noalloc_large_fields_take_tile_groups(ctx):
+    """A few large fields (32,775 tiles, 36 per resident CTA on a 152-SM
+    GB300): the kernel hands out 4 tiles at a time, groups cross field
+    boundaries, and the output equals one ptg_field launch per field bit for
+    bit, on two calls in a row."""
+    descs, outs, refs = [], [], []
+    for k, (w, h, sm) in enumerate([(8192, 4096, P.PTG_C1), (4096, 8192, P.PTG_C2), (8192, 4096, P.PTG_C1),
+                                    (8192, 4096, P.PTG_ZERO_GRADIENT), (64, 64, P.PTG_C1), (192, 128, P.PTG_C2)]):
+        d = P.make_desc(dims=2, size=(w, h), spc=1024, origin=(k * 3, -k, 0), octaves=12, smoothness=sm, seed=k)
+        descs.append(d)
+        outs.append(torch.full((h, w), float("nan"), device="cuda"))
+        refs.append(torch.empty((h, w), device="cuda"))
+        P.ptg_field(ctx, d, refs[-1])
+    torch.cuda.synchronize()
+    for call in range(2):
+        for o in outs:
+            o.fill_(float("nan"))
+        assert _call_noalloc(ctx, descs, outs) == P.PTG_OK, P.ptg_last_error(ctx)
+        torch.cuda.synchronize()
+        for k, (o, r) in enumerate(zip(outs, refs)):
+            assert torch.equal(o, r), (call, k)
