@@ -679,6 +679,8 @@ int ptgo_field_samples(const ptgo_desc* d, const int64_t* idx, int64_t n, double
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel
+#else
+    (void)nthreads;  /* one thread without OpenMP */
 #endif
     {
         double coef[32][216];
