@@ -1,8 +1,6 @@
 """Request loop: admission under the HBM budget, overlap on worker streams,
 results identical alone and in the mix, timestamps, cancel and timeouts
 (the stall is made on the host; no device wait is involved)."""
-import time
-
 import pytest
 
 torch = pytest.importorskip("torch")
