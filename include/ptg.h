@@ -216,8 +216,11 @@ int ptg_generate_host(ptg_ctx* ctx, const ptg_field_desc* desc, int32_t method, 
  * persistent launch: resident CTAs pull 64 x 64 tiles of all fields from a
  * device work counter.  descs: host array of n descriptors; outs: host array
  * of n device output pointers.  Results equal n separate ptg_field calls
- * bit for bit.  Uses context-owned device memory for the launch plans and
- * the counter (grown on demand, kept).  Asynchronous on `stream`. */
+ * bit for bit.  The fields may come in any order: the library lays them out
+ * grouped by kernel path (method and thread shape), which keeps one path in
+ * the instruction cache at a time.  Uses context-owned device memory for the
+ * launch plans and the counter (grown on demand, kept).  Asynchronous on
+ * `stream`. */
 int ptg_batch(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n, void* stream);
 
 /* A prepared batch: plans uploaded once and the launch (counter reset plus
@@ -247,8 +250,8 @@ int ptg_batch_free(ptg_batch_plan* plan);
  * called.  The caller owns every output buffer.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress).  All calls
  * share the array and clear its counter: calls that overlap on the GPU race,
- * so order them (one stream, or events).  n > 256 returns PTG_ERR_INVALID.  The paper has no counterpart;
- * this is a deployment aid. */
+ * so order them (one stream, or events).  n > 256 returns PTG_ERR_INVALID.
+ * The paper has no counterpart; this is a deployment aid. */
 int ptg_batch_noalloc(ptg_ctx* ctx, const ptg_field_desc* descs, void* const* outs, int32_t n, void* stream);
 
 /* Request loop.  Queue one field for asynchronous generation into device
